@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the analytic SPH boundary-integral hot path on one GB300 per rank.
+
+Workload (synthetic, seeded): 1,048,576 particles on a jittered 1024x1024 lattice in the unit
+square, H = 4/1024, inside a closed box wall (8 cells thick) with a solid square obstacle
+[0.375, 0.625]^2, all meshed at dx into 197,120 triangles (interior vertices jittered).
+One step = the whole hot path: particle bounds, cell grid, triangle binning, exact culling,
+then the closed-form integrals (gamma, grad gamma and the 10 monomial moments of degree <= 3)
+for the Wendland C2, Wendland C4 and cubic B-spline kernels, summed per particle, in the
+FP32 + FP64-fix-up mode.  Units: pair integrals (one culled pair, one kernel) per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank solves its own instance (independent problems, weak
+scaling), no collective on the data path; value = all ranks' units / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair integrals/s (∫W+∇W) vs plain FP64 GPU at ≤1e-5 rel err; % pipe peak"
+UNIT = "pair-integrals/s"
+KERNELS = ["wendland_c2", "wendland_c4", "cubic_spline"]
+MOMENT_DEGREE = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (host logic covered by a gloo test)
+# ---------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, ws: int, device="cpu") -> float:
+    """Max over ranks (identity at world size 1)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, elapsed_ms: float, ws: int, device="cpu") -> dict:
+    """Whole-job throughput: all ranks' units / the slowest rank's time."""
+    tmax = reduce_max(elapsed_ms, ws, device)
+    return {"value": units_per_rank * ws / (tmax / 1e3), "max_ms": tmax}
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        smi = shutil.which("nvidia-smi")
+        if smi is None:
+            return
+        self.proc = subprocess.Popen([smi, f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                      "-i", str(self.idx), "-lms", "100"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for i, n in enumerate(names):
+                    if r[5 + i].lower() in ("active", "1", "yes"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (reported baseline; the reference arm)
+# ---------------------------------------------------------------------------------------
+def oracle_sample_run(w, frac: float, seed: int, kernel="wendland_c2"):
+    import oracle
+    rng = np.random.default_rng(seed)
+    n = len(w.particles)
+    idx = np.sort(rng.choice(n, max(1, int(frac * n)), replace=False))
+    sub = w.particles[idx]
+    t0 = time.perf_counter()
+    off, pt = oracle.cull(sub, w.triangles, w.H)
+    oracle.particle_sums(kernel, w.H, sub, w.triangles, off, pt, MOMENT_DEGREE)
+    dt = time.perf_counter() - t0
+    return int(off[-1]), dt, len(idx)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2507_21686_gb300 import workloads as W
+    oracle.build()
+    w = W.box_obstacle()
+    frac = 0.004
+    for s in range(args.warmup):
+        oracle_sample_run(w, frac, 1000 + s)
+    pairs, secs = 0, 0.0
+    for s in range(args.steps):
+        p, dt, _ = oracle_sample_run(w, frac, 2000 + s)
+        pairs += p
+        secs += dt
+    value = pairs / secs
+    cores = oracle.num_threads()
+    sample = (f"{frac:.1%} random particle sample per step ({int(frac * len(w.particles))} particles, "
+              f"brute-force cull over all {len(w.triangles)} triangles + per-particle sums, "
+              f"Wendland C2, gamma+grad+10 moments); value in culled pairs/s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "kernels": ["wendland_c2"],
+                                            "moment_degree": MOMENT_DEGREE, "H": w.H},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(ws, "nccl")
+    from paper_2507_21686_gb300 import build as B
+    B.build()
+    from paper_2507_21686_gb300 import perfmodel as PM
+    from paper_2507_21686_gb300 import workloads as W
+    from paper_2507_21686_gb300.api import Context
+
+    dev = torch.device("cuda", local)
+    w = W.box_obstacle()
+    N, M = len(w.particles), len(w.triangles)
+    parts_h = torch.from_numpy(w.particles).pin_memory()
+    tris_h = torch.from_numpy(w.triangles).pin_memory()
+    parts = parts_h.to(dev)
+    tris = tris_h.to(dev)
+    ctx = Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(mode, timers=None):
+        """cells + cull once, then the integrals of every kernel over that pair list
+        (the same work as sph2d_boundary_integrals per kernel, culling shared)."""
+        outs = []
+        if timers is not None:
+            timers[0][0].record(stream)
+        ctx.build_cells(parts, tris, w.H)
+        if timers is not None:
+            timers[0][1].record(stream)
+        for i, k in enumerate(KERNELS, start=1):
+            if timers is not None:
+                timers[i][0].record(stream)
+            outs.append(ctx.integrals_from_pairs(k, MOMENT_DEGREE, mode))
+            if timers is not None:
+                timers[i][1].record(stream)
+        return outs
+
+    # L2 is 129 MB and the inputs are ~21 MB: flush it between timed steps
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(mode, steps, warmup, sample_clocks=False, per_kernel=False):
+        for _ in range(warmup):
+            step(mode)
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        ev = []
+        kt = []
+        launches0 = ctx.stats()["n_launches"]
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tms = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(len(KERNELS) + 1)] if per_kernel else None
+            a.record(stream)
+            step(mode, tms if per_kernel else None)
+            b.record(stream)
+            ev.append((a, b))
+            kt.append(tms)
+        torch.cuda.synchronize()
+        launches = ctx.stats()["n_launches"] - launches0
+        barrier(ws)
+        clocks = sampler.stop() if sampler else None
+        ms = [x.elapsed_time(y) for x, y in ev]
+        kms = None
+        if per_kernel:
+            kms = [[t[i][0].elapsed_time(t[i][1]) for t in kt] for i in range(len(KERNELS) + 1)]
+        return ms, kms, launches, clocks
+
+    # ---- pairs and their op counts
+    ctx.build_cells(parts, tris, w.H)
+    P = ctx.pair_count()
+    st = ctx.stats()
+    off, ptri = ctx.pair_list()
+    off_c, ptri_c = off.cpu().numpy(), ptri.cpu().numpy()
+    rng = np.random.default_rng(0)
+    qs = rng.choice(P, min(P, 400), replace=False)
+    pid = np.searchsorted(off_c, qs, side="right") - 1
+    loc = (w.triangles[ptri_c[qs]].astype(np.float64).reshape(-1, 3, 2)
+           - w.particles[pid, None, :2].astype(np.float64)) / w.H
+    loc = loc.reshape(-1, 6)
+    flops32 = {k: PM.mean_flops_per_pair(k, True, True, loc) for k in KERNELS}
+    flops64 = {k: PM.mean_flops_per_pair(k, True, False, loc) for k in KERNELS}
+
+    # ---- main timed run: FP32 + FP64 fix-up
+    ms, kms, launches, clocks = timed("fp32_fixup", args.steps, args.warmup, sample_clocks=True,
+                                      per_kernel=True)
+    fix = ctx.stats()["n_fixup"]
+    units = P * len(KERNELS)
+    ms_step = float(np.mean(ms))
+    agg = aggregate(units * args.steps, float(np.sum(ms)), ws, dev)
+
+    # dominant kernel: the integral launch with the largest mean time
+    cull_ms = float(np.mean(kms[0]))
+    kmeans = [float(np.mean(x)) for x in kms[1:]]
+    dom = int(np.argmax(kmeans))
+    dom_k = KERNELS[dom]
+    achieved_tflops = flops32[dom_k] * P / (kmeans[dom] / 1e3) / 1e12
+    peak = PM.fp32_peak_tflops()
+
+    # ---- plain FP64 GPU path, same workload
+    ms64, kms64, _, _ = timed("fp64", max(1, args.fp64_steps), 1, per_kernel=True)
+    k64 = [float(np.mean(x)) for x in kms64[1:]]
+    value64 = units / (float(np.mean(ms64)) / 1e3)
+    dom64 = int(np.argmax(k64))
+    achieved64 = flops64[KERNELS[dom64]] * P / (k64[dom64] / 1e3) / 1e12
+
+    # ---- accuracy of the timed path against the FP64 GPU path on this workload
+    from tests.helpers import rel_err, scales
+    max_err = {}
+    o32 = step("fp32_fixup")
+    o64 = step("fp64")
+    for k, a, b in zip(KERNELS, o32, o64):
+        got = torch.cat([a[0][:, None], a[1], a[2]], 1).double().cpu().numpy()
+        ref = torch.cat([b[0][:, None], b[1], b[2]], 1).cpu().numpy()
+        max_err[k] = float(rel_err(got, ref, scales(k, w.H, 10)).max())
+    del o32, o64
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ctx, parts_h, tris_h, w, dev, stream, P, ws)
+
+    # ---- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        frac = 0.01
+        pr, secs, npart = oracle_sample_run(w, frac, 12345)
+        cpu = {"value": pr / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{frac:.0%} random particle sample ({npart} particles, {pr} culled pairs), "
+                         f"Wendland C2, brute-force cull + gamma/grad/10 moments in FP64, {secs:.1f} s"}
+
+    peaks = measured_peaks()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": agg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "particles": N, "triangles": M, "pairs": P, "H": w.H,
+                   "kernels": KERNELS, "moment_degree": MOMENT_DEGREE, "mode": "fp32_fixup",
+                   "l2": "flushed between timed steps (512 MB memset outside the timed events)",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / peak, "traffic": None,
+                     "kernel": f"integrals_kernel<float,{dom_k},moments>",
+                     "flops_per_pair": flops32[dom_k], "kernel_ms": kmeans[dom],
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)"},
+        "per_kernel_ms": dict(zip(KERNELS, kmeans)),
+        "cull_ms": cull_ms,
+        "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
+                      "per_kernel_ms": dict(zip(KERNELS, k64)),
+                      "achieved_tflops": achieved64, "nominal_peak_tflops": PM.FP64_PEAK_TFLOPS_NOMINAL,
+                      "frac_of_nominal": achieved64 / PM.FP64_PEAK_TFLOPS_NOMINAL,
+                      "flops_per_pair": flops64[KERNELS[dom64]]},
+        "speedup_vs_fp64_path": agg["value"] / value64,
+        "max_rel_err_vs_fp64_path": max_err,
+        "fixup_pairs_per_step": fix,
+        "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "measured_peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, ctx, parts_h, tris_h, w, dev, stream, P, ws):
+    """Same metric through the public API: pinned host inputs copied in, results copied out."""
+    import torch
+    N = parts_h.shape[0]
+    nm = 10
+    outs_h = [(torch.empty(N, dtype=torch.float32).pin_memory(),
+               torch.empty((N, 2), dtype=torch.float32).pin_memory(),
+               torch.empty((N, nm), dtype=torch.float32).pin_memory()) for _ in KERNELS]
+
+    def e2e_step():
+        p = parts_h.to(dev, non_blocking=True)
+        t = tris_h.to(dev, non_blocking=True)
+        res = [ctx.boundary_integrals(p, t, KERNELS[0], w.H, MOMENT_DEGREE, "fp32_fixup")]
+        for k in KERNELS[1:]:
+            res.append(ctx.integrals_from_pairs(k, MOMENT_DEGREE, "fp32_fixup"))
+        for (g, gr, mo), (hg, hgr, hmo) in zip(res, outs_h):
+            hg.copy_(g, non_blocking=True)
+            hgr.copy_(gr, non_blocking=True)
+            hmo.copy_(mo, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    agg = aggregate(P * len(KERNELS) * args.steps, secs * 1e3, ws, dev)
+    h2d = parts_h.numel() * 4 + tris_h.numel() * 4
+    d2h = sum(x.numel() * 4 for o in outs_h for x in o)
+    return {"value": agg["value"], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": secs * 1e3 / args.steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * sph2d -- analytic 2-D SPH boundary integrals on one GPU (sm_103a).
+ *
+ * For every (particle, triangle) pair within the kernel support H this library evaluates
+ * the area integrals of a compact polynomial SPH kernel, of its gradient, and of its
+ * monomial moments over the triangle, and sums them per particle:
+ *
+ *   gamma_i      = sum_T int_T W(x_i - x', H) dx'                       (Sec. 2, Eq. boundaryint
+ *                                                                         with A = 1)
+ *   grad_gamma_i = d gamma_i / d x_i = sum_T int_T grad_x W(x_i - x') dx'  (Sec. 2, Eq.
+ *                                                                         nablaIntegral; Sec. 3,
+ *                                                                         Eq. basicdiff)
+ *   M_ab,i       = sum_T int_T xi^a eta^b W dx',  (xi, eta) = (x' - x_i)/H, a+b <= 3
+ *                  (the monomial integrals of Sec. 3, Eq. taus, in the normalised frame of
+ *                  Sec. 2)
+ *
+ * with W(r, H) = C/H^2 k(r/H) (Sec. 2, Dehnen-Aly form) and one of these kernels k(q), q < 1:
+ *   SPH2D_WENDLAND_C2   (1-q)^4 (1+4q)                       C = 7/pi
+ *   SPH2D_WENDLAND_C4   (1-q)^6 (1+6q+35/3 q^2)              C = 9/pi   (Sec. 2 uses this kernel;
+ *                                                            its printed 27/(16 pi) does not
+ *                                                            satisfy int W = 1 in 2-D)
+ *   SPH2D_WENDLAND_C6   (1-q)^8 (1+8q+25q^2+32q^3)           C = 78/(7 pi)
+ *   SPH2D_CUBIC_SPLINE  1-6q^2+6q^3 (q<1/2), 2(1-q)^3 (q<1)  C = 40/(7 pi)
+ *
+ * Triangles are disjoint (Sec. 2) and may be given in either orientation; a zero-area
+ * triangle contributes exactly 0.  Moments are ordered
+ *   M00 M10 M01 M20 M11 M02 M30 M21 M12 M03   (nm = (deg+1)(deg+2)/2 of them).
+ *
+ * Conventions for every entry point
+ *   - All array arguments are DEVICE pointers on the context's device unless stated; the
+ *     caller owns them.  The library owns only scratch memory held in the context, which it
+ *     grows on demand and frees in sph2d_destroy.
+ *   - Work is enqueued on the context's stream.  Calls that size a pair list synchronise
+ *     that stream once or twice to read counts back (documented per call).
+ *   - Real-valued outputs are double in SPH2D_FP64 mode and float in SPH2D_FP32_FIXUP mode.
+ *   - Every call returns a status; no C++ exception crosses this boundary and no device code
+ *     traps.  On error, sph2d_last_error() describes it and outputs are unspecified.
+ *   - Inputs: particles are float4 per particle (x, y, unused, unused), 16-byte aligned;
+ *     triangles are 6 floats (x0, y0, x1, y1, x2, y2), 4-byte aligned.
+ *
+ * Pair culling (Sec. 2: "triangles that overlap the support radius"): pair (i, T) is kept
+ * iff the closed triangle T lies at Euclidean distance < H from x_i.  The test is evaluated
+ * in IEEE double from the float inputs, without fused multiply-add, in this order:
+ *   for each edge e = (v_e, v_{e+1}):  ex = x_{e+1}-x_e, ey = y_{e+1}-y_e,
+ *       wx = px-x_e, wy = py-y_e, cr = wx*ey - wy*ex, l2 = ex*ex + ey*ey, tn = wx*ex + wy*ey,
+ *       d2 = (tn <= 0) ? wx*wx + wy*wy
+ *          : (tn >= l2) ? (px-x_{e+1})^2 + (py-y_{e+1})^2 : cr*cr / l2
+ *   keep = (no cr > 0 or no cr < 0)  ||  min_e d2 < H*H
+ * Pair lists are particle-major in input particle order, ascending triangle id within a
+ * particle.
+ */
+#ifndef SPH2D_H
+#define SPH2D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPH2D_OK = 0,
+  SPH2D_ERR_INVALID_ARG = 1,      /* null pointer, bad size, H <= 0 or not finite, bad enum */
+  SPH2D_ERR_NONFINITE_INPUT = 2,  /* a particle or vertex coordinate is NaN or infinite */
+  SPH2D_ERR_CAPACITY = 3,         /* caller buffer too small; *required holds the size */
+  SPH2D_ERR_NOT_BUILT = 4,        /* no pair list in the context yet */
+  SPH2D_ERR_CUDA = 5,             /* a CUDA runtime call failed (message in last_error) */
+  SPH2D_ERR_UNSUPPORTED = 6,      /* valid request that this build does not provide */
+  SPH2D_ERR_OUT_OF_MEMORY = 7     /* scratch allocation failed */
+} sph2d_status;
+
+typedef enum {
+  SPH2D_WENDLAND_C2 = 0,
+  SPH2D_WENDLAND_C4 = 1,
+  SPH2D_WENDLAND_C6 = 2,
+  SPH2D_CUBIC_SPLINE = 3
+} sph2d_kernel;
+
+typedef enum {
+  SPH2D_FP64 = 0,        /* every step in IEEE double */
+  SPH2D_FP32_FIXUP = 1,  /* FP32 arithmetic; pairs whose error bound exceeds the budget are
+                            recomputed in FP64 (count reported by sph2d_last_stats) */
+  SPH2D_SURROGATE = 2    /* learned surrogate with guarded analytic fallback (gamma, grad only) */
+} sph2d_mode;
+
+typedef struct sph2d_ctx sph2d_ctx;
+
+/* Statistics of the most recent integral call on a context. */
+typedef struct {
+  int64_t n_particles;
+  int64_t n_triangles;
+  int64_t n_pairs;          /* culled pairs evaluated */
+  int64_t n_fixup;          /* pairs recomputed in FP64 (SPH2D_FP32_FIXUP) */
+  int64_t n_fallback;       /* pairs routed to the analytic path (SPH2D_SURROGATE) */
+  int64_t n_cells;          /* cells of the culling grid */
+  int64_t n_candidates;     /* (triangle, cell) incidences of the culling grid */
+  int64_t n_launches;       /* kernels this context has launched since sph2d_init (cumulative) */
+} sph2d_stats;
+
+/* Create a context on CUDA device `device`; `stream` is a cudaStream_t (NULL = legacy
+ * default stream).  *ctx receives the handle.  Errors: INVALID_ARG, CUDA. */
+sph2d_status sph2d_init(sph2d_ctx** ctx, int device, void* stream);
+
+/* Free the context and its scratch (synchronises its stream first).  NULL is a no-op. */
+sph2d_status sph2d_destroy(sph2d_ctx* ctx);
+
+/* Change the stream later calls enqueue on (a cudaStream_t). */
+sph2d_status sph2d_set_stream(sph2d_ctx* ctx, void* stream);
+
+/* Message for the last failed call on ctx (static storage inside ctx; "" if none). */
+const char* sph2d_last_error(const sph2d_ctx* ctx);
+
+/* Copy the statistics of the last integral call into *out (host pointer).  Synchronises the
+ * context's stream when the last call's fix-up count is still in flight. */
+sph2d_status sph2d_last_stats(const sph2d_ctx* ctx, sph2d_stats* out);
+
+/* Library version, e.g. 100 for 1.0.0. */
+int sph2d_version(void);
+
+/*
+ * Build the culling grid and the pair list for (particles, triangles, H) and keep them in
+ * the context (Sec. 2: the neighbouring triangles N_T of each particle).
+ *   particles  device float4 [N]     (x, y, _, _)
+ *   tris       device float  [M][6]
+ *   H          support radius (> 0, finite), in the same units as the coordinates
+ * The grid covers the particles' bounding box with square cells of side >= H; each
+ * triangle is binned into every cell its H-expanded bounding box touches, and each
+ * particle tests the triangles of its own cell with the exact predicate above.
+ * Synchronises the stream three times (bounds, grid size, pair count).
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_build_cells(sph2d_ctx* ctx, const float* particles, int64_t N,
+                               const float* tris, int64_t M, double H);
+
+/* Number of pairs in the context's current pair list (host pointer out).  NOT_BUILT if none. */
+sph2d_status sph2d_pair_count(const sph2d_ctx* ctx, int64_t* n_pairs);
+
+/*
+ * Copy the current pair list into caller device buffers: off int64 [N+1] (CSR offsets in
+ * input particle order), tri int32 [cap] (triangle ids, ascending within a particle).
+ * If cap < number of pairs, returns CAPACITY and writes the number to *required (host).
+ */
+sph2d_status sph2d_pair_list(sph2d_ctx* ctx, int64_t* off, int32_t* tri, int64_t cap,
+                             int64_t* required);
+
+/*
+ * Full hot path: build cells and pair list (as sph2d_build_cells), then evaluate every
+ * pair's integrals in closed form and sum them per particle (Sec. 4-5 decomposition,
+ * realised as the exact edge/sector fan form described in the implementation).
+ *   kernel         sph2d_kernel
+ *   moment_degree  -1 (no moments) or 0..3
+ *   mode           SPH2D_FP64 or SPH2D_FP32_FIXUP
+ *   gamma          device real [N]
+ *   grad_gamma     device real [N][2]          (may be NULL)
+ *   moments        device real [N][nm]         (NULL iff moment_degree < 0)
+ * "real" is double for SPH2D_FP64 and float for SPH2D_FP32_FIXUP.  Particles with no pair
+ * get zeros.  Synchronises as sph2d_build_cells does.
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, UNSUPPORTED, CUDA.
+ */
+sph2d_status sph2d_boundary_integrals(sph2d_ctx* ctx, const float* particles, int64_t N,
+                                      const float* tris, int64_t M, int kernel, double H,
+                                      int moment_degree, int mode, void* gamma,
+                                      void* grad_gamma, void* moments);
+
+/*
+ * Integrals over the pair list already in the context (built by sph2d_build_cells or by a
+ * previous sph2d_boundary_integrals on the same inputs), so that several kernels or modes
+ * can reuse one culling pass.  The particle and triangle arrays of that build must still
+ * hold the same data.  Does not synchronise.  Arguments as sph2d_boundary_integrals.
+ * Errors: NOT_BUILT, INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+sph2d_status sph2d_integrals_from_pairs(sph2d_ctx* ctx, int kernel, int moment_degree,
+                                        int mode, void* gamma, void* grad_gamma,
+                                        void* moments);
+
+/*
+ * Independent pairs, no culling and no per-particle sum (precision studies, surrogate
+ * training labels).
+ *   pairs   device double [P][8] = (px, py, x0, y0, x1, y1, x2, y2); world units, H > 0
+ *   out     device real [P][3+nm] = (gamma, dgamma/dpx, dgamma/dpy, M00..)
+ * In SPH2D_FP32_FIXUP mode the local-frame geometry (v - p)/H is formed in double and
+ * rounded once to float; outputs are float.  Does not synchronise.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+sph2d_status sph2d_pair_integrals(sph2d_ctx* ctx, const double* pairs, int64_t P, int kernel,
+                                  double H, int moment_degree, int mode, void* out);
+
+/*
+ * Adjoint of sph2d_boundary_integrals for a loss L(gamma): given dL/dgamma, returns
+ *   d_particles [N][2] = dL/dx_i      = dL/dgamma_i * grad_gamma_i   (Sec. 3, Eq. basicdiff)
+ *   d_tris      [M][6] = dL/dnu_j     = sum_i dL/dgamma_i * d gamma_i / d nu_j
+ * where d gamma_i/d nu_j is the transport-theorem edge integral of W weighted by the
+ * vertex's hat function (no counterpart printed in the paper; it is the derivative of its
+ * area integral with respect to the boundary).  The pair list is rebuilt from the inputs;
+ * per-pair geometry is recomputed, nothing is stored from the forward call.  Vertex
+ * gradients are reduced triangle-major in a fixed order (deterministic).
+ *   d_gamma       device real [N]
+ *   d_grad_gamma  must be NULL (second-order terms are not provided: UNSUPPORTED)
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, UNSUPPORTED, CUDA.
+ */
+sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* ctx, const float* particles,
+                                               int64_t N, const float* tris, int64_t M,
+                                               int kernel, double H, int mode,
+                                               const void* d_gamma, const void* d_grad_gamma,
+                                               void* d_particles, void* d_tris);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH2D_H */

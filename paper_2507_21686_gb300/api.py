@@ -1,0 +1,228 @@
+"""Python API over libsph2d: PyTorch supplies device memory and streams; every step of the
+computation runs in the library's CUDA kernels.
+
+    from paper_2507_21686_gb300 import boundary_integrals
+    gamma, grad_gamma, moments = boundary_integrals(particles, tris, "wendland_c2", H,
+                                                    moment_degree=3, mode="fp32_fixup")
+
+particles: float32 [N, 4] (x, y, 0, 0) or [N, 2]; tris: float32 [M, 6] or [M, 3, 2].  CUDA
+tensors are used in place; CPU tensors are copied to the device (and results copied back).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import KERNELS, MODES, Stats, check
+
+
+def _kernel_id(kernel) -> int:
+    if isinstance(kernel, str):
+        if kernel not in KERNELS:
+            raise ValueError(f"unknown kernel {kernel!r}; expected one of {sorted(KERNELS)}")
+        return KERNELS[kernel]
+    return int(kernel)
+
+
+def _mode_id(mode) -> int:
+    if isinstance(mode, str):
+        if mode not in MODES:
+            raise ValueError(f"unknown mode {mode!r}; expected one of {sorted(MODES)}")
+        return MODES[mode]
+    return int(mode)
+
+
+def num_moments(deg: int) -> int:
+    return 0 if deg < 0 else (deg + 1) * (deg + 2) // 2
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def as_particles(p: torch.Tensor, device) -> torch.Tensor:
+    """float32 [N, 4] contiguous on `device` (pads [N, 2] with zeros)."""
+    if p.dim() != 2 or p.shape[1] not in (2, 4):
+        raise ValueError("particles must be [N, 2] or [N, 4]")
+    if p.shape[1] == 2:
+        q = torch.zeros((p.shape[0], 4), dtype=torch.float32, device=p.device)
+        q[:, :2] = p
+        p = q
+    return p.to(device=device, dtype=torch.float32, non_blocking=True).contiguous()
+
+
+def as_triangles(t: torch.Tensor, device) -> torch.Tensor:
+    if t.dim() == 3:
+        t = t.reshape(t.shape[0], 6)
+    if t.dim() != 2 or t.shape[1] != 6:
+        raise ValueError("triangles must be [M, 6] or [M, 3, 2]")
+    return t.to(device=device, dtype=torch.float32, non_blocking=True).contiguous()
+
+
+class Context:
+    """One libsph2d context (scratch memory + culling state) on one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        self.lib = _lib.load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        st = self.lib.sph2d_init(ctypes.byref(h), self.device, None)
+        if st != 0:
+            raise _lib.Sph2dError(st, "sph2d_init failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sph2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        check(self.lib, self.h, self.lib.sph2d_set_stream(self.h, ctypes.c_void_p(s)))
+
+    def _dev(self):
+        return torch.device("cuda", self.device)
+
+    # -- culling ------------------------------------------------------------------------
+    def build_cells(self, particles, tris, H: float):
+        p = as_particles(particles, self._dev())
+        t = as_triangles(tris, self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_build_cells(self.h, _ptr(p), p.shape[0], _ptr(t),
+                                                            t.shape[0], float(H)))
+        self._keep = (p, t)
+        return self
+
+    def pair_count(self) -> int:
+        n = ctypes.c_int64()
+        check(self.lib, self.h, self.lib.sph2d_pair_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def pair_list(self):
+        """(off int64 [N+1], tri int32 [P]) on the device, input particle order."""
+        P = self.pair_count()
+        n = self._keep[0].shape[0]
+        off = torch.empty(n + 1, dtype=torch.int64, device=self._dev())
+        tri = torch.empty(max(P, 1), dtype=torch.int32, device=self._dev())
+        req = ctypes.c_int64()
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_pair_list(self.h, _ptr(off), _ptr(tri), P, ctypes.byref(req)))
+        return off, tri[:P]
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(self.lib, self.h, self.lib.sph2d_last_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    # -- forward -----------------------------------------------------------------------
+    def _alloc_out(self, n, moment_degree, mode, want_grad):
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        d = self._dev()
+        g = torch.empty(n, dtype=dt, device=d)
+        gr = torch.empty((n, 2), dtype=dt, device=d) if want_grad else None
+        nm = num_moments(moment_degree)
+        mo = torch.empty((n, nm), dtype=dt, device=d) if nm else None
+        return g, gr, mo
+
+    def boundary_integrals(self, particles, tris, kernel, H: float, moment_degree: int = -1,
+                           mode="fp64", want_grad: bool = True):
+        """Full path: cells, cull, closed-form pair integrals, per-particle sums."""
+        src = particles.device
+        p = as_particles(particles, self._dev())
+        t = as_triangles(tris, self._dev())
+        g, gr, mo = self._alloc_out(p.shape[0], moment_degree, mode, want_grad)
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_boundary_integrals(
+            self.h, _ptr(p), p.shape[0], _ptr(t), t.shape[0], _kernel_id(kernel), float(H),
+            int(moment_degree), _mode_id(mode), _ptr(g), _ptr(gr), _ptr(mo)))
+        self._keep = (p, t)
+        if src.type != "cuda":
+            g = g.to(src)
+            gr = gr.to(src) if gr is not None else None
+            mo = mo.to(src) if mo is not None else None
+        return g, gr, mo
+
+    def integrals_from_pairs(self, kernel, moment_degree: int = -1, mode="fp64", want_grad=True):
+        n = self._keep[0].shape[0]
+        g, gr, mo = self._alloc_out(n, moment_degree, mode, want_grad)
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_integrals_from_pairs(
+            self.h, _kernel_id(kernel), int(moment_degree), _mode_id(mode), _ptr(g), _ptr(gr), _ptr(mo)))
+        return g, gr, mo
+
+    def pair_integrals(self, pairs, kernel, H: float, moment_degree: int = -1, mode="fp64"):
+        """Independent pairs float64 [P, 8] -> [P, 3 + nm] (gamma, grad x, grad y, moments)."""
+        q = pairs.to(device=self._dev(), dtype=torch.float64).contiguous()
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        out = torch.empty((q.shape[0], 3 + num_moments(moment_degree)), dtype=dt, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_pair_integrals(
+            self.h, _ptr(q), q.shape[0], _kernel_id(kernel), float(H), int(moment_degree),
+            _mode_id(mode), _ptr(out)))
+        return out
+
+    # -- adjoint -----------------------------------------------------------------------
+    def backward(self, particles, tris, kernel, H: float, d_gamma, mode="fp64"):
+        """dL/dx [N, 2] and dL/dvertices [M, 6] from dL/dgamma [N]."""
+        p = as_particles(particles, self._dev())
+        t = as_triangles(tris, self._dev())
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        dg = d_gamma.to(device=self._dev(), dtype=dt).contiguous()
+        dp = torch.empty((p.shape[0], 2), dtype=dt, device=self._dev())
+        dtr = torch.empty((t.shape[0], 6), dtype=dt, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_boundary_integrals_backward(
+            self.h, _ptr(p), p.shape[0], _ptr(t), t.shape[0], _kernel_id(kernel), float(H),
+            _mode_id(mode), _ptr(dg), None, _ptr(dp), _ptr(dtr)))
+        return dp, dtr
+
+
+_contexts: dict[int, Context] = {}
+
+
+def context(device: int | None = None) -> Context:
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _contexts:
+        _contexts[d] = Context(d)
+    return _contexts[d]
+
+
+def boundary_integrals(particles, tris, kernel, H: float, moment_degree: int = -1, mode="fp64",
+                       want_grad: bool = True):
+    """gamma [N], grad_gamma [N, 2] (or None), moments [N, nm] (or None)."""
+    return context().boundary_integrals(particles, tris, kernel, H, moment_degree, mode, want_grad)
+
+
+def pair_integrals(pairs, kernel, H: float, moment_degree: int = -1, mode="fp64"):
+    return context().pair_integrals(pairs, kernel, H, moment_degree, mode)
+
+
+class BoundaryGamma(torch.autograd.Function):
+    """gamma(particles, triangles) with the library's adjoint kernel as backward.
+
+    Gradients flow to particle positions (x, y) and triangle vertices.  Only gamma is
+    differentiable here (grad_gamma is returned detached)."""
+
+    @staticmethod
+    def forward(ctx, particles, tris, kernel, H, mode):
+        g, gr, _ = context().boundary_integrals(particles, tris, kernel, H, -1, mode, True)
+        ctx.save_for_backward(particles, tris)
+        ctx.kernel, ctx.H, ctx.mode = kernel, H, mode
+        ctx.mark_non_differentiable(gr)
+        return g, gr
+
+    @staticmethod
+    def backward(ctx, d_gamma, d_grad):
+        particles, tris = ctx.saved_tensors
+        dp, dt = context().backward(particles, tris, ctx.kernel, ctx.H, d_gamma, ctx.mode)
+        gp = torch.zeros_like(particles)
+        gp[:, :2] = dp.to(particles.dtype)
+        return gp, dt.to(tris.dtype).reshape(tris.shape), None, None, None

@@ -1,0 +1,140 @@
+// Algorithmic operation count of the pair formula.  The closed-form pair integrals of
+// pair_math.cuh are instantiated with a scalar type that counts every floating-point
+// operation it performs, so the count is of exactly the formula the CUDA kernels execute
+// (FP64 path: double; FP32 path: float with compensated FF radial sums).  Host code only;
+// the benchmark uses it for the roofline's algorithmic FLOPs per pair.
+//
+// Counting convention: add/sub, mul, div, sqrt and each transcendental call (atan2, log)
+// count 1 flop, fma counts 2; comparisons, min/max, abs and selects count 0 flops (reported
+// separately as "other").
+#include <cmath>
+#include <cstdint>
+
+namespace sph2d {
+struct OpTally {
+  int64_t add = 0, mul = 0, fma = 0, div = 0, sqrt = 0, transc = 0, other = 0;
+};
+static OpTally g_tally;
+
+template <typename T>
+struct Counted {
+  T v;
+  Counted() : v(0) {}
+  Counted(double x) : v(T(x)) {}
+  Counted(float x) : v(T(x)) {}
+  Counted(int x) : v(T(x)) {}
+  explicit operator bool() const { return v != 0; }
+};
+template <typename T> inline Counted<T> mk(T x) { Counted<T> r; r.v = x; return r; }
+#define SPH2D_CBIN(op, field)                                                             \
+  template <typename T> inline Counted<T> operator op(Counted<T> a, Counted<T> b) {         \
+    ++g_tally.field;                                                                      \
+    return mk<T>(a.v op b.v);                                                             \
+  }
+SPH2D_CBIN(+, add)
+SPH2D_CBIN(-, add)
+SPH2D_CBIN(*, mul)
+SPH2D_CBIN(/, div)
+#undef SPH2D_CBIN
+template <typename T> inline Counted<T> operator-(Counted<T> a) { return mk<T>(-a.v); }
+template <typename T> inline Counted<T>& operator+=(Counted<T>& a, Counted<T> b) { a = a + b; return a; }
+#define SPH2D_CCMP(op)                                                                    \
+  template <typename T> inline bool operator op(Counted<T> a, Counted<T> b) {               \
+    ++g_tally.other;                                                                      \
+    return a.v op b.v;                                                                    \
+  }
+SPH2D_CCMP(<)
+SPH2D_CCMP(>)
+SPH2D_CCMP(<=)
+SPH2D_CCMP(>=)
+SPH2D_CCMP(==)
+SPH2D_CCMP(!=)
+#undef SPH2D_CCMP
+template <typename T> inline Counted<T> sqrt(Counted<T> a) { ++g_tally.sqrt; return mk<T>(std::sqrt(a.v)); }
+template <typename T> inline Counted<T> log(Counted<T> a) { ++g_tally.transc; return mk<T>(std::log(a.v)); }
+template <typename T> inline Counted<T> atan2(Counted<T> a, Counted<T> b) {
+  ++g_tally.transc;
+  return mk<T>(std::atan2(a.v, b.v));
+}
+template <typename T> inline Counted<T> fabs(Counted<T> a) { ++g_tally.other; return mk<T>(std::fabs(a.v)); }
+template <typename T> inline Counted<T> fmin(Counted<T> a, Counted<T> b) { ++g_tally.other; return mk<T>(std::fmin(a.v, b.v)); }
+template <typename T> inline Counted<T> fmax(Counted<T> a, Counted<T> b) { ++g_tally.other; return mk<T>(std::fmax(a.v, b.v)); }
+inline Counted<float> fma_f(Counted<float> a, Counted<float> b, Counted<float> c) {
+  ++g_tally.fma;
+  return mk<float>(std::fma(a.v, b.v, c.v));
+}
+inline Counted<float> frexp_f(Counted<float> x, int* e) { return mk<float>(std::frexp(x.v, e)); }
+inline Counted<float> ldexp_f(Counted<float> x, int e) { return mk<float>(std::ldexp(x.v, e)); }
+}  // namespace sph2d
+
+#include "pair_math.cuh"
+
+namespace sph2d {
+// FP32 semantics of diff_of_products and the tiny-distance cut for the counted types
+inline Counted<float> diff_of_products(Counted<float> a, Counted<float> b, Counted<float> c, Counted<float> d) {
+  const Counted<float> w = c * d;
+  const Counted<float> e = fma_f(-c, d, w);
+  const Counted<float> f = fma_f(a, b, -w);
+  return f + e;
+}
+inline Counted<double> diff_of_products(Counted<double> a, Counted<double> b, Counted<double> c, Counted<double> d) {
+  return a * b - c * d;
+}
+template <> struct Tiny<Counted<double>> { static Counted<double> v() { return Counted<double>(1e-150); } };
+template <> struct Tiny<Counted<float>> { static Counted<float> v() { return Counted<float>(1e-18f); } };
+template <> struct Acc<Counted<double>> {
+  using R = Counted<double>;
+  using T = R;
+  static R c(double v) { return R(v); }
+  static R from(R v) { return v; }
+  static R sq(R v) { return v * v; }
+  static R root(R v) { return sqrt(v); }
+  static R out(R v) { return v; }
+  static R mulr(R a, R b) { return a * b; }
+  static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
+};
+template <> struct Acc<Counted<float>> : AccFF<Counted<float>> {};
+
+template <typename R, int KID, bool MOM>
+static void count_one(const double* l) {
+  R v[6];
+  for (int j = 0; j < 6; ++j) v[j] = R(l[j]);
+  PairOut<R> o;
+  (void)tri_orientation<R>(v[0], v[1], v[2], v[3], v[4], v[5]);
+  tri_raw<R, KID, MOM>(v[0], v[1], v[2], v[3], v[4], v[5], o);
+  // constants and orientation applied per output, as in the kernels
+  const R k(1.0);
+  R s = k * o.g;
+  s = k * o.gx;
+  s = k * o.gy;
+  if (MOM)
+    for (int m = 0; m < 10; ++m) s = k * o.m[m];
+  (void)s;
+}
+
+template <typename R>
+static void count_kernel(int kid, bool mom, const double* l) {
+  switch (kid) {
+    case 0: mom ? count_one<R, 0, true>(l) : count_one<R, 0, false>(l); break;
+    case 1: mom ? count_one<R, 1, true>(l) : count_one<R, 1, false>(l); break;
+    case 2: mom ? count_one<R, 2, true>(l) : count_one<R, 2, false>(l); break;
+    default: mom ? count_one<R, 3, true>(l) : count_one<R, 3, false>(l); break;
+  }
+}
+}  // namespace sph2d
+
+extern "C" {
+// Count the operations of one pair (local-frame triangle l[6], H = 1).  out[7] = add, mul,
+// fma, div, sqrt, transcendental, other.  Returns flops (fma = 2).
+int64_t sph2d_count_pair_ops(int kernel, int moments, int fp32, const double* l, int64_t* out) {
+  sph2d::g_tally = sph2d::OpTally{};
+  if (fp32) sph2d::count_kernel<sph2d::Counted<float>>(kernel, moments != 0, l);
+  else sph2d::count_kernel<sph2d::Counted<double>>(kernel, moments != 0, l);
+  const sph2d::OpTally& t = sph2d::g_tally;
+  if (out) {
+    out[0] = t.add; out[1] = t.mul; out[2] = t.fma; out[3] = t.div;
+    out[4] = t.sqrt; out[5] = t.transc; out[6] = t.other;
+  }
+  return t.add + t.mul + 2 * t.fma + t.div + t.sqrt + t.transc;
+}
+}

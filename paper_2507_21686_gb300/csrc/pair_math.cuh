@@ -1,0 +1,521 @@
+// Closed-form integrals of a compact polynomial SPH kernel over one triangle, in the
+// normalised frame of Sec. 2 (particle at the origin, support radius 1).
+//
+// Decomposition.  The paper splits the triangle into sectors, segments and stubs about the
+// particle (Sec. 4, Alg. 1-4) and evaluates each piece in closed form (Sec. 5).  Here the
+// same integral is written as the signed sum of the three "fans" (origin, v_e, v_{e+1}) over
+// the edges -- the signed-area combination of Sec. 4.4, Eq. intermediateWedge, applied to
+// every edge at once -- and each fan is cut where its edge leaves the unit disc:
+//   * sector pieces (edge beyond r = 1): the cone integrals of Sec. 5.2, radius 1;
+//   * the edge piece (r runs to the edge, r <= 1): the segment/stub integrals of
+//     Sec. 5.3-5.4.  In the edge's own frame (normal n at distance d, tangent coordinate t),
+//     r = rho(t) = sqrt(d^2 + t^2), the angle u obeys du = d dt / rho^2 and the angular
+//     factors become algebraic, cos u = d/rho and sin u = t/rho (the role the Chebyshev
+//     identities T_a, U_{a-1} of asin/acos play in Sec. 5.1).  Every radial power then
+//     reduces to the square-root integrals
+//         J_q(t) = int_0^t (d^2 + s^2)^{q/2} ds = t d^q 2F1(-q/2, 1/2; 3/2; -t^2/d^2)
+//     of Sec. 5.1, which satisfy the Gauss contiguous relation
+//         J_q = (t rho^q + q d^2 J_{q-2}) / (q + 1),   J_0 = t,  J_{-1} = asinh(t/d).
+//     On each side of the foot point all terms of the recurrence have one sign, so the
+//     upward recurrence is stable as d -> 0 (the particle approaching the edge line, where
+//     the paper's 2F1 argument approaches 1 and it resorts to an epsilon shift).
+// No branch depends on how many vertices lie inside the support: the paper's case switch
+// (Sec. 4.6) becomes clamping of the tangent coordinates to [-sqrt(1-d^2), sqrt(1-d^2)].
+//
+// Outputs per triangle (raw, without the constant C, the orientation sign or 1/H):
+//   g      = int k(|p|) dA
+//   gx,gy  = int k'(|p|) p/|p| dA
+//   m[10]  = int p_x^a p_y^b k(|p|) dA   in the order 00 10 01 20 11 02 30 21 12 03
+#pragma once
+
+#include <math.h>
+
+#if defined(__CUDACC__)
+#define SPH2D_HD __host__ __device__ __forceinline__
+#else
+#define SPH2D_HD inline
+#include <cmath>
+#endif
+
+namespace sph2d {
+
+#if !defined(__CUDA_ARCH__)
+using std::atan2;
+using std::fabs;
+using std::fmax;
+using std::fmin;
+using std::log;
+using std::sqrt;
+#endif
+
+enum : int { KID_WC2 = 0, KID_WC4 = 1, KID_WC6 = 2, KID_CUBIC = 3 };
+
+// ---------------------------------------------------------------------------------------
+// kernel polynomials k(q) = sum_k b_k q^k (Sec. 2: integer powers of q); the cubic spline is
+// split into compact pieces 2 (1-q)^3_+ - (1-2q)^3_+ so every piece is one polynomial on
+// its own support (Sec. 2, piecewise kernels "by careful evaluation of the bounds").
+// ---------------------------------------------------------------------------------------
+struct PolyWC2 {
+  static constexpr int K = 5;
+  SPH2D_HD static constexpr double b(int k) {
+    return k == 0 ? 1.0 : k == 2 ? -10.0 : k == 3 ? 20.0 : k == 4 ? -15.0 : k == 5 ? 4.0 : 0.0;
+  }
+};
+struct PolyWC4 {
+  static constexpr int K = 8;
+  SPH2D_HD static constexpr double b(int k) {
+    return k == 0 ? 1.0 : k == 2 ? -28.0 / 3.0 : k == 4 ? 70.0 : k == 5 ? -448.0 / 3.0
+         : k == 6 ? 140.0 : k == 7 ? -64.0 : k == 8 ? 35.0 / 3.0 : 0.0;
+  }
+};
+struct PolyWC6 {
+  static constexpr int K = 11;
+  SPH2D_HD static constexpr double b(int k) {
+    return k == 0 ? 1.0 : k == 2 ? -11.0 : k == 4 ? 66.0 : k == 6 ? -462.0 : k == 7 ? 1056.0
+         : k == 8 ? -1155.0 : k == 9 ? 704.0 : k == 10 ? -231.0 : k == 11 ? 32.0 : 0.0;
+  }
+};
+struct PolyCube {  // (1-q)^3
+  static constexpr int K = 3;
+  SPH2D_HD static constexpr double b(int k) {
+    return k == 0 ? 1.0 : k == 1 ? -3.0 : k == 2 ? 3.0 : k == 3 ? -1.0 : 0.0;
+  }
+};
+
+// sum_k b_k / (k + n)
+template <class P>
+SPH2D_HD constexpr double kappa(int n) {
+  double s = 0.0;
+  for (int k = 0; k <= P::K; ++k) s += P::b(k) / double(k + n);
+  return s;
+}
+// sum_k k b_k / (k + 1)   (int_0^1 k'(r) r dr)
+template <class P>
+SPH2D_HD constexpr double kappa_grad() {
+  double s = 0.0;
+  for (int k = 1; k <= P::K; ++k) s += double(k) * P::b(k) / double(k + 1);
+  return s;
+}
+
+// 2-D normalisation constants C (int W = 1)
+SPH2D_HD constexpr double kernel_C(int kid) {
+  return kid == KID_WC2 ? 7.0 / 3.14159265358979323846
+       : kid == KID_WC4 ? 9.0 / 3.14159265358979323846
+       : kid == KID_WC6 ? 78.0 / (7.0 * 3.14159265358979323846)
+                        : 40.0 / (7.0 * 3.14159265358979323846);
+}
+
+template <typename R>
+struct PairOut {
+  R g, gx, gy;
+  R m[10];
+};
+
+template <typename R>
+SPH2D_HD void clear(PairOut<R>& o) {
+  o.g = o.gx = o.gy = R(0);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) o.m[i] = R(0);
+}
+
+template <typename R> struct Tiny;
+template <> struct Tiny<double> { SPH2D_HD static constexpr double v() { return 1e-150; } };
+template <> struct Tiny<float> { SPH2D_HD static constexpr float v() { return 1e-18f; } };
+
+// a*b - c*d.  In FP32 Kahan's compensated form (error <= 1.5 ulp of the result), so that a
+// cross product of nearly parallel vectors keeps its relative accuracy.
+SPH2D_HD double diff_of_products(double a, double b, double c, double d) { return a * b - c * d; }
+SPH2D_HD float diff_of_products(float a, float b, float c, float d) {
+#if defined(__CUDA_ARCH__)
+  float w = c * d;
+  float e = __fmaf_rn(-c, d, w);
+  float f = __fmaf_rn(a, b, -w);
+  return f + e;
+#else
+  float w = c * d;
+  float e = std::fma(-c, d, w);
+  float f = std::fma(a, b, -w);
+  return f + e;
+#endif
+}
+
+// asinh(t2/d) - asinh(t1/d), with rho_i = sqrt(d^2 + t_i^2) given and |t| + rho >= d
+// formed without cancellation (asinh(t/d) = sgn(t) log((|t| + rho)/d)).
+template <typename R>
+SPH2D_HD R asinh_diff(R t1, R t2, R r1, R r2, R d) {
+  const R a1 = fabs(t1) + r1, a2 = fabs(t2) + r2;
+  const bool p1 = t1 >= R(0), p2 = t2 >= R(0);
+  if (p1 == p2) {
+    const R l = log(a2 / a1);
+    return p2 ? l : -l;
+  }
+  const R l = log((a1 / d) * (a2 / d));
+  return p2 ? l : -l;
+}
+
+// ---------------------------------------------------------------------------------------
+// compensated FP32 ("float-float"): value = hi + lo with |lo| <= ulp(hi)/2, built from FMA
+// error-free transformations.  Used for the radial recurrence and the kernel-coefficient
+// sums of the FP32 path, whose alternating coefficients (sum |b_k|/(k+2) is 140x to 9000x
+// the result for C2..C6) would otherwise amplify FP32 rounding by the same factor.
+// ---------------------------------------------------------------------------------------
+template <typename F>
+struct FFT {
+  F hi, lo;
+};
+using FF = FFT<float>;
+SPH2D_HD float fma_f(float a, float b, float c) {
+#if defined(__CUDA_ARCH__)
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+SPH2D_HD constexpr FF ff_const(double c) {
+  return FF{float(c), float(c - double(float(c)))};
+}
+template <typename F>
+SPH2D_HD FFT<F> ff_two_sum(F a, F b) {
+  const F s = a + b;
+  const F bb = s - a;
+  return FFT<F>{s, (a - (s - bb)) + (b - bb)};
+}
+template <typename F>
+SPH2D_HD FFT<F> ff_fast_two_sum(F a, F b) {
+  const F s = a + b;
+  return FFT<F>{s, b - (s - a)};
+}
+template <typename F>
+SPH2D_HD FFT<F> ff_two_prod(F a, F b) {
+  const F p = a * b;
+  return FFT<F>{p, fma_f(a, b, -p)};
+}
+// error <= eps^2 (|a| + |b|): adequate where cancellation is between large terms
+template <typename F>
+SPH2D_HD FFT<F> operator+(FFT<F> a, FFT<F> b) {
+  const FFT<F> s = ff_two_sum(a.hi, b.hi);
+  return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+template <typename F>
+SPH2D_HD FFT<F> operator-(FFT<F> a) { return FFT<F>{-a.hi, -a.lo}; }
+template <typename F>
+SPH2D_HD FFT<F> operator-(FFT<F> a, FFT<F> b) { return a + (-b); }
+template <typename F>
+SPH2D_HD FFT<F> operator*(FFT<F> a, FFT<F> b) {
+  const FFT<F> p = ff_two_prod(a.hi, b.hi);
+  return ff_fast_two_sum(p.hi, fma_f(a.hi, b.lo, fma_f(a.lo, b.hi, p.lo)));
+}
+template <typename F>
+SPH2D_HD FFT<F> operator*(FFT<F> a, F b) {
+  const FFT<F> p = ff_two_prod(a.hi, b);
+  return ff_fast_two_sum(p.hi, fma_f(a.lo, b, p.lo));
+}
+template <typename F>
+SPH2D_HD FFT<F> ff_sqrt(FFT<F> x) {               // one Newton step on sqrt(hi)
+  if (x.hi <= F(0)) return FFT<F>{F(0), F(0)};
+  const F r = sqrt(x.hi);
+  const FFT<F> r2 = ff_two_prod(r, r);
+  const F res = ((x.hi - r2.hi) - r2.lo) + x.lo;
+  return ff_fast_two_sum(r, res / (F(2) * r));
+}
+template <typename F>
+SPH2D_HD F to_f(FFT<F> a) { return a.hi + a.lo; }
+template <typename F>
+SPH2D_HD FFT<F> operator/(FFT<F> a, FFT<F> b) {   // long division, two quotient digits
+  const F q1 = a.hi / b.hi;
+  const FFT<F> r = a - b * q1;
+  const F q2 = r.hi / b.hi;
+  return ff_fast_two_sum(q1, q2);
+}
+template <typename F>
+SPH2D_HD FFT<F> ffc(double c) {
+  const FF v = ff_const(c);
+  return FFT<F>{F(v.hi), F(v.lo)};
+}
+SPH2D_HD float frexp_f(float x, int* e) {
+#if defined(__CUDA_ARCH__)
+  return frexpf(x, e);
+#else
+  return std::frexp(x, e);
+#endif
+}
+SPH2D_HD float ldexp_f(float x, int e) {
+#if defined(__CUDA_ARCH__)
+  return ldexpf(x, e);
+#else
+  return std::ldexp(x, e);
+#endif
+}
+// natural log of x > 0 to ~2^-44 relative: x = m 2^e with m in [1/sqrt2, sqrt2),
+// log m = 2 atanh(z), z = (m-1)/(m+1), |z| <= 0.1716, series through z^19 (Horner, FF).
+template <typename F>
+SPH2D_HD FFT<F> ff_log(FFT<F> x) {
+  int e = 0;
+  const F m = frexp_f(x.hi, &e);
+  if (m < F(0.70710678f)) e -= 1;
+  const FFT<F> xm{ldexp_f(x.hi, -e), ldexp_f(x.lo, -e)};
+  const FFT<F> one{F(1), F(0)};
+  const FFT<F> z = (xm - one) / (xm + one);
+  const FFT<F> z2 = z * z;
+  FFT<F> sum = ffc<F>(1.0 / 19.0);
+#pragma unroll
+  for (int k = 17; k >= 1; k -= 2) sum = sum * z2 + ffc<F>(1.0 / double(k));
+  const FFT<F> lz = (z * sum) * F(2);
+  return lz + ffc<F>(0.69314718055994530942) * F(float(e));
+}
+// asinh(t2/d) - asinh(t1/d) in FF (see asinh_diff)
+template <typename F>
+SPH2D_HD FFT<F> asinh_diff_ff(F t1, F t2, FFT<F> r1, FFT<F> r2, F d) {
+  const FFT<F> a1 = r1 + FFT<F>{fabs(t1), F(0)}, a2 = r2 + FFT<F>{fabs(t2), F(0)};
+  const bool p1 = t1 >= F(0), p2 = t2 >= F(0);
+  FFT<F> l;
+  if (p1 == p2) {
+    l = ff_log(a2 / a1);
+  } else {
+    const FFT<F> dd{d, F(0)};
+    l = ff_log((a1 / dd) * (a2 / dd));
+  }
+  return p2 ? l : -l;
+}
+
+// accumulation type of the radial part: double for the FP64 path, FF for the FP32 path
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+  using T = double;
+  SPH2D_HD static constexpr double c(double v) { return v; }
+  SPH2D_HD static double from(double v) { return v; }
+  SPH2D_HD static double sq(double v) { return v * v; }
+  SPH2D_HD static double root(double v) { return sqrt(v); }
+  SPH2D_HD static double out(double v) { return v; }
+  SPH2D_HD static double mulr(double a, double b) { return a * b; }
+  SPH2D_HD static double jm1(double t1, double t2, double r1, double r2, double d, double ra,
+                             double rb) {
+    (void)ra; (void)rb;
+    return asinh_diff(t1, t2, r1, r2, d);
+  }
+};
+// FP32 (or an FP32-like scalar F): compensated accumulation
+template <typename F>
+struct AccFF {
+  using T = FFT<F>;
+  SPH2D_HD static FFT<F> c(double v) { return ffc<F>(v); }
+  SPH2D_HD static FFT<F> from(F v) { return FFT<F>{v, F(0)}; }
+  SPH2D_HD static FFT<F> sq(F v) { return ff_two_prod(v, v); }
+  SPH2D_HD static FFT<F> root(FFT<F> v) { return ff_sqrt(v); }
+  SPH2D_HD static F out(FFT<F> v) { return to_f(v); }
+  SPH2D_HD static FFT<F> mulr(FFT<F> a, F b) { return a * b; }
+  SPH2D_HD static FFT<F> jm1(F t1, F t2, F r1, F r2, F d, FFT<F> ra, FFT<F> rb) {
+    (void)r1; (void)r2;
+    return asinh_diff_ff(t1, t2, ra, rb, d);
+  }
+};
+template <> struct Acc<float> : AccFF<float> {};
+
+// ---------------------------------------------------------------------------------------
+// one edge (fan (0, A, B)) of a triangle for the polynomial kernel P; accumulates the
+// signed fan integrals into o (global frame, raw)
+// ---------------------------------------------------------------------------------------
+template <typename R, class P, bool MOM>
+SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
+  const R ex = bx - ax, ey = by - ay;
+  const R l2 = ex * ex + ey * ey;
+  const R c = diff_of_products(ax, by, ay, bx);          // A x B = |A||B| sin(fan angle)
+  if (l2 == R(0) || c == R(0)) return;                   // degenerate fan: zero area
+  const R il = R(1) / sqrt(l2);
+  const R d = fabs(c) * il;                              // distance of the edge line
+  if (d < Tiny<R>::v()) return;                          // contribution O(d log d)
+  const R sg = c > R(0) ? R(1) : R(-1);
+  const R nx = sg * ey * il, ny = -sg * ex * il;         // unit normal towards the line
+  // tangent e2 = (-ny, nx); t = p . e2 (increasing with the polar angle)
+  const R tA = ay * nx - ax * ny;
+  const R tB = by * nx - bx * ny;
+  const R dth = atan2(c, ax * bx + ay * by);             // signed fan angle u_B - u_A
+  const R ts = d < R(1) ? sqrt((R(1) - d) * (R(1) + d)) : R(0);
+  const R t1 = fmin(fmax(tA, -ts), ts);
+  const R t2 = fmin(fmax(tB, -ts), ts);
+  const R d2 = d * d;
+  const R r1 = sqrt(d2 + t1 * t1), r2 = sqrt(d2 + t2 * t2);
+  const R rA = sqrt(d2 + tA * tA), rB = sqrt(d2 + tB * tB);
+  const R due = atan2(d * (t2 - t1), d2 + t1 * t2);      // edge-piece angle u_2 - u_1
+  const R dus = dth - due;                               // sector pieces, total angle
+  // (cos u, sin u) at u_A, u_1, u_2, u_B
+  const R iA = R(1) / rA, iB = R(1) / rB, i1 = R(1) / r1, i2 = R(1) / r2;
+  const R cA = d * iA, sA = tA * iA, cB = d * iB, sB = tB * iB;
+  const R c1 = d * i1, s1 = t1 * i1, c2 = d * i2, s2 = t2 * i2;
+
+  // ---- sector pieces: radius 1, angular antiderivatives over [u_A,u_1] and [u_2,u_B]
+  // [F] := F(u_1) - F(u_A) + F(u_B) - F(u_2)
+#define SPH2D_BR(F1, FA, F2, FB) (((F1) - (FA)) + ((FB) - (F2)))
+  const R I_c = SPH2D_BR(s1, sA, s2, sB);                // int cos u
+  const R I_s = SPH2D_BR(cA, c1, cB, c2);                // int sin u = [-cos u]
+  constexpr double k2 = kappa<P>(2);
+  constexpr double kg = kappa_grad<P>();
+  R eg = R(k2) * dus;                                    // gamma (edge frame = any frame)
+  R en = R(kg) * I_c;                                    // gradient along n
+  R et = R(kg) * I_s;                                    // gradient along e2
+  R E[10];                                               // edge-frame moments s^j t^l
+  if (MOM) {
+    constexpr double k3 = kappa<P>(3), k4 = kappa<P>(4), k5 = kappa<P>(5);
+    const R scA = sA * cA, sc1 = s1 * c1, sc2 = s2 * c2, scB = sB * cB;
+    const R I_sc = SPH2D_BR(sc1, scA, sc2, scB);         // [s c]
+    const R I_ss = SPH2D_BR(s1 * s1, sA * sA, s2 * s2, sB * sB);
+    const R I_s3 = SPH2D_BR(s1 * s1 * s1, sA * sA * sA, s2 * s2 * s2, sB * sB * sB);
+    const R I_c3 = SPH2D_BR(c1 * c1 * c1, cA * cA * cA, c2 * c2 * c2, cB * cB * cB);
+    E[0] = eg;
+    E[1] = R(k3) * I_c;                                  // s
+    E[2] = R(k3) * I_s;                                  // t
+    E[3] = R(k4) * R(0.5) * (dus + I_sc);                // s^2 : int cos^2
+    E[4] = R(k4) * R(0.5) * I_ss;                        // s t : int sin cos = [sin^2/2]
+    E[5] = R(k4) * R(0.5) * (dus - I_sc);                // t^2 : int sin^2
+    E[6] = R(k5) * (I_c - I_s3 / R(3));                  // s^3 : int cos^3 = [s - s^3/3]
+    E[7] = R(k5) * (-I_c3 / R(3));                       // s^2 t: int cos^2 sin = [-c^3/3]
+    E[8] = R(k5) * (I_s3 / R(3));                        // s t^2: int cos sin^2 = [s^3/3]
+    E[9] = R(k5) * (I_s + I_c3 / R(3));                  // t^3 : int sin^3 = [-c + c^3/3]
+  }
+#undef SPH2D_BR
+
+  // ---- edge piece: t in [t1, t2], r = rho(t) <= 1, in the accumulation type A
+  using AC = Acc<R>;
+  using A = typename AC::T;
+  const A d2a = AC::sq(d);
+  const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
+  // running sums without their d^(j+1) factors
+  A Sg = AC::c(0), Sn = AC::c(0), St = AC::c(0);
+  A S10 = AC::c(0), S01 = AC::c(0), S20 = AC::c(0), S11 = AC::c(0), S02 = AC::c(0);
+  A S30 = AC::c(0), S21 = AC::c(0), S12 = AC::c(0), S03 = AC::c(0);
+  const A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);      // Delta J_{-1}
+  const A dJp = AC::from(t2) - AC::from(t1);              // Delta J_0
+  {
+    Sg = Sg + dJp * AC::c(P::b(0) / 2.0);
+    if (P::b(2) != 0.0) Sn = Sn + dJp * AC::c(2.0 * P::b(2) / 3.0);  // k = 2 normal term
+    if (MOM) {
+      S10 = S10 + dJp * AC::c(P::b(0) / 3.0);
+      S20 = S20 + dJp * AC::c(P::b(0) / 4.0);
+      S30 = S30 + dJp * AC::c(P::b(0) / 5.0);
+      S02 = S02 + dJp * d2a * AC::c(-P::b(0) / 4.0);
+      S12 = S12 + dJp * d2a * AC::c(-P::b(0) / 5.0);
+    }
+  }
+  if (P::b(1) != 0.0) Sn = Sn + dJm * AC::c(P::b(1) / 2.0);  // k = 1 normal term: J_{-1}
+  A p1 = AC::c(1), p2 = AC::c(1);                            // rho^q at the two ends
+  A dJq2 = dJm, dJq1 = dJp;                                  // Delta J_{q-2}, Delta J_{q-1}
+  constexpr int QMAX = MOM ? P::K + 4 : P::K;
+#pragma unroll
+  for (int q = 1; q <= QMAX; ++q) {
+    p1 = p1 * r1a;
+    p2 = p2 * r2a;
+    const A dP = p2 - p1;                                    // Delta rho^q
+    const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);        // Delta (t rho^q)
+    const A dJ = (dT + dJq2 * d2a * AC::c(double(q))) * AC::c(1.0 / double(q + 1));
+    if (q <= P::K && P::b(q) != 0.0) Sg = Sg + dJ * AC::c(P::b(q) / double(q + 2));
+    if (q + 2 <= P::K && P::b(q + 2) != 0.0)
+      Sn = Sn + dJ * AC::c(double(q + 2) * P::b(q + 2) / double(q + 3));
+    if (q <= P::K && P::b(q) != 0.0) St = St + dP * AC::c(P::b(q) / double(q + 1));
+    if (MOM) {
+      if (q <= P::K && P::b(q) != 0.0) {
+        S10 = S10 + dJ * AC::c(P::b(q) / double(q + 3));
+        S20 = S20 + dJ * AC::c(P::b(q) / double(q + 4));
+        S30 = S30 + dJ * AC::c(P::b(q) / double(q + 5));
+        S02 = S02 + dJ * d2a * AC::c(-P::b(q) / double(q + 4));
+        S12 = S12 + dJ * d2a * AC::c(-P::b(q) / double(q + 5));
+      }
+      if (q >= 2 && q - 2 <= P::K && P::b(q - 2) != 0.0) {
+        S02 = S02 + dJ * AC::c(P::b(q - 2) / double(q + 2));
+        S12 = S12 + dJ * AC::c(P::b(q - 2) / double(q + 3));
+        S01 = S01 + dP * AC::c(P::b(q - 2) / (double(q + 1) * double(q)));
+        S11 = S11 + dP * AC::c(P::b(q - 2) / (double(q + 2) * double(q)));
+        S21 = S21 + dP * AC::c(P::b(q - 2) / (double(q + 3) * double(q)));
+        S03 = S03 + dP * d2a * AC::c(-P::b(q - 2) / (double(q + 3) * double(q)));
+      }
+      if (q >= 4 && q - 4 <= P::K && P::b(q - 4) != 0.0)
+        S03 = S03 + dP * AC::c(P::b(q - 4) / (double(q + 1) * double(q)));
+    }
+    dJq2 = dJq1;
+    dJq1 = dJ;
+  }
+  eg += d * AC::out(Sg);
+  en += d2 * AC::out(Sn);
+  et += d * AC::out(St);
+  // rotate the gradient back from the edge frame (Sec. 2, Eq. improper)
+  o.g += eg;
+  o.gx += en * nx - et * ny;
+  o.gy += en * ny + et * nx;
+  if (MOM) {
+    const R d3 = d2 * d, d4 = d2 * d2;
+    E[1] += d2 * AC::out(S10);
+    E[2] += d * AC::out(S01);
+    E[3] += d3 * AC::out(S20);
+    E[4] += d2 * AC::out(S11);
+    E[5] += d * AC::out(S02);
+    E[6] += d4 * AC::out(S30);
+    E[7] += d3 * AC::out(S21);
+    E[8] += d2 * AC::out(S12);
+    E[9] += d * AC::out(S03);
+    // p_x = s nx - t ny, p_y = s ny + t nx: expand p_x^a p_y^b into s^j t^l
+    const R X = nx, Y = ny;
+    o.m[0] += eg;
+    o.m[1] += X * E[1] - Y * E[2];
+    o.m[2] += Y * E[1] + X * E[2];
+    const R XX = X * X, YY = Y * Y, XY = X * Y;
+    o.m[3] += XX * E[3] - R(2) * XY * E[4] + YY * E[5];
+    o.m[4] += XY * E[3] + (XX - YY) * E[4] - XY * E[5];
+    o.m[5] += YY * E[3] + R(2) * XY * E[4] + XX * E[5];
+    // cubic: (X s - Y t)^a (Y s + X t)^b
+    o.m[6] += XX * X * E[6] - R(3) * XX * Y * E[7] + R(3) * X * YY * E[8] - YY * Y * E[9];
+    o.m[7] += XX * Y * E[6] + (XX * X - R(2) * X * YY) * E[7] + (YY * Y - R(2) * XX * Y) * E[8]
+            + X * YY * E[9];
+    o.m[8] += X * YY * E[6] + (R(2) * XX * Y - YY * Y) * E[7] + (XX * X - R(2) * X * YY) * E[8]
+            - XX * Y * E[9];
+    o.m[9] += YY * Y * E[6] + R(3) * X * YY * E[7] + R(3) * XX * Y * E[8] + XX * X * E[9];
+  }
+}
+
+// signed sum over the three fans of one local-frame triangle, single polynomial piece
+template <typename R, class P, bool MOM>
+SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
+  add_fan<R, P, MOM>(ax, ay, bx, by, o);
+  add_fan<R, P, MOM>(bx, by, cx, cy, o);
+  add_fan<R, P, MOM>(cx, cy, ax, ay, o);
+}
+
+// raw integrals of kernel KID over the local-frame triangle, in input orientation
+// (multiply by the orientation sign for the unsigned integral)
+template <typename R, int KID, bool MOM>
+SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
+  clear(o);
+  if (KID == KID_WC2) tri_poly<R, PolyWC2, MOM>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MOM>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MOM>(ax, ay, bx, by, cx, cy, o);
+  else {
+    // k(q) = 2 k1(q) - k1(2q), k1 = (1-q)^3_+.  With p' = 2p:
+    //   int f(p) k1(2|p|) dA = 1/4 int f(p'/2) k1(|p'|) dA',  f = p^m -> 2^-m
+    //   int k1'(2|p|) p/|p| dA = 1/4 int k1'(|p'|) p'/|p'| dA'   and k'(q) = 2k1'(q) - 2k1'(2q)
+    PairOut<R> h;
+    clear(h);
+    tri_poly<R, PolyCube, MOM>(ax, ay, bx, by, cx, cy, o);
+    tri_poly<R, PolyCube, MOM>(R(2) * ax, R(2) * ay, R(2) * bx, R(2) * by, R(2) * cx,
+                               R(2) * cy, h);
+    o.g = R(2) * o.g - R(0.25) * h.g;
+    o.gx = R(2) * o.gx - R(0.5) * h.gx;
+    o.gy = R(2) * o.gy - R(0.5) * h.gy;
+    if (MOM) {
+      // 2^-(m+2) for the degree m of each moment
+      o.m[0] = R(2) * o.m[0] - R(0.25) * h.m[0];
+#pragma unroll
+      for (int i = 1; i < 3; ++i) o.m[i] = R(2) * o.m[i] - R(0.125) * h.m[i];
+#pragma unroll
+      for (int i = 3; i < 6; ++i) o.m[i] = R(2) * o.m[i] - R(0.0625) * h.m[i];
+#pragma unroll
+      for (int i = 6; i < 10; ++i) o.m[i] = R(2) * o.m[i] - R(0.03125) * h.m[i];
+    }
+  }
+}
+
+// orientation sign of a local-frame triangle (0 for zero area)
+template <typename R>
+SPH2D_HD int tri_orientation(R ax, R ay, R bx, R by, R cx, R cy) {
+  const R a2 = diff_of_products(bx - ax, cy - ay, by - ay, cx - ax);
+  return a2 > R(0) ? 1 : (a2 < R(0) ? -1 : 0);
+}
+
+}  // namespace sph2d

@@ -1,0 +1,83 @@
+// Internal declarations shared by the translation units of libsph2d.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sph2d.h"
+
+namespace sph2d {
+
+// grows on demand; never shrinks until the context is destroyed
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// culling grid + pair list of the last build
+struct Cells {
+  bool built = false;
+  const float* particles = nullptr;
+  const float* tris = nullptr;
+  int64_t N = 0, M = 0;
+  double H = 0.0;
+  // grid
+  double x0 = 0.0, y0 = 0.0, cs = 1.0;
+  int nx = 0, ny = 0;
+  int64_t n_cells = 0, n_incid = 0;
+  // pair list
+  int64_t P = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  sph2d_stats stats{};
+  Cells cells;
+  // scratch buffers (named slots)
+  DevBuf cell_start, cell_cursor, cell_tris, block_tmp, scan_tmp, pair_off, pair_tri, pair_pid,
+      counts, slots, host_flags_dev, misc;
+  int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
+  bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
+  int64_t launches = 0;        // kernels launched by this context (cumulative)
+};
+
+// error helpers ------------------------------------------------------------------------
+sph2d_status set_err(Ctx* c, sph2d_status s, const std::string& msg);
+sph2d_status cuda_err(Ctx* c, cudaError_t e, const char* where);
+sph2d_status ensure(Ctx* c, DevBuf& b, size_t bytes);
+
+// device-wide exclusive scan of int64 [n] -> out [n+1] (out[n] = total), on c->stream
+sph2d_status exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n);
+
+// culling (cells.cu): builds c->cells and the pair list buffers pair_off/pair_tri/pair_pid
+sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float* tris,
+                         int64_t M, double H);
+
+// forward integrals over the context's pair list (integrals.cu)
+sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, void* gamma,
+                              void* grad, void* moments);
+
+// independent pairs (integrals.cu)
+sph2d_status launch_pair_integrals(Ctx* c, const double* pairs, int64_t P, int kernel, double H,
+                                   int moment_degree, int mode, void* out);
+
+// adjoint (backward.cu)
+sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma,
+                             void* d_particles, void* d_tris);
+
+inline int num_moments(int deg) { return deg < 0 ? 0 : (deg + 1) * (deg + 2) / 2; }
+
+constexpr int kBlock = 256;
+
+// every kernel launch of the library goes through this, so the context can report a count
+#define SPH2D_LAUNCH(ctx, kern, grid, block, ...)                          \
+  do {                                                                     \
+    (kern)<<<(grid), (block), 0, (ctx)->stream>>>(__VA_ARGS__);          \
+    ++(ctx)->launches;                                                     \
+  } while (0)
+
+}  // namespace sph2d
