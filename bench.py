@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling runs: timed FP32 path only (no FP64 leg, e2e, CPU baseline, L2 flush)")
     return ap.parse_args()
 
 
@@ -236,7 +238,7 @@ def run_ours(args):
         return outs
 
     # L2 is 129 MB and the inputs are ~21 MB: flush it between timed steps
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    flush = torch.empty(16 if args.quick else 512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def timed(mode, steps, warmup, sample_clocks=False, per_kernel=False):
         for _ in range(warmup):
@@ -301,6 +303,13 @@ def run_ours(args):
     dom_k = KERNELS[dom]
     achieved_tflops = flops32[dom_k] * P / (kmeans[dom] / 1e3) / 1e12
     peak = PM.fp32_peak_tflops()
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": ms_step, "per_kernel_ms": dict(zip(KERNELS, kmeans)),
+                              "cull_ms": cull_ms, "pairs": P, "gpu_launches": launches,
+                              "achieved_tflops": achieved_tflops, "frac": achieved_tflops / peak}), flush=True)
+        return
 
     # ---- plain FP64 GPU path, same workload
     ms64, kms64, _, _ = timed("fp64", max(1, args.fp64_steps), 1, per_kernel=True)

@@ -45,7 +45,9 @@
  *       wx = px-x_e, wy = py-y_e, cr = wx*ey - wy*ex, l2 = ex*ex + ey*ey, tn = wx*ex + wy*ey,
  *       d2 = (tn <= 0) ? wx*wx + wy*wy
  *          : (tn >= l2) ? (px-x_{e+1})^2 + (py-y_{e+1})^2 : cr*cr / l2
- *   keep = (no cr > 0 or no cr < 0)  ||  min_e d2 < H*H
+ *   keep = (some cr != 0 and (no cr > 0 or no cr < 0))  ||  min_e d2 < H*H
+ * (the first clause is "inside"; a zero-area triangle is a segment, and a particle on its
+ * line, where every cr is 0, is decided by the distance alone).
  * Pair lists are particle-major in input particle order, ascending triangle id within a
  * particle.
  */

@@ -533,7 +533,9 @@ static int cull_keep(double px, double py, const float* tf, double H2) {
     }
     if (d2 < best) best = d2;
   }
-  if (npos == 0 || nneg == 0) return 1;           /* inside or on the boundary: distance 0 */
+  /* inside or on the boundary: distance 0.  With every cross product 0 the particle lies on
+   * the line of a zero-area triangle (a segment), whose distance decides. */
+  if ((npos + nneg > 0) && (npos == 0 || nneg == 0)) return 1;
   return best < H2;
 }
 

@@ -225,7 +225,7 @@ __device__ __noinline__ bool keep_exact(double px, double py, const float* __res
     }
     if (d2 < best) best = d2;
   }
-  if (npos == 0 || nneg == 0) return true;
+  if ((npos + nneg > 0) && (npos == 0 || nneg == 0)) return true;   // inside (not collinear)
   return best < H2;
 }
 

@@ -63,6 +63,12 @@ inline Counted<float> fma_f(Counted<float> a, Counted<float> b, Counted<float> c
   ++g_tally.fma;
   return mk<float>(std::fma(a.v, b.v, c.v));
 }
+inline Counted<double> fma_f(Counted<double> a, Counted<double> b, Counted<double> c) {
+  ++g_tally.fma;
+  return mk<double>(std::fma(a.v, b.v, c.v));
+}
+inline Counted<double> frexp_f(Counted<double> x, int* e) { return mk<double>(std::frexp(x.v, e)); }
+inline Counted<double> ldexp_f(Counted<double> x, int e) { return mk<double>(std::ldexp(x.v, e)); }
 inline Counted<float> frexp_f(Counted<float> x, int* e) { return mk<float>(std::frexp(x.v, e)); }
 inline Counted<float> ldexp_f(Counted<float> x, int e) { return mk<float>(std::ldexp(x.v, e)); }
 }  // namespace sph2d
@@ -86,6 +92,7 @@ template <> struct Acc<Counted<double>> {
   using R = Counted<double>;
   using T = R;
   static R c(double v) { return R(v); }
+  static R c2(double num, double den) { return R(num / den); }
   static R from(R v) { return v; }
   static R sq(R v) { return v * v; }
   static R root(R v) { return sqrt(v); }
@@ -94,6 +101,7 @@ template <> struct Acc<Counted<double>> {
   static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
 };
 template <> struct Acc<Counted<float>> : AccFF<Counted<float>> {};
+template <> struct AccSel<Counted<double>, PolyWC6> { using type = AccDD<Counted<double>>; };
 
 template <typename R, int KID, bool MOM>
 static void count_one(const double* l) {

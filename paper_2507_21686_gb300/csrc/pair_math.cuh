@@ -171,6 +171,22 @@ SPH2D_HD float fma_f(float a, float b, float c) {
   return std::fma(a, b, c);
 #endif
 }
+SPH2D_HD double fma_f(double a, double b, double c) {
+#if defined(__CUDA_ARCH__)
+  return __fma_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+// num/den as a double-double, for small integer den: hi = num/den rounded, lo = the exact
+// residual (num - hi*den)/den, with hi*den formed exactly from a Dekker split of hi
+SPH2D_HD constexpr FFT<double> dd_rational(double num, double den) {
+  const double hi = num / den;
+  const double cs = 134217729.0 * hi;
+  const double h1 = cs - (cs - hi), h2 = hi - h1;
+  const double r = (num - h1 * den) - h2 * den;
+  return FFT<double>{hi, r / den};
+}
 SPH2D_HD constexpr FF ff_const(double c) {
   return FF{float(c), float(c - double(float(c)))};
 }
@@ -232,6 +248,24 @@ SPH2D_HD FFT<F> ffc(double c) {
   const FF v = ff_const(c);
   return FFT<F>{F(v.hi), F(v.lo)};
 }
+// num/den as a compensated constant of the base precision B (float pair or double pair)
+template <typename F, typename B>
+SPH2D_HD FFT<F> ffk(double num, double den) {
+  if (sizeof(B) == sizeof(double)) {
+    const FFT<double> v = dd_rational(num, den);
+    return FFT<F>{F(v.hi), F(v.lo)};
+  }
+  const FF v = ff_const(num / den);
+  return FFT<F>{F(v.hi), F(v.lo)};
+}
+// ln 2 to ~2^-106: 0.6931471805599453094172321214581766 = hi + lo
+template <typename F, typename B>
+SPH2D_HD FFT<F> ffln2() {
+  if (sizeof(B) == sizeof(double))
+    return FFT<F>{F(0.6931471805599453094), F(2.3190468138462996e-17)};
+  const FF v = ff_const(0.69314718055994530942);
+  return FFT<F>{F(v.hi), F(v.lo)};
+}
 SPH2D_HD float frexp_f(float x, int* e) {
 #if defined(__CUDA_ARCH__)
   return frexpf(x, e);
@@ -239,6 +273,24 @@ SPH2D_HD float frexp_f(float x, int* e) {
   return std::frexp(x, e);
 #endif
 }
+SPH2D_HD double frexp_f(double x, int* e) {
+#if defined(__CUDA_ARCH__)
+  return frexp(x, e);
+#else
+  return std::frexp(x, e);
+#endif
+}
+SPH2D_HD double ldexp_f(double x, int e) {
+#if defined(__CUDA_ARCH__)
+  return ldexp(x, e);
+#else
+  return std::ldexp(x, e);
+#endif
+}
+// highest odd power of the atanh series for the compensated log: |z|^(k+2)/(k+2) must stay
+// below the compensated unit roundoff (2^-48 for float pairs, 2^-104 for double pairs)
+template <typename F> struct LogTerms { static constexpr int top = 19; };
+template <> struct LogTerms<double> { static constexpr int top = 43; };
 SPH2D_HD float ldexp_f(float x, int e) {
 #if defined(__CUDA_ARCH__)
   return ldexpf(x, e);
@@ -246,9 +298,9 @@ SPH2D_HD float ldexp_f(float x, int e) {
   return std::ldexp(x, e);
 #endif
 }
-// natural log of x > 0 to ~2^-44 relative: x = m 2^e with m in [1/sqrt2, sqrt2),
-// log m = 2 atanh(z), z = (m-1)/(m+1), |z| <= 0.1716, series through z^19 (Horner, FF).
-template <typename F>
+// natural log of x > 0 in compensated arithmetic: x = m 2^e with m in [1/sqrt2, sqrt2),
+// log m = 2 atanh(z), z = (m-1)/(m+1), |z| <= 0.1716, odd series through z^top (Horner).
+template <typename F, typename B = F>
 SPH2D_HD FFT<F> ff_log(FFT<F> x) {
   int e = 0;
   const F m = frexp_f(x.hi, &e);
@@ -257,23 +309,24 @@ SPH2D_HD FFT<F> ff_log(FFT<F> x) {
   const FFT<F> one{F(1), F(0)};
   const FFT<F> z = (xm - one) / (xm + one);
   const FFT<F> z2 = z * z;
-  FFT<F> sum = ffc<F>(1.0 / 19.0);
+  constexpr int top = LogTerms<B>::top;
+  FFT<F> sum = ffk<F, B>(1.0, double(top));
 #pragma unroll
-  for (int k = 17; k >= 1; k -= 2) sum = sum * z2 + ffc<F>(1.0 / double(k));
+  for (int k = top - 2; k >= 1; k -= 2) sum = sum * z2 + ffk<F, B>(1.0, double(k));
   const FFT<F> lz = (z * sum) * F(2);
-  return lz + ffc<F>(0.69314718055994530942) * F(float(e));
+  return lz + ffln2<F, B>() * F(double(e));
 }
 // asinh(t2/d) - asinh(t1/d) in FF (see asinh_diff)
-template <typename F>
+template <typename F, typename B = F>
 SPH2D_HD FFT<F> asinh_diff_ff(F t1, F t2, FFT<F> r1, FFT<F> r2, F d) {
   const FFT<F> a1 = r1 + FFT<F>{fabs(t1), F(0)}, a2 = r2 + FFT<F>{fabs(t2), F(0)};
   const bool p1 = t1 >= F(0), p2 = t2 >= F(0);
   FFT<F> l;
   if (p1 == p2) {
-    l = ff_log(a2 / a1);
+    l = ff_log<F, B>(a2 / a1);
   } else {
     const FFT<F> dd{d, F(0)};
-    l = ff_log((a1 / dd) * (a2 / dd));
+    l = ff_log<F, B>((a1 / dd) * (a2 / dd));
   }
   return p2 ? l : -l;
 }
@@ -283,6 +336,7 @@ template <typename R> struct Acc;
 template <> struct Acc<double> {
   using T = double;
   SPH2D_HD static constexpr double c(double v) { return v; }
+  SPH2D_HD static constexpr double c2(double num, double den) { return num / den; }
   SPH2D_HD static double from(double v) { return v; }
   SPH2D_HD static double sq(double v) { return v * v; }
   SPH2D_HD static double root(double v) { return sqrt(v); }
@@ -299,6 +353,7 @@ template <typename F>
 struct AccFF {
   using T = FFT<F>;
   SPH2D_HD static FFT<F> c(double v) { return ffc<F>(v); }
+  SPH2D_HD static FFT<F> c2(double num, double den) { return ffc<F>(num / den); }
   SPH2D_HD static FFT<F> from(F v) { return FFT<F>{v, F(0)}; }
   SPH2D_HD static FFT<F> sq(F v) { return ff_two_prod(v, v); }
   SPH2D_HD static FFT<F> root(FFT<F> v) { return ff_sqrt(v); }
@@ -310,6 +365,31 @@ struct AccFF {
   }
 };
 template <> struct Acc<float> : AccFF<float> {};
+
+// double-double accumulation (FP64 path of the highest-degree kernel, whose alternating
+// coefficients would cost FP64 three to four digits)
+template <typename D>
+struct AccDD {
+  using T = FFT<D>;
+  SPH2D_HD static FFT<D> c(double v) { return FFT<D>{D(v), D(0)}; }
+  SPH2D_HD static FFT<D> c2(double num, double den) {
+    const FFT<double> v = dd_rational(num, den);
+    return FFT<D>{D(v.hi), D(v.lo)};
+  }
+  SPH2D_HD static FFT<D> from(D v) { return FFT<D>{v, D(0)}; }
+  SPH2D_HD static FFT<D> sq(D v) { return ff_two_prod(v, v); }
+  SPH2D_HD static FFT<D> root(FFT<D> v) { return ff_sqrt(v); }
+  SPH2D_HD static D out(FFT<D> v) { return to_f(v); }
+  SPH2D_HD static FFT<D> mulr(FFT<D> a, D b) { return a * b; }
+  SPH2D_HD static FFT<D> jm1(D t1, D t2, D r1, D r2, D d, FFT<D> ra, FFT<D> rb) {
+    (void)r1; (void)r2;
+    return asinh_diff_ff<D, double>(t1, t2, ra, rb, d);
+  }
+};
+
+// accumulation type per precision and kernel polynomial
+template <typename R, class P> struct AccSel { using type = Acc<R>; };
+template <> struct AccSel<double, PolyWC6> { using type = AccDD<double>; };
 
 // ---------------------------------------------------------------------------------------
 // one edge (fan (0, A, B)) of a triangle for the polynomial kernel P; accumulates the
@@ -374,83 +454,89 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   }
 #undef SPH2D_BR
 
-  // ---- edge piece: t in [t1, t2], r = rho(t) <= 1, in the accumulation type A
-  using AC = Acc<R>;
-  using A = typename AC::T;
-  const A d2a = AC::sq(d);
-  const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
-  // running sums without their d^(j+1) factors
-  A Sg = AC::c(0), Sn = AC::c(0), St = AC::c(0);
-  A S10 = AC::c(0), S01 = AC::c(0), S20 = AC::c(0), S11 = AC::c(0), S02 = AC::c(0);
-  A S30 = AC::c(0), S21 = AC::c(0), S12 = AC::c(0), S03 = AC::c(0);
-  const A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);      // Delta J_{-1}
-  const A dJp = AC::from(t2) - AC::from(t1);              // Delta J_0
-  {
-    Sg = Sg + dJp * AC::c(P::b(0) / 2.0);
-    if (P::b(2) != 0.0) Sn = Sn + dJp * AC::c(2.0 * P::b(2) / 3.0);  // k = 2 normal term
+  // ---- edge piece: t in [t1, t2], r = rho(t) <= 1.  Empty when both ends are clamped to the
+  // same side (or d >= 1); it is then skipped, which keeps every power rho^q <= 1 and makes
+  // its contribution exactly zero whatever the compiler contracts into FMAs.
+  if (t1 != t2) {
+    using AC = typename AccSel<R, P>::type;
+    using A = typename AC::T;
+    const A d2a = AC::sq(d);
+    const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
+    // running sums without their d^(j+1) factors
+    A Sg = AC::c(0), Sn = AC::c(0), St = AC::c(0);
+    A S10 = AC::c(0), S01 = AC::c(0), S20 = AC::c(0), S11 = AC::c(0), S02 = AC::c(0);
+    A S30 = AC::c(0), S21 = AC::c(0), S12 = AC::c(0), S03 = AC::c(0);
+    const A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);      // Delta J_{-1}
+    const A dJp = AC::from(t2) - AC::from(t1);              // Delta J_0
+    {
+      Sg = Sg + dJp * AC::c2(P::b(0), 2.0);
+      if (P::b(2) != 0.0) Sn = Sn + dJp * AC::c2(2.0 * P::b(2), 3.0);  // k = 2 normal term
+      if (MOM) {
+        S10 = S10 + dJp * AC::c2(P::b(0), 3.0);
+        S20 = S20 + dJp * AC::c2(P::b(0), 4.0);
+        S30 = S30 + dJp * AC::c2(P::b(0), 5.0);
+        S02 = S02 + dJp * d2a * AC::c2(-P::b(0), 4.0);
+        S12 = S12 + dJp * d2a * AC::c2(-P::b(0), 5.0);
+      }
+    }
+    if (P::b(1) != 0.0) Sn = Sn + dJm * AC::c2(P::b(1), 2.0);  // k = 1 normal term: J_{-1}
+    A p1 = AC::c(1), p2 = AC::c(1);                            // rho^q at the two ends
+    A dJq2 = dJm, dJq1 = dJp;                                  // Delta J_{q-2}, Delta J_{q-1}
+    constexpr int QMAX = MOM ? P::K + 4 : P::K;
+  #pragma unroll
+    for (int q = 1; q <= QMAX; ++q) {
+      p1 = p1 * r1a;
+      p2 = p2 * r2a;
+      const A dP = p2 - p1;                                    // Delta rho^q
+      const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);        // Delta (t rho^q)
+      const A dJ = (dT + dJq2 * d2a * AC::c(double(q))) * AC::c2(1.0, double(q + 1));
+      if (q <= P::K && P::b(q) != 0.0) Sg = Sg + dJ * AC::c2(P::b(q), double(q + 2));
+      if (q + 2 <= P::K && P::b(q + 2) != 0.0)
+        Sn = Sn + dJ * AC::c2(double(q + 2) * P::b(q + 2), double(q + 3));
+      if (q <= P::K && P::b(q) != 0.0) St = St + dP * AC::c2(P::b(q), double(q + 1));
+      if (MOM) {
+        if (q <= P::K && P::b(q) != 0.0) {
+          S10 = S10 + dJ * AC::c2(P::b(q), double(q + 3));
+          S20 = S20 + dJ * AC::c2(P::b(q), double(q + 4));
+          S30 = S30 + dJ * AC::c2(P::b(q), double(q + 5));
+          S02 = S02 + dJ * d2a * AC::c2(-P::b(q), double(q + 4));
+          S12 = S12 + dJ * d2a * AC::c2(-P::b(q), double(q + 5));
+        }
+        if (q >= 2 && q - 2 <= P::K && P::b(q - 2) != 0.0) {
+          S02 = S02 + dJ * AC::c2(P::b(q - 2), double(q + 2));
+          S12 = S12 + dJ * AC::c2(P::b(q - 2), double(q + 3));
+          S01 = S01 + dP * AC::c2(P::b(q - 2), double(q + 1) * double(q));
+          S11 = S11 + dP * AC::c2(P::b(q - 2), double(q + 2) * double(q));
+          S21 = S21 + dP * AC::c2(P::b(q - 2), double(q + 3) * double(q));
+          S03 = S03 + dP * d2a * AC::c2(-P::b(q - 2), double(q + 3) * double(q));
+        }
+        if (q >= 4 && q - 4 <= P::K && P::b(q - 4) != 0.0)
+          S03 = S03 + dP * AC::c2(P::b(q - 4), double(q + 1) * double(q));
+      }
+      dJq2 = dJq1;
+      dJq1 = dJ;
+    }
+    eg += d * AC::out(Sg);
+    en += d2 * AC::out(Sn);
+    et += d * AC::out(St);
     if (MOM) {
-      S10 = S10 + dJp * AC::c(P::b(0) / 3.0);
-      S20 = S20 + dJp * AC::c(P::b(0) / 4.0);
-      S30 = S30 + dJp * AC::c(P::b(0) / 5.0);
-      S02 = S02 + dJp * d2a * AC::c(-P::b(0) / 4.0);
-      S12 = S12 + dJp * d2a * AC::c(-P::b(0) / 5.0);
+      const R d3 = d2 * d, d4 = d2 * d2;
+      E[1] += d2 * AC::out(S10);
+      E[2] += d * AC::out(S01);
+      E[3] += d3 * AC::out(S20);
+      E[4] += d2 * AC::out(S11);
+      E[5] += d * AC::out(S02);
+      E[6] += d4 * AC::out(S30);
+      E[7] += d3 * AC::out(S21);
+      E[8] += d2 * AC::out(S12);
+      E[9] += d * AC::out(S03);
     }
   }
-  if (P::b(1) != 0.0) Sn = Sn + dJm * AC::c(P::b(1) / 2.0);  // k = 1 normal term: J_{-1}
-  A p1 = AC::c(1), p2 = AC::c(1);                            // rho^q at the two ends
-  A dJq2 = dJm, dJq1 = dJp;                                  // Delta J_{q-2}, Delta J_{q-1}
-  constexpr int QMAX = MOM ? P::K + 4 : P::K;
-#pragma unroll
-  for (int q = 1; q <= QMAX; ++q) {
-    p1 = p1 * r1a;
-    p2 = p2 * r2a;
-    const A dP = p2 - p1;                                    // Delta rho^q
-    const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);        // Delta (t rho^q)
-    const A dJ = (dT + dJq2 * d2a * AC::c(double(q))) * AC::c(1.0 / double(q + 1));
-    if (q <= P::K && P::b(q) != 0.0) Sg = Sg + dJ * AC::c(P::b(q) / double(q + 2));
-    if (q + 2 <= P::K && P::b(q + 2) != 0.0)
-      Sn = Sn + dJ * AC::c(double(q + 2) * P::b(q + 2) / double(q + 3));
-    if (q <= P::K && P::b(q) != 0.0) St = St + dP * AC::c(P::b(q) / double(q + 1));
-    if (MOM) {
-      if (q <= P::K && P::b(q) != 0.0) {
-        S10 = S10 + dJ * AC::c(P::b(q) / double(q + 3));
-        S20 = S20 + dJ * AC::c(P::b(q) / double(q + 4));
-        S30 = S30 + dJ * AC::c(P::b(q) / double(q + 5));
-        S02 = S02 + dJ * d2a * AC::c(-P::b(q) / double(q + 4));
-        S12 = S12 + dJ * d2a * AC::c(-P::b(q) / double(q + 5));
-      }
-      if (q >= 2 && q - 2 <= P::K && P::b(q - 2) != 0.0) {
-        S02 = S02 + dJ * AC::c(P::b(q - 2) / double(q + 2));
-        S12 = S12 + dJ * AC::c(P::b(q - 2) / double(q + 3));
-        S01 = S01 + dP * AC::c(P::b(q - 2) / (double(q + 1) * double(q)));
-        S11 = S11 + dP * AC::c(P::b(q - 2) / (double(q + 2) * double(q)));
-        S21 = S21 + dP * AC::c(P::b(q - 2) / (double(q + 3) * double(q)));
-        S03 = S03 + dP * d2a * AC::c(-P::b(q - 2) / (double(q + 3) * double(q)));
-      }
-      if (q >= 4 && q - 4 <= P::K && P::b(q - 4) != 0.0)
-        S03 = S03 + dP * AC::c(P::b(q - 4) / (double(q + 1) * double(q)));
-    }
-    dJq2 = dJq1;
-    dJq1 = dJ;
-  }
-  eg += d * AC::out(Sg);
-  en += d2 * AC::out(Sn);
-  et += d * AC::out(St);
   // rotate the gradient back from the edge frame (Sec. 2, Eq. improper)
   o.g += eg;
   o.gx += en * nx - et * ny;
   o.gy += en * ny + et * nx;
   if (MOM) {
-    const R d3 = d2 * d, d4 = d2 * d2;
-    E[1] += d2 * AC::out(S10);
-    E[2] += d * AC::out(S01);
-    E[3] += d3 * AC::out(S20);
-    E[4] += d2 * AC::out(S11);
-    E[5] += d * AC::out(S02);
-    E[6] += d4 * AC::out(S30);
-    E[7] += d3 * AC::out(S21);
-    E[8] += d2 * AC::out(S12);
-    E[9] += d * AC::out(S03);
     // p_x = s nx - t ny, p_y = s ny + t nx: expand p_x^a p_y^b into s^j t^l
     const R X = nx, Y = ny;
     o.m[0] += eg;

@@ -361,7 +361,7 @@ def _exact_keep(px, py, tri, H):
         dx, dy = wx - t * ex, wy - t * ey
         d2 = dx * dx + dy * dy
         best = d2 if best is None else min(best, d2)
-    if all(c >= 0 for c in crs) or all(c <= 0 for c in crs):
+    if any(c != 0 for c in crs) and (all(c >= 0 for c in crs) or all(c <= 0 for c in crs)):
         return True, Fr(0)
     return best < Fr(H) * Fr(H), best
 
@@ -372,6 +372,10 @@ def test_cull_matches_exact_rational_predicate():
     parts[:, :2] = rng.uniform(0, 1, size=(300, 2)).astype(np.float32)
     tris = rng.uniform(0, 1, size=(60, 6)).astype(np.float32)
     tris[:20] = (tris[:20] - 0.5) * 0.1 + tris[:20, :2].repeat(3, axis=0).reshape(20, 6)
+    # zero-area triangles: a segment with a repeated vertex, and three collinear vertices
+    tris[20] = [0.5, 0.0, 0.5, 0.0, 0.5, 0.5]
+    tris[21] = [0.125, 0.25, 0.25, 0.5, 0.5, 1.0]
+    parts[:4, :2] = [[0.5, 0.9], [0.5, 0.55], [0.625, 1.25], [0.0625, 0.125]]   # on those lines
     H = 0.0625
     off, pt = oracle.cull(parts, tris, H)
     got = set()
