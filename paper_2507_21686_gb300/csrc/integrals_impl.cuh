@@ -168,7 +168,7 @@ __device__ __forceinline__ void write_particle(const IntArgs& a, int64_t pid, co
 }
 
 template <typename OT, int KID, bool MOM>
-__global__ void __launch_bounds__(256) integrals_kernel(IntArgs a) {
+__global__ void __launch_bounds__(128) integrals_kernel(IntArgs a) {
   constexpr int NV = MOM ? 13 : 3;
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = (a.P + 31) >> 5;
@@ -287,7 +287,7 @@ static sph2d_status run_integrals(Ctx* c, IntArgs a) {
   static int grid_blocks = 0;
   if (grid_blocks == 0) {
     int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrals_kernel<OT, KID, MOM>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrals_kernel<OT, KID, MOM>, 128, 0);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     grid_blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
@@ -297,9 +297,9 @@ static sph2d_status run_integrals(Ctx* c, IntArgs a) {
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
   if (a.P > 0) {
-    int64_t want = (nchunks + 7) / 8;
+    int64_t want = (nchunks + 3) / 4;                    // 4 warps per block
     const unsigned blocks = unsigned(want < grid_blocks ? (want > 0 ? want : 1) : grid_blocks);
-    SPH2D_LAUNCH(c, (integrals_kernel<OT, KID, MOM>), blocks, 256, a);
+    SPH2D_LAUNCH(c, (integrals_kernel<OT, KID, MOM>), blocks, 128, a);
   }
   if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MOM>), unsigned((a.N + 255) / 256), 256, a);
   cudaError_t e = cudaGetLastError();

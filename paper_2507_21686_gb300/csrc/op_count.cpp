@@ -99,6 +99,17 @@ template <> struct Acc<Counted<double>> {
   static R out(R v) { return v; }
   static R mulr(R a, R b) { return a * b; }
   static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
+  using Sum = R;
+  static R zero() { return R(0.0); }
+  template <class P>
+  static R madd(R acc, R x, int row, int slot) {
+    const NumDen c = edge_coef<P>(row - 1, slot);
+    const double k = c.num / c.den;
+    if (k == 0.0) return acc;
+    return fma_f(x, R(k), acc);
+  }
+  static R result(R a) { return a; }
+  static R recip1(int, R iq) { return iq; }
 };
 template <> struct Acc<Counted<float>> : AccFF<Counted<float>> {};
 template <> struct AccSel<Counted<double>, PolyWC6> { using type = AccDD<Counted<double>>; };

@@ -37,6 +37,16 @@
 #include <cmath>
 #endif
 
+// Code shape (measured on GB300): the radial recurrence is unrolled with compile-time
+// coefficients (zero terms vanish) -- SPH2D_Q_UNROLL=0 selects a loop over rows of a
+// constant-memory table instead, which measured 15-40% slower.  The three fans of a triangle
+// are inlined for the single-polynomial kernels (more independent work to hide latency) and
+// looped for the two-piece cubic spline, whose six inlined fans overflow the instruction
+// cache (3.5x slower measured).
+#ifndef SPH2D_Q_UNROLL
+#define SPH2D_Q_UNROLL 1
+#endif
+
 namespace sph2d {
 
 #if !defined(__CUDA_ARCH__)
@@ -331,6 +341,110 @@ SPH2D_HD FFT<F> asinh_diff_ff(F t1, F t2, FFT<F> r1, FFT<F> r2, F d) {
   return p2 ? l : -l;
 }
 
+// ---------------------------------------------------------------------------------------
+// per-step coefficient rows of the edge-piece sums.  Step q of the recurrence produces
+// Delta J_q and Delta rho^q; each running sum adds them times a constant that depends only on
+// the kernel polynomial and q (b_k = 0 outside 0..K):
+//   gamma      Sg  += dJ  b_q/(q+2)              grad n  Sn  += dJ (q+2) b_{q+2}/(q+3)
+//   grad t     St  += dP  b_q/(q+1)
+//   M10,M20,M30      += dJ  b_q/(q+3), b_q/(q+4), b_q/(q+5)
+//   M02, M12         += dJ  b_{q-2}/(q+2) | b_{q-2}/(q+3)   and  dJ d^2 (-b_q/(q+4) | -b_q/(q+5))
+//   M01, M11, M21    += dP  b_{q-2}/((q+1+m-1) q)   (m = 1, 2, 3)
+//   M03              += dP  b_{q-4}/((q+1) q)        and  dP d^2 (-b_{q-2}/((q+3) q))
+// The rows live in constant memory (the step index is uniform across a warp) so the
+// recurrence loop needs no unrolling.
+// ---------------------------------------------------------------------------------------
+enum : int {
+  SL_G = 0, SL_N, SL_T, SL_10, SL_20, SL_30, SL_02A, SL_02B, SL_12A, SL_12B,
+  SL_01, SL_11, SL_21, SL_03A, SL_03B, NSL
+};
+struct NumDen {
+  double num, den;
+};
+template <class P>
+SPH2D_HD constexpr double bk(int k) { return (k < 0 || k > P::K) ? 0.0 : P::b(k); }
+template <class P>
+SPH2D_HD constexpr NumDen edge_coef(int q, int s) {
+  const double Q = double(q);
+  switch (s) {
+    case SL_G: return {bk<P>(q), Q + 2};
+    case SL_N: return {(Q + 2) * bk<P>(q + 2), Q + 3};
+    case SL_T: return q >= 1 ? NumDen{bk<P>(q), Q + 1} : NumDen{0.0, 1.0};
+    case SL_10: return {bk<P>(q), Q + 3};
+    case SL_20: return {bk<P>(q), Q + 4};
+    case SL_30: return {bk<P>(q), Q + 5};
+    case SL_02A: return {bk<P>(q - 2), Q + 2};
+    case SL_02B: return {-bk<P>(q), Q + 4};
+    case SL_12A: return {bk<P>(q - 2), Q + 3};
+    case SL_12B: return {-bk<P>(q), Q + 5};
+    case SL_01: return q >= 1 ? NumDen{bk<P>(q - 2), (Q + 1) * Q} : NumDen{0.0, 1.0};
+    case SL_11: return q >= 1 ? NumDen{bk<P>(q - 2), (Q + 2) * Q} : NumDen{0.0, 1.0};
+    case SL_21: return q >= 1 ? NumDen{bk<P>(q - 2), (Q + 3) * Q} : NumDen{0.0, 1.0};
+    case SL_03A: return q >= 1 ? NumDen{bk<P>(q - 4), (Q + 1) * Q} : NumDen{0.0, 1.0};
+    case SL_03B: return q >= 1 ? NumDen{-bk<P>(q - 2), (Q + 3) * Q} : NumDen{0.0, 1.0};
+  }
+  return {0.0, 1.0};
+}
+template <class P>
+struct EdgeRows {
+  static constexpr int QMIN = -1, QMAX = P::K + 4, ROWS = QMAX - QMIN + 1;
+  double d[ROWS][NSL];                    // double
+  double dlo[ROWS][NSL];                  // double-double low parts
+  float fhi[ROWS][NSL], flo[ROWS][NSL];   // float-float
+  constexpr EdgeRows() : d(), dlo(), fhi(), flo() {
+    for (int q = QMIN; q <= QMAX; ++q)
+      for (int s = 0; s < NSL; ++s) {
+        const NumDen c = edge_coef<P>(q, s);
+        const FFT<double> dd = dd_rational(c.num, c.den);
+        d[q - QMIN][s] = dd.hi;
+        dlo[q - QMIN][s] = dd.lo;
+        const FF ff = ff_const(c.num / c.den);
+        fhi[q - QMIN][s] = ff.hi;
+        flo[q - QMIN][s] = ff.lo;
+      }
+  }
+};
+#if defined(__CUDACC__) && !SPH2D_Q_UNROLL
+static __constant__ EdgeRows<PolyWC2> g_rows_wc2 = EdgeRows<PolyWC2>();
+static __constant__ EdgeRows<PolyWC4> g_rows_wc4 = EdgeRows<PolyWC4>();
+static __constant__ EdgeRows<PolyWC6> g_rows_wc6 = EdgeRows<PolyWC6>();
+static __constant__ EdgeRows<PolyCube> g_rows_cube = EdgeRows<PolyCube>();
+#endif
+template <class P>
+struct HostRows {
+  static constexpr EdgeRows<P> rows = EdgeRows<P>();
+};
+template <class P> SPH2D_HD const EdgeRows<P>& edge_rows();
+#if defined(__CUDA_ARCH__) && !SPH2D_Q_UNROLL
+#define SPH2D_ROWS(POLY, VAR) \
+  template <> SPH2D_HD const EdgeRows<POLY>& edge_rows<POLY>() { return VAR; }
+#else
+#define SPH2D_ROWS(POLY, VAR) \
+  template <> SPH2D_HD const EdgeRows<POLY>& edge_rows<POLY>() { return HostRows<POLY>::rows; }
+#endif
+SPH2D_ROWS(PolyWC2, g_rows_wc2)
+SPH2D_ROWS(PolyWC4, g_rows_wc4)
+SPH2D_ROWS(PolyWC6, g_rows_wc6)
+SPH2D_ROWS(PolyCube, g_rows_cube)
+#undef SPH2D_ROWS
+
+// compensated running sum for the FF / double-double paths: s + c, where every product
+// x*k is formed to ~2^-2p and every addition's rounding error goes into c
+template <typename F>
+struct CSum {
+  F s, c;
+};
+template <typename F>
+SPH2D_HD CSum<F> csum_madd(CSum<F> a, FFT<F> x, F khi, F klo) {
+  const F ph = x.hi * khi;
+  F pl = fma_f(x.hi, khi, -ph);
+  pl = fma_f(x.hi, klo, fma_f(x.lo, khi, pl));
+  const F s = a.s + ph;
+  const F bb = s - a.s;
+  const F err = (a.s - (s - bb)) + (ph - bb);
+  return CSum<F>{s, a.c + (err + pl)};
+}
+
 // accumulation type of the radial part: double for the FP64 path, FF for the FP32 path
 template <typename R> struct Acc;
 template <> struct Acc<double> {
@@ -342,6 +456,20 @@ template <> struct Acc<double> {
   SPH2D_HD static double root(double v) { return sqrt(v); }
   SPH2D_HD static double out(double v) { return v; }
   SPH2D_HD static double mulr(double a, double b) { return a * b; }
+  using Sum = double;
+  SPH2D_HD static double zero() { return 0.0; }
+  template <class P>
+  SPH2D_HD static double madd(double acc, double x, int row, int slot) {
+#if SPH2D_Q_UNROLL
+    const NumDen c = edge_coef<P>(row - 1, slot);
+    const double k = c.num / c.den;
+#else
+    const double k = edge_rows<P>().d[row][slot];
+#endif
+    return k == 0.0 ? acc : fma_f(x, k, acc);      // zero test is uniform across the warp
+  }
+  SPH2D_HD static double recip1(int, double iq) { return iq; }
+  SPH2D_HD static double result(double acc) { return acc; }
   SPH2D_HD static double jm1(double t1, double t2, double r1, double r2, double d, double ra,
                              double rb) {
     (void)ra; (void)rb;
@@ -363,6 +491,27 @@ struct AccFF {
     (void)r1; (void)r2;
     return asinh_diff_ff(t1, t2, ra, rb, d);
   }
+  using Sum = CSum<F>;
+  SPH2D_HD static CSum<F> zero() { return CSum<F>{F(0), F(0)}; }
+  template <class P>
+  SPH2D_HD static CSum<F> madd(CSum<F> acc, FFT<F> x, int row, int slot) {
+#if SPH2D_Q_UNROLL
+    const NumDen c = edge_coef<P>(row - 1, slot);
+    if (c.num == 0.0) return acc;
+    const FF k = ff_const(c.num / c.den);
+    return csum_madd(acc, x, F(k.hi), F(k.lo));
+#else
+    const EdgeRows<P>& r = edge_rows<P>();
+    if (r.fhi[row][slot] == 0.0f) return acc;        // uniform across the warp
+    return csum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]));
+#endif
+  }
+  // 1/(q+1) as a compensated pair: hi rounded, lo from the exact residual 1 - hi (q+1)
+  SPH2D_HD static FFT<F> recip1(int q, F iq) {
+    const F r = fma_f(-iq, F(float(q + 1)), F(1));
+    return FFT<F>{iq, r * iq};
+  }
+  SPH2D_HD static F result(CSum<F> a) { return a.s + a.c; }
 };
 template <> struct Acc<float> : AccFF<float> {};
 
@@ -385,6 +534,26 @@ struct AccDD {
     (void)r1; (void)r2;
     return asinh_diff_ff<D, double>(t1, t2, ra, rb, d);
   }
+  using Sum = CSum<D>;
+  SPH2D_HD static CSum<D> zero() { return CSum<D>{D(0), D(0)}; }
+  template <class P>
+  SPH2D_HD static CSum<D> madd(CSum<D> acc, FFT<D> x, int row, int slot) {
+#if SPH2D_Q_UNROLL
+    const NumDen c = edge_coef<P>(row - 1, slot);
+    if (c.num == 0.0) return acc;
+    const FFT<double> k = dd_rational(c.num, c.den);
+    return csum_madd(acc, x, D(k.hi), D(k.lo));
+#else
+    const EdgeRows<P>& r = edge_rows<P>();
+    if (r.d[row][slot] == 0.0) return acc;           // uniform across the warp
+    return csum_madd(acc, x, D(r.d[row][slot]), D(r.dlo[row][slot]));
+#endif
+  }
+  SPH2D_HD static FFT<D> recip1(int q, D iq) {
+    const D r = fma_f(-iq, D(double(q + 1)), D(1));
+    return FFT<D>{iq, r * iq};
+  }
+  SPH2D_HD static D result(CSum<D> a) { return a.s + a.c; }
 };
 
 // accumulation type per precision and kernel polynomial
@@ -463,73 +632,66 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     const A d2a = AC::sq(d);
     const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
     // running sums without their d^(j+1) factors
-    A Sg = AC::c(0), Sn = AC::c(0), St = AC::c(0);
-    A S10 = AC::c(0), S01 = AC::c(0), S20 = AC::c(0), S11 = AC::c(0), S02 = AC::c(0);
-    A S30 = AC::c(0), S21 = AC::c(0), S12 = AC::c(0), S03 = AC::c(0);
+    using SM = typename AC::Sum;
+    SM Sg = AC::zero(), Sn = AC::zero(), St = AC::zero();
+    SM S10 = AC::zero(), S01 = AC::zero(), S20 = AC::zero(), S11 = AC::zero(), S02 = AC::zero();
+    SM S30 = AC::zero(), S21 = AC::zero(), S12 = AC::zero(), S03 = AC::zero();
+    const A zeroA = AC::c(0);
+    // one step of the sums: q's row, Delta J_q and Delta rho^q
+    auto step = [&](int row, const A& dJ, const A& dP) {
+      Sg = AC::template madd<P>(Sg, dJ, row, SL_G);
+      Sn = AC::template madd<P>(Sn, dJ, row, SL_N);
+      St = AC::template madd<P>(St, dP, row, SL_T);
+      if (MOM) {
+        const A e1 = dJ * d2a, e2 = dP * d2a;
+        S10 = AC::template madd<P>(S10, dJ, row, SL_10);
+        S20 = AC::template madd<P>(S20, dJ, row, SL_20);
+        S30 = AC::template madd<P>(S30, dJ, row, SL_30);
+        S02 = AC::template madd<P>(AC::template madd<P>(S02, dJ, row, SL_02A), e1, row, SL_02B);
+        S12 = AC::template madd<P>(AC::template madd<P>(S12, dJ, row, SL_12A), e1, row, SL_12B);
+        S01 = AC::template madd<P>(S01, dP, row, SL_01);
+        S11 = AC::template madd<P>(S11, dP, row, SL_11);
+        S21 = AC::template madd<P>(S21, dP, row, SL_21);
+        S03 = AC::template madd<P>(AC::template madd<P>(S03, dP, row, SL_03A), e2, row, SL_03B);
+      }
+    };
     const A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);      // Delta J_{-1}
     const A dJp = AC::from(t2) - AC::from(t1);              // Delta J_0
-    {
-      Sg = Sg + dJp * AC::c2(P::b(0), 2.0);
-      if (P::b(2) != 0.0) Sn = Sn + dJp * AC::c2(2.0 * P::b(2), 3.0);  // k = 2 normal term
-      if (MOM) {
-        S10 = S10 + dJp * AC::c2(P::b(0), 3.0);
-        S20 = S20 + dJp * AC::c2(P::b(0), 4.0);
-        S30 = S30 + dJp * AC::c2(P::b(0), 5.0);
-        S02 = S02 + dJp * d2a * AC::c2(-P::b(0), 4.0);
-        S12 = S12 + dJp * d2a * AC::c2(-P::b(0), 5.0);
-      }
-    }
-    if (P::b(1) != 0.0) Sn = Sn + dJm * AC::c2(P::b(1), 2.0);  // k = 1 normal term: J_{-1}
-    A p1 = AC::c(1), p2 = AC::c(1);                            // rho^q at the two ends
-    A dJq2 = dJm, dJq1 = dJp;                                  // Delta J_{q-2}, Delta J_{q-1}
+    step(0, dJm, zeroA);                                    // q = -1
+    step(1, dJp, zeroA);                                    // q = 0
+    A p1 = AC::c(1), p2 = AC::c(1);                         // rho^q at the two ends
+    A dJq2 = dJm, dJq1 = dJp;                               // Delta J_{q-2}, Delta J_{q-1}
     constexpr int QMAX = MOM ? P::K + 4 : P::K;
-  #pragma unroll
+#if SPH2D_Q_UNROLL
+#pragma unroll
+#else
+#pragma unroll 1
+#endif
     for (int q = 1; q <= QMAX; ++q) {
       p1 = p1 * r1a;
       p2 = p2 * r2a;
-      const A dP = p2 - p1;                                    // Delta rho^q
-      const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);        // Delta (t rho^q)
-      const A dJ = (dT + dJq2 * d2a * AC::c(double(q))) * AC::c2(1.0, double(q + 1));
-      if (q <= P::K && P::b(q) != 0.0) Sg = Sg + dJ * AC::c2(P::b(q), double(q + 2));
-      if (q + 2 <= P::K && P::b(q + 2) != 0.0)
-        Sn = Sn + dJ * AC::c2(double(q + 2) * P::b(q + 2), double(q + 3));
-      if (q <= P::K && P::b(q) != 0.0) St = St + dP * AC::c2(P::b(q), double(q + 1));
-      if (MOM) {
-        if (q <= P::K && P::b(q) != 0.0) {
-          S10 = S10 + dJ * AC::c2(P::b(q), double(q + 3));
-          S20 = S20 + dJ * AC::c2(P::b(q), double(q + 4));
-          S30 = S30 + dJ * AC::c2(P::b(q), double(q + 5));
-          S02 = S02 + dJ * d2a * AC::c2(-P::b(q), double(q + 4));
-          S12 = S12 + dJ * d2a * AC::c2(-P::b(q), double(q + 5));
-        }
-        if (q >= 2 && q - 2 <= P::K && P::b(q - 2) != 0.0) {
-          S02 = S02 + dJ * AC::c2(P::b(q - 2), double(q + 2));
-          S12 = S12 + dJ * AC::c2(P::b(q - 2), double(q + 3));
-          S01 = S01 + dP * AC::c2(P::b(q - 2), double(q + 1) * double(q));
-          S11 = S11 + dP * AC::c2(P::b(q - 2), double(q + 2) * double(q));
-          S21 = S21 + dP * AC::c2(P::b(q - 2), double(q + 3) * double(q));
-          S03 = S03 + dP * d2a * AC::c2(-P::b(q - 2), double(q + 3) * double(q));
-        }
-        if (q >= 4 && q - 4 <= P::K && P::b(q - 4) != 0.0)
-          S03 = S03 + dP * AC::c2(P::b(q - 4), double(q + 1) * double(q));
-      }
+      const A dP = p2 - p1;                                 // Delta rho^q
+      const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);     // Delta (t rho^q)
+      const R qf = R(q), iq = R(1) / R(q + 1);
+      const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);   // Delta J_q
+      step(q + 1, dJ, dP);
       dJq2 = dJq1;
       dJq1 = dJ;
     }
-    eg += d * AC::out(Sg);
-    en += d2 * AC::out(Sn);
-    et += d * AC::out(St);
+    eg += d * AC::result(Sg);
+    en += d2 * AC::result(Sn);
+    et += d * AC::result(St);
     if (MOM) {
       const R d3 = d2 * d, d4 = d2 * d2;
-      E[1] += d2 * AC::out(S10);
-      E[2] += d * AC::out(S01);
-      E[3] += d3 * AC::out(S20);
-      E[4] += d2 * AC::out(S11);
-      E[5] += d * AC::out(S02);
-      E[6] += d4 * AC::out(S30);
-      E[7] += d3 * AC::out(S21);
-      E[8] += d2 * AC::out(S12);
-      E[9] += d * AC::out(S03);
+      E[1] += d2 * AC::result(S10);
+      E[2] += d * AC::result(S01);
+      E[3] += d3 * AC::result(S20);
+      E[4] += d2 * AC::result(S11);
+      E[5] += d * AC::result(S02);
+      E[6] += d4 * AC::result(S30);
+      E[7] += d3 * AC::result(S21);
+      E[8] += d2 * AC::result(S12);
+      E[9] += d * AC::result(S03);
     }
   }
   // rotate the gradient back from the edge frame (Sec. 2, Eq. improper)
@@ -557,11 +719,34 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
 }
 
 // signed sum over the three fans of one local-frame triangle, single polynomial piece
-template <typename R, class P, bool MOM>
+template <typename R, class P, bool MOM, bool UNROLL_FANS>
 SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
-  add_fan<R, P, MOM>(ax, ay, bx, by, o);
-  add_fan<R, P, MOM>(bx, by, cx, cy, o);
-  add_fan<R, P, MOM>(cx, cy, ax, ay, o);
+  R x0 = ax, y0 = ay, x1 = bx, y1 = by, x2 = cx, y2 = cy;
+  if (UNROLL_FANS) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      add_fan<R, P, MOM>(x0, y0, x1, y1, o);
+      const R tx = x0, ty = y0;
+      x0 = x1;
+      y0 = y1;
+      x1 = x2;
+      y1 = y2;
+      x2 = tx;
+      y2 = ty;
+    }
+    return;
+  }
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    add_fan<R, P, MOM>(x0, y0, x1, y1, o);
+    const R tx = x0, ty = y0;
+    x0 = x1;
+    y0 = y1;
+    x1 = x2;
+    y1 = y2;
+    x2 = tx;
+    y2 = ty;
+  }
 }
 
 // raw integrals of kernel KID over the local-frame triangle, in input orientation
@@ -569,30 +754,36 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
 template <typename R, int KID, bool MOM>
 SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   clear(o);
-  if (KID == KID_WC2) tri_poly<R, PolyWC2, MOM>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MOM>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MOM>(ax, ay, bx, by, cx, cy, o);
+  if (KID == KID_WC2) tri_poly<R, PolyWC2, MOM, true>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MOM, true>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MOM, true>(ax, ay, bx, by, cx, cy, o);
   else {
     // k(q) = 2 k1(q) - k1(2q), k1 = (1-q)^3_+.  With p' = 2p:
     //   int f(p) k1(2|p|) dA = 1/4 int f(p'/2) k1(|p'|) dA',  f = p^m -> 2^-m
     //   int k1'(2|p|) p/|p| dA = 1/4 int k1'(|p'|) p'/|p'| dA'   and k'(q) = 2k1'(q) - 2k1'(2q)
-    PairOut<R> h;
-    clear(h);
-    tri_poly<R, PolyCube, MOM>(ax, ay, bx, by, cx, cy, o);
-    tri_poly<R, PolyCube, MOM>(R(2) * ax, R(2) * ay, R(2) * bx, R(2) * by, R(2) * cx,
-                               R(2) * cy, h);
-    o.g = R(2) * o.g - R(0.25) * h.g;
-    o.gx = R(2) * o.gx - R(0.5) * h.gx;
-    o.gy = R(2) * o.gy - R(0.5) * h.gy;
-    if (MOM) {
-      // 2^-(m+2) for the degree m of each moment
-      o.m[0] = R(2) * o.m[0] - R(0.25) * h.m[0];
+    // Both pieces run through one instance of the (1-q)^3 code.
+#pragma unroll 1
+    for (int piece = 0; piece < 2; ++piece) {
+      const R sc = piece ? R(2) : R(1);
+      PairOut<R> h;
+      clear(h);
+      tri_poly<R, PolyCube, MOM, false>(sc * ax, sc * ay, sc * bx, sc * by, sc * cx, sc * cy, h);
+      const R wg = piece ? R(-0.25) : R(2);     // 2^-(m+2), m = 0
+      const R wd = piece ? R(-0.5) : R(2);      // gradient
+      o.g += wg * h.g;
+      o.gx += wd * h.gx;
+      o.gy += wd * h.gy;
+      if (MOM) {
+        const R w1 = piece ? R(-0.125) : R(2), w2 = piece ? R(-0.0625) : R(2),
+                w3 = piece ? R(-0.03125) : R(2);
+        o.m[0] += wg * h.m[0];
 #pragma unroll
-      for (int i = 1; i < 3; ++i) o.m[i] = R(2) * o.m[i] - R(0.125) * h.m[i];
+        for (int i = 1; i < 3; ++i) o.m[i] += w1 * h.m[i];
 #pragma unroll
-      for (int i = 3; i < 6; ++i) o.m[i] = R(2) * o.m[i] - R(0.0625) * h.m[i];
+        for (int i = 3; i < 6; ++i) o.m[i] += w2 * h.m[i];
 #pragma unroll
-      for (int i = 6; i < 10; ++i) o.m[i] = R(2) * o.m[i] - R(0.03125) * h.m[i];
+        for (int i = 6; i < 10; ++i) o.m[i] += w3 * h.m[i];
+      }
     }
   }
 }

@@ -21,7 +21,13 @@ FP32_LANES_PER_SM = 128
 
 
 def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
+    """FMA-flop peak (every lane issuing one FMA per clock)."""
     return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def fp32_lane_op_peak_tops(mhz: float = SM_MAX_MHZ) -> float:
+    """FP32 lane-operation peak: every FP32 lane issuing one add, mul or fma per clock."""
+    return SMS * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
 
 
 # NVIDIA's published dense FP64 rate for the GB300 (Blackwell Ultra) GPU, at boost clock
@@ -53,3 +59,8 @@ def pair_ops(kernel, moments: bool, fp32: bool, local_tri) -> tuple[int, np.ndar
 def mean_flops_per_pair(kernel, moments: bool, fp32: bool, local_tris: np.ndarray) -> float:
     """Average over a sample of real pairs (rows of local-frame triangles, H = 1)."""
     return float(np.mean([pair_ops(kernel, moments, fp32, t)[0] for t in local_tris]))
+
+
+def mean_ops_per_pair(kernel, moments: bool, fp32: bool, local_tris: np.ndarray) -> float:
+    """Floating-point operations per pair with fma counted once (lane-operations)."""
+    return float(np.mean([pair_ops(kernel, moments, fp32, t)[1][:6].sum() for t in local_tris]))
