@@ -206,6 +206,35 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* ctx, const float* part
                                                const void* d_gamma, const void* d_grad_gamma,
                                                void* d_particles, void* d_tris);
 
+/*
+ * Allocation-free integrals over a caller-supplied pair list (gamma and grad gamma).
+ * The paper has no counterpart: this serves callers that cannot allocate device memory while
+ * they run -- memory pools that forbid cudaMalloc inside a solver step, frameworks that own
+ * all device memory, code that must not risk an allocation's implicit synchronisation or
+ * failure.  It takes no context (creating one allocates) and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its only scratch is a file-scope device array of
+ * SPH2D_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until process exit.
+ *   particles   device float4 [N]; tris device float [M][6]
+ *   pair_off    device int64 [N+1], pair_tri device int32 [P]: the pair list of
+ *               sph2d_pair_list (particle-major CSR, P = pair_off[N])
+ *   kernel, H, mode as sph2d_boundary_integrals (SPH2D_FP64 or SPH2D_FP32_FIXUP)
+ *   gamma       device real [N];  grad_gamma device real [N][2] or NULL
+ *   stream      cudaStream_t (NULL = legacy default stream); runs on the current device
+ * Limit: P <= 32 * floor((SPH2D_NOALLOC_SCRATCH_BYTES - 256) / (6 * sizeof(real))), i.e.
+ * 5,592,405 pairs in SPH2D_FP64 and 11,184,810 in SPH2D_FP32_FIXUP; larger lists return
+ * SPH2D_ERR_CAPACITY before any work is enqueued.
+ * All calls share the array: calls that overlap on the GPU (other streams or host threads at
+ * the same time) race.  The first call on a device resolves the array's address with that
+ * device current; make it before any stream capture.
+ * Errors (status only, there is no context for a message): INVALID_ARG, CAPACITY, CUDA.
+ */
+#define SPH2D_NOALLOC_SCRATCH_BYTES (8u << 20)
+sph2d_status sph2d_pair_list_integrals_noalloc(const float* particles, int64_t N,
+                                               const float* tris, int64_t M,
+                                               const int64_t* pair_off, const int32_t* pair_tri,
+                                               int64_t P, int kernel, double H, int mode,
+                                               void* gamma, void* grad_gamma, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
