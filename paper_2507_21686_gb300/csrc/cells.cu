@@ -312,6 +312,14 @@ __global__ void cull_kernel(CullArgs a, const float4* __restrict__ parts, int64_
   if (!FILL) counts[i] = n;
 }
 
+// sort the int32 segments data[start[i] .. start[i+1]) ascending (used for cell lists and,
+// by the adjoint, for per-triangle particle lists)
+void launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg) {
+  if (nseg <= 0) return;
+  const int blocks = nseg < 65535 ? int(nseg) : 65535;
+  SPH2D_LAUNCH(c, (sort_cells_kernel), blocks, 256, start, data, nseg);
+}
+
 // ---------------------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------------------

@@ -469,6 +469,9 @@ template <> struct Acc<double> {
     return k == 0.0 ? acc : fma_f(x, k, acc);      // zero test is uniform across the warp
   }
   SPH2D_HD static double recip1(int, double iq) { return iq; }
+  SPH2D_HD static double maddc(double acc, double x, double num, double den) {
+    return num == 0.0 ? acc : fma_f(x, num / den, acc);
+  }
   SPH2D_HD static double result(double acc) { return acc; }
   SPH2D_HD static double jm1(double t1, double t2, double r1, double r2, double d, double ra,
                              double rb) {
@@ -505,6 +508,11 @@ struct AccFF {
     if (r.fhi[row][slot] == 0.0f) return acc;        // uniform across the warp
     return csum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]));
 #endif
+  }
+  SPH2D_HD static CSum<F> maddc(CSum<F> acc, FFT<F> x, double num, double den) {
+    if (num == 0.0) return acc;
+    const FF k = ff_const(num / den);
+    return csum_madd(acc, x, F(k.hi), F(k.lo));
   }
   // 1/(q+1) as a compensated pair: hi rounded, lo from the exact residual 1 - hi (q+1)
   SPH2D_HD static FFT<F> recip1(int q, F iq) {
@@ -548,6 +556,11 @@ struct AccDD {
     if (r.d[row][slot] == 0.0) return acc;           // uniform across the warp
     return csum_madd(acc, x, D(r.d[row][slot]), D(r.dlo[row][slot]));
 #endif
+  }
+  SPH2D_HD static CSum<D> maddc(CSum<D> acc, FFT<D> x, double num, double den) {
+    if (num == 0.0) return acc;
+    const FFT<double> k = dd_rational(num, den);
+    return csum_madd(acc, x, D(k.hi), D(k.lo));
   }
   SPH2D_HD static FFT<D> recip1(int q, D iq) {
     const D r = fma_f(-iq, D(double(q + 1)), D(1));
@@ -793,6 +806,104 @@ template <typename R>
 SPH2D_HD int tri_orientation(R ax, R ay, R bx, R by, R cx, R cy) {
   const R a2 = diff_of_products(bx - ax, cy - ay, by - ay, cx - ax);
   return a2 > R(0) ? 1 : (a2 < R(0) ? -1 : 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// adjoint: derivative of the area integral with respect to the triangle's vertices.  Moving
+// vertex j moves its two edges with the hat weight lambda_j, so (transport theorem)
+//   d gamma / d nu_j = (C/H) sum_{e ni j} n_e int_e k(|p|) lambda_j ds      (local frame)
+// with n_e the outward unit normal.  On an edge with tangent coordinate t (foot of the
+// perpendicular at t = 0, distance d) |p| = rho(t) = sqrt(d^2 + t^2), so the two integrals
+//   Jo = int k(rho) dt = sum_k b_k Delta J_k,   To = int k(rho) t dt = sum_k b_k Delta rho^{k+2}/(k+2)
+// over t clipped to the support are the same square-root integrals as the forward edge piece.
+// ---------------------------------------------------------------------------------------
+template <typename R, class P>
+SPH2D_HD void edge_line_integrals(R d, R t1, R t2, R& Jo, R& To) {
+  using AC = typename AccSel<R, P>::type;
+  using A = typename AC::T;
+  using SM = typename AC::Sum;
+  SM sJ = AC::zero(), sT = AC::zero();
+  const A d2a = AC::sq(d);
+  const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
+  // Delta J_{-1} enters only as d^2 J_{-1}; at d = 0 that product vanishes
+  const R r1 = sqrt(d * d + t1 * t1), r2 = sqrt(d * d + t2 * t2);
+  const A dJm = d > Tiny<R>::v() ? AC::jm1(t1, t2, r1, r2, d, r1a, r2a) : AC::c(0);
+  const A dJp = AC::from(t2) - AC::from(t1);
+  sJ = AC::maddc(sJ, dJp, P::b(0), 1.0);
+  A p1 = AC::c(1), p2 = AC::c(1);
+  A dJq2 = dJm, dJq1 = dJp;
+#pragma unroll
+  for (int q = 1; q <= P::K + 2; ++q) {
+    p1 = p1 * r1a;
+    p2 = p2 * r2a;
+    const A dP = p2 - p1;
+    if (q <= P::K) {
+      const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);
+      const R qf = R(q), iq = R(1) / R(q + 1);
+      const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);
+      sJ = AC::maddc(sJ, dJ, bk<P>(q), 1.0);
+      dJq2 = dJq1;
+      dJq1 = dJ;
+    }
+    if (q >= 2) sT = AC::maddc(sT, dP, bk<P>(q - 2), double(q));
+  }
+  Jo = AC::result(sJ);
+  To = AC::result(sT);
+}
+
+// raw vertex gradients (without C/H) of one local-frame triangle for polynomial P
+template <typename R, class P>
+SPH2D_HD void tri_vertex_grad_poly(const R* v, R* g) {
+  const R area2 = diff_of_products(v[2] - v[0], v[5] - v[1], v[3] - v[1], v[4] - v[0]);
+  if (area2 == R(0)) return;
+  const R sg = area2 > R(0) ? R(1) : R(-1);
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    const int ia = e, ib = e == 2 ? 0 : e + 1;
+    const R ax = v[2 * ia], ay = v[2 * ia + 1], bx = v[2 * ib], by = v[2 * ib + 1];
+    const R ex = bx - ax, ey = by - ay;
+    const R l2 = ex * ex + ey * ey;
+    if (l2 == R(0)) continue;
+    const R L = sqrt(l2), il = R(1) / L;
+    const R ux = ex * il, uy = ey * il;                  // edge direction
+    const R d = fabs(diff_of_products(ax, by, ay, bx)) * il;
+    const R tA = ax * ux + ay * uy;                      // tB = tA + L
+    const R tB = bx * ux + by * uy;
+    if (!(d < R(1))) continue;                           // edge outside the support
+    const R ts = sqrt((R(1) - d) * (R(1) + d));
+    const R t1 = fmin(fmax(tA, -ts), ts), t2 = fmin(fmax(tB, -ts), ts);
+    if (!(t2 > t1)) continue;
+    R Jo, To;
+    edge_line_integrals<R, P>(d, t1, t2, Jo, To);
+    const R wb = (To - tA * Jo) * il;                    // int k lambda_b ds
+    const R wa = Jo - wb;                                // int k lambda_a ds
+    const R nx = sg * uy, ny = -sg * ux;                 // outward unit normal
+    g[2 * ia] += wa * nx;
+    g[2 * ia + 1] += wa * ny;
+    g[2 * ib] += wb * nx;
+    g[2 * ib + 1] += wb * ny;
+  }
+}
+
+// d gamma / d (x0, y0, x1, y1, x2, y2) in local units (multiply by C/H for world units)
+template <typename R, int KID>
+SPH2D_HD void tri_vertex_grad(const R* v, R* g) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) g[i] = R(0);
+  if (KID == KID_WC2) tri_vertex_grad_poly<R, PolyWC2>(v, g);
+  else if (KID == KID_WC4) tri_vertex_grad_poly<R, PolyWC4>(v, g);
+  else if (KID == KID_WC6) tri_vertex_grad_poly<R, PolyWC6>(v, g);
+  else {
+    // k = 2 k1(q) - k1(2q): edge integrals of k1(2 rho) in the doubled frame, ds' = 2 ds
+    R h[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    tri_vertex_grad_poly<R, PolyCube>(v, g);
+    R w[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) w[i] = R(2) * v[i];
+    tri_vertex_grad_poly<R, PolyCube>(w, h);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = R(2) * g[i] - R(0.5) * h[i];
+  }
 }
 
 }  // namespace sph2d

@@ -195,7 +195,8 @@ sph2d_status sph2d_destroy(sph2d_ctx* h) {
   cudaStreamSynchronize(c.stream);
   DevBuf* bufs[] = {&c.cell_start, &c.cell_cursor, &c.cell_tris, &c.block_tmp, &c.scan_tmp,
                     &c.pair_off,  &c.pair_tri,    &c.pair_pid,  &c.counts,    &c.slots,
-                    &c.host_flags_dev, &c.misc};
+                    &c.host_flags_dev, &c.misc, &c.tri_off, &c.tri_pid, &c.tri_cursor,
+                    &c.bwd_g, &c.bwd_grad};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c.pinned) cudaFreeHost(c.pinned);

@@ -39,7 +39,7 @@ struct Ctx {
   Cells cells;
   // scratch buffers (named slots)
   DevBuf cell_start, cell_cursor, cell_tris, block_tmp, scan_tmp, pair_off, pair_tri, pair_pid,
-      counts, slots, host_flags_dev, misc;
+      counts, slots, host_flags_dev, misc, tri_off, tri_pid, tri_cursor, bwd_g, bwd_grad;
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
   bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
   int64_t launches = 0;        // kernels launched by this context (cumulative)
@@ -56,6 +56,9 @@ sph2d_status exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t
 // culling (cells.cu): builds c->cells and the pair list buffers pair_off/pair_tri/pair_pid
 sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float* tris,
                          int64_t M, double H);
+
+// ascending sort of int32 segments (cells.cu)
+void launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg);
 
 // forward integrals over the context's pair list (integrals.cu)
 sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, void* gamma,
