@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: timed FP32 path only (no FP64 leg, e2e, CPU baseline, L2 flush)")
     return ap.parse_args()
@@ -333,6 +334,27 @@ def run_ours(args):
         max_err[k] = float(rel_err(got, ref, scales(k, w.H, 10)).max())
     del o32, o64
 
+    # ---- gamma + grad gamma only (the metric's integrals), same pair list, FP32 + fix-up
+    gg = {}
+    for k in KERNELS:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        ctx.integrals_from_pairs(k, -1, "fp32_fixup")
+        for a_, b_ in ev:
+            flush.zero_()
+            a_.record(stream)
+            ctx.integrals_from_pairs(k, -1, "fp32_fixup")
+            b_.record(stream)
+        torch.cuda.synchronize()
+        gg[k] = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+    gamma_grad_only = {"per_kernel_ms": gg, "value": P * len(KERNELS) / (sum(gg.values()) / 1e3),
+                       "unit": UNIT, "note": "integral launches only (culling excluded), no moments"}
+
+    # ---- adjoint workload: 262,144 particles x 51,712 triangles, Wendland C4
+    adjoint = run_adjoint(ctx, dev, stream, flush)
+
+    # ---- learned surrogate: train, then serve the 4M x 1M box against the analytic paths
+    surrogate = None if args.no_surrogate else run_surrogate(ctx, dev, stream, flush)
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -382,11 +404,100 @@ def run_ours(args):
         "max_rel_err_vs_fp64_path": max_err,
         "fixup_pairs_per_step": fix,
         "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
+        "gamma_grad_only": gamma_grad_only,
+        "adjoint": adjoint,
+        "surrogate": surrogate,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "measured_peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_adjoint(ctx, dev, stream, flush, steps=3):
+    """Forward + backward of L = sum (gamma - gamma*)^2 on the adjoint workload."""
+    import torch
+    from paper_2507_21686_gb300 import workloads as W
+    w = W.adjoint_box()
+    parts = torch.from_numpy(w.particles).to(dev)
+    tris = torch.from_numpy(w.triangles).to(dev)
+    star = torch.from_numpy(w.extra["target_triangles"]).to(dev)
+    out = {"workload": w.name, "kernel": "wendland_c4"}
+    for mode in ("fp32_fixup", "fp64"):
+        gs, _, _ = ctx.boundary_integrals(parts, star, "wendland_c4", w.H, -1, mode)
+        g, _, _ = ctx.boundary_integrals(parts, tris, "wendland_c4", w.H, -1, mode)
+        P = ctx.pair_count()
+        dg = 2.0 * (g - gs)
+        ctx.backward(parts, tris, "wendland_c4", w.H, dg, mode)
+        fw, bw = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            g, _, _ = ctx.boundary_integrals(parts, tris, "wendland_c4", w.H, -1, mode)
+            e[1].record(stream)
+            ctx.backward(parts, tris, "wendland_c4", w.H, 2.0 * (g - gs), mode)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            fw.append(e[0].elapsed_time(e[1]))
+            bw.append(e[1].elapsed_time(e[2]))
+        out[mode] = {"pairs": P, "forward_ms": float(np.mean(fw)), "backward_ms": float(np.mean(bw)),
+                     "backward_pairs_per_s": P / (np.mean(bw) / 1e3)}
+    return out
+
+
+def run_surrogate(ctx, dev, stream, flush, reps=3):
+    """Train the surrogate on analytic pairs, then time gamma + grad gamma over the pair list
+    of the 2048^2-particle box (surrogate with guarded fallback vs FP32 + fix-up vs FP64)."""
+    import torch
+    from paper_2507_21686_gb300 import workloads as W
+    from tests.helpers import rel_err, scales
+    k = "wendland_c2"
+    t0 = time.time()
+    tp = W.surrogate_training_pairs(2_000_000, np.random.default_rng(55))
+    gen_s = time.time() - t0
+    tpd = torch.from_numpy(tp).to(dev)
+    ctx.surrogate_init(k, 5)
+    epochs, batch = 8, 4096
+    torch.cuda.synchronize()
+    t0 = time.time()
+    loss, used = ctx.surrogate_train(tpd, 1.0, epochs=epochs, batch=batch, lr=3e-3, seed=5)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    del tpd
+    w = W.surrogate_box()
+    parts = torch.from_numpy(w.particles).to(dev)
+    tris = torch.from_numpy(w.triangles).to(dev)
+    ctx.build_cells(parts, tris, w.H)
+    P = ctx.pair_count()
+    res, outs = {}, {}
+    for mode in ("surrogate", "fp32_fixup", "fp64"):
+        outs[mode] = ctx.integrals_from_pairs(k, -1, mode)
+        st = ctx.stats()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a_, b_ in ev:
+            flush.zero_()
+            a_.record(stream)
+            ctx.integrals_from_pairs(k, -1, mode)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+        res[mode] = {"ms": ms, "pairs_per_s": P / (ms / 1e3)}
+        if mode == "surrogate":
+            res[mode]["fallback_rate"] = st["n_fallback"] / max(P, 1)
+    ref = torch.cat([outs["fp64"][0][:, None], outs["fp64"][1]], 1).cpu().numpy()
+    for mode in ("surrogate", "fp32_fixup"):
+        got = torch.cat([outs[mode][0][:, None], outs[mode][1]], 1).double().cpu().numpy()
+        e = rel_err(got, ref, scales(k, w.H, 0)).max(axis=1)
+        res[mode]["particle_err_vs_fp64_path"] = {"p50": float(np.median(e)), "p99": float(np.percentile(e, 99)),
+                                                  "max": float(e.max())}
+    del outs
+    return {"workload": w.name, "kernel": k, "pairs": P,
+            "train": {"pairs": len(tp), "in_domain": used, "epochs": epochs, "batch": batch,
+                      "steps": epochs * (used // batch), "seconds": train_s, "final_batch_loss": loss,
+                      "data_generation_s_host": gen_s},
+            "speedup_vs_fp32_fixup": res["fp32_fixup"]["ms"] / res["surrogate"]["ms"],
+            "speedup_vs_fp64": res["fp64"]["ms"] / res["surrogate"]["ms"], **res}
 
 
 def run_e2e(args, ctx, parts_h, tris_h, w, dev, stream, P, ws):

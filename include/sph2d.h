@@ -151,13 +151,16 @@ sph2d_status sph2d_pair_list(sph2d_ctx* ctx, int64_t* off, int32_t* tri, int64_t
  * realised as the exact edge/sector fan form described in the implementation).
  *   kernel         sph2d_kernel
  *   moment_degree  -1 (no moments) or 0..3
- *   mode           SPH2D_FP64 or SPH2D_FP32_FIXUP
+ *   mode           SPH2D_FP64, SPH2D_FP32_FIXUP, or SPH2D_SURROGATE (needs
+ *                  moment_degree = -1 and the kernel the surrogate was initialised for;
+ *                  float outputs; see the surrogate section below)
  *   gamma          device real [N]
  *   grad_gamma     device real [N][2]          (may be NULL)
  *   moments        device real [N][nm]         (NULL iff moment_degree < 0)
- * "real" is double for SPH2D_FP64 and float for SPH2D_FP32_FIXUP.  Particles with no pair
+ * "real" is double for SPH2D_FP64 and float otherwise.  Particles with no pair
  * get zeros.  Synchronises as sph2d_build_cells does.
- * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, UNSUPPORTED, CUDA.
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, UNSUPPORTED, NOT_BUILT (surrogate
+ * mode before sph2d_surrogate_init), CUDA.
  */
 sph2d_status sph2d_boundary_integrals(sph2d_ctx* ctx, const float* particles, int64_t N,
                                       const float* tris, int64_t M, int kernel, double H,
@@ -234,6 +237,94 @@ sph2d_status sph2d_pair_list_integrals_noalloc(const float* particles, int64_t N
                                                const int64_t* pair_off, const int32_t* pair_tri,
                                                int64_t P, int kernel, double H, int mode,
                                                void* gamma, void* grad_gamma, void* stream);
+
+/*
+ * ---- Learned surrogate -------------------------------------------------------------------
+ * The paper has no counterpart: a small network that replaces the closed form for pairs
+ * inside a trained domain, evaluated on BF16 tensor cores with FP32 accumulation; every other
+ * pair takes the analytic path (SPH2D_FP32_FIXUP arithmetic).  Outputs are gamma and grad
+ * gamma only, always float.
+ *
+ * Canonical frame (H = 1): the pair's triangle, relative to the particle, is rotated so that
+ * its centroid lies on +x, reflected y -> -y if it is then clockwise, and its vertices are
+ * listed from the one closest to the particle.  Network: 6 canonical coordinates -> 64 -> 64
+ * -> 64 -> 3 (tanh-form GELU between layers), predicting gamma / area and the canonical
+ * local-frame gradient / area; outputs are multiplied by the exact area and mapped back by
+ * the inverse reflection and rotation (gamma is invariant under both).
+ * Guard (the network is used only if all hold, else the pair falls back): largest edge in
+ * [SPH2D_SURROGATE_MIN_SIZE, SPH2D_SURROGATE_MAX_SIZE] H, smallest angle >= 15 degrees,
+ * centroid >= SPH2D_SURROGATE_MIN_CENTROID H from the particle, every vertex within
+ * SPH2D_SURROGATE_MAX_RADIUS H, non-zero finite area.  The guard is evaluated in FP32 on the
+ * FP32 local frame.
+ * Parameters: SPH2D_SURROGATE_PARAMS FP32 values in the order W1[64][6] b1[64] W2[64][64]
+ * b2[64] W3[64][64] b3[64] W4[3][64] b4[3] (W[out][in], row-major); tensor-core operands are
+ * their BF16 roundings.
+ */
+#define SPH2D_SURROGATE_PARAMS 8963
+#define SPH2D_SURROGATE_MIN_SIZE 0.1
+#define SPH2D_SURROGATE_MAX_SIZE 0.45
+#define SPH2D_SURROGATE_MIN_CENTROID 0.2
+#define SPH2D_SURROGATE_MAX_RADIUS 1.5
+
+/* (Re)initialise the surrogate for `kernel`: Glorot-uniform weights from `seed` (64-bit
+ * Mersenne twister, mt19937_64), zero biases and optimiser state.  Synchronises.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+sph2d_status sph2d_surrogate_init(sph2d_ctx* ctx, int kernel, uint64_t seed);
+
+/*
+ * Train on independent pairs (device double [P][8], as sph2d_pair_integrals, support H):
+ * labels are the FP64 analytic integrals; pairs outside the guard are dropped.  Loss: mean
+ * over a batch of sum_c w_c (y_c - t_c)^2 with w = (1/C^2, 1/(4C^2), 1/(4C^2)); AdamW
+ * (beta 0.9, 0.999, eps 1e-8, decoupled weight decay `weight_decay`) with a learning rate
+ * rising from lr/10 to lr over the first 5% of the steps, then a cosine decay to lr/100.
+ * Each epoch visits floor(used / batch) batches in an order shuffled from `seed`.  The run
+ * is deterministic.  *final_loss (host, may be NULL) = loss of the last batch; *n_used (host,
+ * may be NULL) = pairs inside the guard.  Synchronises once per epoch.
+ * Errors: NOT_BUILT (no sph2d_surrogate_init), INVALID_ARG (bad sizes, fewer usable pairs
+ * than one batch), OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_surrogate_train(sph2d_ctx* ctx, const double* pairs, int64_t P, double H,
+                                   int epochs, int batch, double lr, double weight_decay,
+                                   uint64_t seed, double* final_loss, int64_t* n_used);
+
+/*
+ * Independent pairs through the surrogate: out device float [P][3] = (gamma, dgamma/dpx,
+ * dgamma/dpy) in world units; accepted device int32 [P] (may be NULL) = 1 where the network
+ * was used.  sph2d_last_stats reports n_fallback.  Does not synchronise.
+ * Errors: NOT_BUILT, INVALID_ARG, OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_surrogate_pairs(sph2d_ctx* ctx, const double* pairs, int64_t P, double H,
+                                   float* out, int32_t* accepted);
+
+/*
+ * The network alone: canonical inputs x device float [B][6] -> raw outputs y device float
+ * [B][3] (gamma/area, canonical gradient/area), no guard.  Does not synchronise.
+ * Errors: NOT_BUILT, INVALID_ARG, CUDA.
+ */
+sph2d_status sph2d_surrogate_forward(sph2d_ctx* ctx, const float* x, int64_t B, float* y);
+
+/*
+ * Loss and parameter gradient of one batch (the training step without the update):
+ * x device float [B][6], t device float [B][3] -> grad device float [SPH2D_SURROGATE_PARAMS],
+ * loss device float [1].  Does not synchronise.  Errors: NOT_BUILT, INVALID_ARG, CUDA.
+ */
+sph2d_status sph2d_surrogate_grad(sph2d_ctx* ctx, const float* x, const float* t, int64_t B,
+                                  float* grad, float* loss);
+
+/* Copy the FP32 parameters to / from host memory (n = SPH2D_SURROGATE_PARAMS).  get returns
+ * CAPACITY if cap is smaller.  Synchronise.  Errors: NOT_BUILT, INVALID_ARG, CAPACITY, CUDA. */
+sph2d_status sph2d_surrogate_get_params(sph2d_ctx* ctx, float* host, int64_t cap);
+sph2d_status sph2d_surrogate_set_params(sph2d_ctx* ctx, const float* host, int64_t n);
+
+/*
+ * Checkpoint: a versioned binary file (magic "SPH2DSUR", version 1, kernel, layer sizes,
+ * parameter count, optimiser step, FNV-1a 64 checksum) followed by the FP32 parameters and
+ * both Adam moment vectors, so that training resumes exactly.  load checks every header
+ * field, the length and the checksum before it touches the context.  Synchronise.
+ * Errors: NOT_BUILT (save), INVALID_ARG (unreadable or incompatible file), CUDA.
+ */
+sph2d_status sph2d_surrogate_save(sph2d_ctx* ctx, const char* path);
+sph2d_status sph2d_surrogate_load(sph2d_ctx* ctx, const char* path);
 
 #ifdef __cplusplus
 }

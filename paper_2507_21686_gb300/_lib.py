@@ -55,7 +55,19 @@ SIGNATURES = {
     "sph2d_pair_integrals": (_ST, [_P, _P, _I64, _I, _D, _I, _I, _P]),
     "sph2d_boundary_integrals_backward": (_ST, [_P, _P, _I64, _P, _I64, _I, _D, _I, _P, _P, _P, _P]),
     "sph2d_pair_list_integrals_noalloc": (_ST, [_P, _I64, _P, _I64, _P, _P, _I64, _I, _D, _I, _P, _P, _P]),
+    "sph2d_surrogate_init": (_ST, [_P, _I, ctypes.c_uint64]),
+    "sph2d_surrogate_train": (_ST, [_P, _P, _I64, _D, _I, _I, _D, _D, ctypes.c_uint64,
+                                    ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "sph2d_surrogate_pairs": (_ST, [_P, _P, _I64, _D, _P, _P]),
+    "sph2d_surrogate_forward": (_ST, [_P, _P, _I64, _P]),
+    "sph2d_surrogate_grad": (_ST, [_P, _P, _P, _I64, _P, _P]),
+    "sph2d_surrogate_get_params": (_ST, [_P, _P, _I64]),
+    "sph2d_surrogate_set_params": (_ST, [_P, _P, _I64]),
+    "sph2d_surrogate_save": (_ST, [_P, ctypes.c_char_p]),
+    "sph2d_surrogate_load": (_ST, [_P, ctypes.c_char_p]),
 }
+
+SURROGATE_PARAMS = 8963
 
 _lib = None
 

@@ -184,6 +184,73 @@ class Context:
             _mode_id(mode), _ptr(dg), None, _ptr(dp), _ptr(dtr)))
         return dp, dtr
 
+    # -- learned surrogate -------------------------------------------------------------
+    def surrogate_init(self, kernel, seed: int = 0):
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_init(self.h, _kernel_id(kernel), int(seed)))
+        return self
+
+    def surrogate_train(self, pairs, H: float, epochs: int, batch: int = 4096, lr: float = 3e-3,
+                        weight_decay: float = 0.0, seed: int = 0):
+        """Train on independent pairs float64 [P, 8]; returns (last batch loss, pairs used)."""
+        q = pairs.to(device=self._dev(), dtype=torch.float64).contiguous()
+        loss = ctypes.c_double()
+        used = ctypes.c_int64()
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_train(
+            self.h, _ptr(q), q.shape[0], float(H), int(epochs), int(batch), float(lr),
+            float(weight_decay), int(seed), ctypes.byref(loss), ctypes.byref(used)))
+        return loss.value, used.value
+
+    def surrogate_pairs(self, pairs, H: float):
+        """Independent pairs float64 [P, 8] -> (float32 [P, 3] gamma and grad, int32 [P] accepted)."""
+        q = pairs.to(device=self._dev(), dtype=torch.float64).contiguous()
+        out = torch.empty((q.shape[0], 3), dtype=torch.float32, device=self._dev())
+        acc = torch.empty(q.shape[0], dtype=torch.int32, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_pairs(self.h, _ptr(q), q.shape[0], float(H),
+                                                                _ptr(out), _ptr(acc)))
+        return out, acc
+
+    def surrogate_forward(self, x):
+        """Raw network on canonical inputs float32 [B, 6] -> float32 [B, 3]."""
+        xx = x.to(device=self._dev(), dtype=torch.float32).contiguous()
+        y = torch.empty((xx.shape[0], 3), dtype=torch.float32, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_forward(self.h, _ptr(xx), xx.shape[0], _ptr(y)))
+        return y
+
+    def surrogate_grad(self, x, t):
+        """(parameter gradient float32 [SURROGATE_PARAMS], loss) of one batch."""
+        xx = x.to(device=self._dev(), dtype=torch.float32).contiguous()
+        tt = t.to(device=self._dev(), dtype=torch.float32).contiguous()
+        g = torch.empty(_lib.SURROGATE_PARAMS, dtype=torch.float32, device=self._dev())
+        loss = torch.empty(1, dtype=torch.float32, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_grad(self.h, _ptr(xx), _ptr(tt), xx.shape[0],
+                                                               _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def surrogate_params(self) -> torch.Tensor:
+        p = torch.empty(_lib.SURROGATE_PARAMS, dtype=torch.float32)
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_get_params(self.h, _ptr(p), p.numel()))
+        return p
+
+    def set_surrogate_params(self, p):
+        q = torch.as_tensor(p, dtype=torch.float32).contiguous().cpu()
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_set_params(self.h, _ptr(q), q.numel()))
+
+    def surrogate_save(self, path: str):
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_save(self.h, str(path).encode()))
+
+    def surrogate_load(self, path: str):
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_surrogate_load(self.h, str(path).encode()))
+        return self
+
 
 _contexts: dict[int, Context] = {}
 

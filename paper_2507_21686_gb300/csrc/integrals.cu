@@ -43,7 +43,9 @@ sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, v
                       c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "fixup count copy");
   c->stats.n_pairs = cl.P;
+  c->stats.n_fallback = 0;
   c->fixup_pending = true;
+  c->fallback_pending = false;
   return SPH2D_OK;
 }
 
@@ -63,6 +65,7 @@ sph2d_status launch_pair_integrals(Ctx* c, const double* pairs, int64_t P, int k
   c->stats = sph2d_stats{};
   c->stats.n_pairs = P;
   c->fixup_pending = true;
+  c->fallback_pending = false;
   return SPH2D_OK;
 }
 

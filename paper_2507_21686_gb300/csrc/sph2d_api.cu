@@ -196,7 +196,8 @@ sph2d_status sph2d_destroy(sph2d_ctx* h) {
   DevBuf* bufs[] = {&c.cell_start, &c.cell_cursor, &c.cell_tris, &c.block_tmp, &c.scan_tmp,
                     &c.pair_off,  &c.pair_tri,    &c.pair_pid,  &c.counts,    &c.slots,
                     &c.host_flags_dev, &c.misc, &c.tri_off, &c.tri_pid, &c.tri_cursor,
-                    &c.bwd_g, &c.bwd_grad};
+                    &c.bwd_g, &c.bwd_grad, &c.sur_prm, &c.sur_split, &c.sur_act,
+                    &c.sur_data, &c.sur_idx, &c.sur_vals, &c.sur_fb};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c.pinned) cudaFreeHost(c.pinned);
@@ -223,6 +224,12 @@ sph2d_status sph2d_last_stats(const sph2d_ctx* h, sph2d_stats* out) {
     if (e != cudaSuccess) return SPH2D_ERR_CUDA;
     out->n_fixup = c.pinned[8];
   }
+  if (c.fallback_pending) {
+    cudaSetDevice(c.device);
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return SPH2D_ERR_CUDA;
+    out->n_fallback = c.pinned[10];
+  }
   return SPH2D_OK;
 }
 
@@ -245,10 +252,15 @@ static sph2d_status check_outputs(Ctx* c, int kernel, int moment_degree, int mod
   if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
   if (moment_degree < -1 || moment_degree > 3)
     return set_err(c, SPH2D_ERR_INVALID_ARG, "moment_degree must be -1..3");
-  if (mode == SPH2D_SURROGATE)
-    return set_err(c, SPH2D_ERR_UNSUPPORTED, "surrogate mode goes through the sph2d_surrogate_* calls");
-  if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
+  if (mode == SPH2D_SURROGATE) {
+    if (moment_degree >= 0)
+      return set_err(c, SPH2D_ERR_UNSUPPORTED, "the surrogate provides gamma and grad gamma only");
+    if (!c->sur_ready) return set_err(c, SPH2D_ERR_NOT_BUILT, "surrogate not initialised");
+    if (kernel != c->sur_kernel)
+      return set_err(c, SPH2D_ERR_INVALID_ARG, "the surrogate was initialised for another kernel");
+  } else if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP) {
     return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown mode");
+  }
   if (N > 0 && !gamma) return set_err(c, SPH2D_ERR_INVALID_ARG, "gamma must not be NULL");
   if (moment_degree >= 0 && N > 0 && !moments)
     return set_err(c, SPH2D_ERR_INVALID_ARG, "moments must not be NULL when moment_degree >= 0");
@@ -309,6 +321,7 @@ sph2d_status sph2d_boundary_integrals(sph2d_ctx* h, const float* particles, int6
   cudaSetDevice(c->device);
   s = build_cells(c, particles, N, tris, M, H);
   if (s != SPH2D_OK) return s;
+  if (mode == SPH2D_SURROGATE) return surrogate_integrals(c, gamma, grad_gamma);
   return launch_integrals(c, kernel, moment_degree, mode, gamma, grad_gamma, moments);
 }
 
@@ -321,6 +334,7 @@ sph2d_status sph2d_integrals_from_pairs(sph2d_ctx* h, int kernel, int moment_deg
   sph2d_status s = check_outputs(c, kernel, moment_degree, mode, gamma, moments, c->cells.N);
   if (s != SPH2D_OK) return s;
   cudaSetDevice(c->device);
+  if (mode == SPH2D_SURROGATE) return surrogate_integrals(c, gamma, grad_gamma);
   return launch_integrals(c, kernel, moment_degree, mode, gamma, grad_gamma, moments);
 }
 
@@ -336,7 +350,7 @@ sph2d_status sph2d_pair_integrals(sph2d_ctx* h, const double* pairs, int64_t P, 
   if (moment_degree < -1 || moment_degree > 3)
     return set_err(c, SPH2D_ERR_INVALID_ARG, "moment_degree must be -1..3");
   if (mode == SPH2D_SURROGATE)
-    return set_err(c, SPH2D_ERR_UNSUPPORTED, "surrogate mode goes through the sph2d_surrogate_* calls");
+    return set_err(c, SPH2D_ERR_UNSUPPORTED, "independent pairs go through sph2d_surrogate_pairs");
   if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
     return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown mode");
   if (reinterpret_cast<uintptr_t>(pairs) & 7u)
@@ -367,6 +381,106 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* h, const float* partic
   s = build_cells(c, particles, N, tris, M, H);
   if (s != SPH2D_OK) return s;
   return launch_backward(c, kernel, mode, d_gamma, d_particles, d_tris);
+}
+
+// ---- learned surrogate -----------------------------------------------------------------
+static sph2d_status sur_ctx(sph2d_ctx* h, Ctx** out, bool need_ready) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  c->err.clear();
+  *out = c;
+  if (need_ready && !c->sur_ready) return set_err(c, SPH2D_ERR_NOT_BUILT, "surrogate not initialised");
+  cudaSetDevice(c->device);
+  return SPH2D_OK;
+}
+
+sph2d_status sph2d_surrogate_init(sph2d_ctx* h, int kernel, uint64_t seed) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, false);
+  if (s != SPH2D_OK) return s;
+  if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
+  return surrogate_init(c, kernel, seed);
+}
+
+sph2d_status sph2d_surrogate_train(sph2d_ctx* h, const double* pairs, int64_t P, double H, int epochs,
+                                   int batch, double lr, double weight_decay, uint64_t seed,
+                                   double* final_loss, int64_t* n_used) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (P <= 0 || P > (int64_t(1) << 31) - 1 || !pairs || (reinterpret_cast<uintptr_t>(pairs) & 7u))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "pairs must be a non-empty 8-byte aligned [P][8] array, P < 2^31");
+  if (!(H > 0.0) || !std::isfinite(H)) return set_err(c, SPH2D_ERR_INVALID_ARG, "H must be finite and > 0");
+  if (epochs < 0 || batch < 1 || batch > (1 << 20))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "epochs >= 0 and 1 <= batch <= 2^20 required");
+  if (!(lr > 0.0) || !std::isfinite(lr) || !(weight_decay >= 0.0) || !std::isfinite(weight_decay))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "lr > 0 and weight_decay >= 0 required");
+  return surrogate_train(c, pairs, P, H, epochs, batch, lr, weight_decay, seed, final_loss, n_used);
+}
+
+sph2d_status sph2d_surrogate_pairs(sph2d_ctx* h, const double* pairs, int64_t P, double H, float* out,
+                                   int32_t* accepted) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (P < 0) return set_err(c, SPH2D_ERR_INVALID_ARG, "P must be >= 0");
+  if (P > 0 && (!pairs || !out)) return set_err(c, SPH2D_ERR_INVALID_ARG, "null pointer");
+  if (reinterpret_cast<uintptr_t>(pairs) & 7u) return set_err(c, SPH2D_ERR_INVALID_ARG, "pairs must be 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(out) & 3u) return set_err(c, SPH2D_ERR_INVALID_ARG, "out must be 4-byte aligned");
+  if (!(H > 0.0) || !std::isfinite(H)) return set_err(c, SPH2D_ERR_INVALID_ARG, "H must be finite and > 0");
+  return surrogate_pairs(c, pairs, P, H, out, accepted);
+}
+
+sph2d_status sph2d_surrogate_forward(sph2d_ctx* h, const float* x, int64_t B, float* y) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (B < 0 || (B > 0 && (!x || !y))) return set_err(c, SPH2D_ERR_INVALID_ARG, "bad batch or null pointer");
+  return surrogate_forward(c, x, B, y);
+}
+
+sph2d_status sph2d_surrogate_grad(sph2d_ctx* h, const float* x, const float* t, int64_t B, float* grad,
+                                  float* loss) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (B < 1 || B > (1 << 20) || !x || !t || !grad || !loss)
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "1 <= B <= 2^20 and non-null pointers required");
+  return surrogate_grad(c, x, t, B, grad, loss);
+}
+
+sph2d_status sph2d_surrogate_get_params(sph2d_ctx* h, float* host, int64_t cap) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (!host) return set_err(c, SPH2D_ERR_INVALID_ARG, "null pointer");
+  if (cap < SPH2D_SURROGATE_PARAMS) return set_err(c, SPH2D_ERR_CAPACITY, "buffer smaller than SPH2D_SURROGATE_PARAMS");
+  return surrogate_get_params(c, host);
+}
+
+sph2d_status sph2d_surrogate_set_params(sph2d_ctx* h, const float* host, int64_t n) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (!host || n != SPH2D_SURROGATE_PARAMS)
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "expected SPH2D_SURROGATE_PARAMS host floats");
+  return surrogate_set_params(c, host);
+}
+
+sph2d_status sph2d_surrogate_save(sph2d_ctx* h, const char* path) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, true);
+  if (s != SPH2D_OK) return s;
+  if (!path) return set_err(c, SPH2D_ERR_INVALID_ARG, "null path");
+  return surrogate_save(c, path);
+}
+
+sph2d_status sph2d_surrogate_load(sph2d_ctx* h, const char* path) {
+  Ctx* c;
+  sph2d_status s = sur_ctx(h, &c, false);
+  if (s != SPH2D_OK) return s;
+  if (!path) return set_err(c, SPH2D_ERR_INVALID_ARG, "null path");
+  return surrogate_load(c, path);
 }
 
 }  // extern "C"

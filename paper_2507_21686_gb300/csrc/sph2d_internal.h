@@ -40,9 +40,16 @@ struct Ctx {
   // scratch buffers (named slots)
   DevBuf cell_start, cell_cursor, cell_tris, block_tmp, scan_tmp, pair_off, pair_tri, pair_pid,
       counts, slots, host_flags_dev, misc, tri_off, tri_pid, tri_cursor, bwd_g, bwd_grad;
+  // learned surrogate: parameters (+ Adam state), training data and scratch, serving scratch
+  DevBuf sur_prm, sur_split, sur_act, sur_data, sur_idx, sur_vals, sur_fb;
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
   bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
+  bool fallback_pending = false;  // pinned[10] holds the fallback count of the last surrogate call
   int64_t launches = 0;        // kernels launched by this context (cumulative)
+  bool sur_ready = false;      // surrogate parameters initialised
+  int sur_kernel = -1;         // kernel the surrogate is trained for
+  int64_t sur_step = 0;        // optimiser steps taken
+  float sur_w[3] = {1.0f, 1.0f, 1.0f};   // per-output loss weights
 };
 
 // error helpers ------------------------------------------------------------------------
@@ -71,6 +78,19 @@ sph2d_status launch_pair_integrals(Ctx* c, const double* pairs, int64_t P, int k
 // adjoint (backward.cu)
 sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma,
                              void* d_particles, void* d_tris);
+
+// learned surrogate (surrogate.cu); callers validate arguments and sur_ready
+sph2d_status surrogate_init(Ctx* c, int kernel, uint64_t seed);
+sph2d_status surrogate_train(Ctx* c, const double* pairs, int64_t P, double H, int epochs, int batch,
+                             double lr, double wd, uint64_t seed, double* final_loss, int64_t* used);
+sph2d_status surrogate_pairs(Ctx* c, const double* pairs, int64_t P, double H, float* out, int32_t* accepted);
+sph2d_status surrogate_integrals(Ctx* c, void* gamma, void* grad);
+sph2d_status surrogate_forward(Ctx* c, const float* X, int64_t B, float* Y);
+sph2d_status surrogate_grad(Ctx* c, const float* X, const float* T, int64_t B, float* grad, float* loss);
+sph2d_status surrogate_set_params(Ctx* c, const float* host);
+sph2d_status surrogate_get_params(Ctx* c, float* host);
+sph2d_status surrogate_save(Ctx* c, const char* path);
+sph2d_status surrogate_load(Ctx* c, const char* path);
 
 inline int num_moments(int deg) { return deg < 0 ? 0 : (deg + 1) * (deg + 2) / 2; }
 

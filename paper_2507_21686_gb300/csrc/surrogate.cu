@@ -1,0 +1,935 @@
+// Learned surrogate: BF16 tensor-core (mma.sync m16n8k16, FP32 accumulation) training and
+// inference of the 6-64-64-64-3 MLP of surrogate.cuh, with the guarded analytic fallback.
+// This part has no counterpart in the paper.
+//
+// Training runs entirely in this file's kernels: canonicalisation of analytic training pairs,
+// per-step forward (GEMM + bias + GELU), loss gradient, backward (GEMMs for activation and
+// weight gradients, GELU derivative, bias column sums), AdamW on FP32 master weights.  Weight
+// gradients reduce over the batch with split-K partials summed in a fixed order, so a
+// training run is reproducible bit for bit.
+//
+// Serving, three kernels:
+//   values   one warp per 32 pairs: every lane canonicalises its pair and applies the guard;
+//            the 32 rows go through the network as two m16 tiles with the layer outputs kept
+//            in registers and fed back as the next layer's A operand (the accumulator fragment
+//            of two adjacent n8 tiles is exactly the A fragment of one k16 step).  Accepted
+//            pairs write their value; rejected pairs are appended to a fallback list (one
+//            atomic per warp).
+//   fallback the analytic FP32 path (with its FP64 fix-up) over the compacted list, so a
+//            warp's lanes all do analytic work instead of idling beside network lanes.
+//   reduce   per-particle sums over the per-pair values in pair order (the same 32-pair
+//            chunk reduction and crossing slots as the analytic kernel), so the result does
+//            not depend on the order in which the list was filled.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "integrals_impl.cuh"
+#include "surrogate.cuh"
+
+namespace sph2d {
+
+static_assert(kSurParams == SPH2D_SURROGATE_PARAMS, "parameter count differs from the header");
+static_assert(kSurMinSize == float(SPH2D_SURROGATE_MIN_SIZE) && kSurMaxSize == float(SPH2D_SURROGATE_MAX_SIZE) &&
+                  kSurMinCentroid == float(SPH2D_SURROGATE_MIN_CENTROID) &&
+                  kSurMaxRadius == float(SPH2D_SURROGATE_MAX_RADIUS),
+              "guard constants differ from the header");
+
+// ---------------------------------------------------------------------------------------
+// generic GEMM: C[M][N] = alpha * op(A) op(B)   (FP32 in/out, BF16 operands, FP32 accumulate)
+//   op(A) is M x K: ta=0 -> A[m*lda + k], ta=1 -> A[k*lda + m]
+//   op(B) is K x N: tb=0 -> B[n*ldb + k],  tb=1 -> B[k*ldb + n]
+// Block tile 64 x 64 x 32, 4 warps of 32 x 32.  blockIdx.z splits K; with ksplit > 1 each
+// split writes its own partial (M x N, row stride N) at C + z * M * N.
+// ---------------------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                        int lda, int ta, const float* __restrict__ B, int ldb,
+                                                        int tb, float* __restrict__ C, int ldc, float alpha,
+                                                        int ksplit) {
+  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+  const int kper = (K + ksplit - 1) / ksplit;
+  const int kbeg = blockIdx.z * kper, kend = min(K, kbeg + kper);
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+    for (int i = 0; i < (GBM * GBK) / 128; ++i) {
+      const int e = tid + 128 * i;
+      int m, k;
+      if (!ta) { m = e / GBK; k = e % GBK; } else { k = e / GBM; m = e % GBM; }
+      const int gm = m0 + m, gk = k0 + k;
+      float v = 0.0f;
+      if (gm < M && gk < kend) v = ta ? A[size_t(gk) * lda + gm] : A[size_t(gm) * lda + gk];
+      As[m][k] = __float2bfloat16_rn(v);
+    }
+#pragma unroll
+    for (int i = 0; i < (GBN * GBK) / 128; ++i) {
+      const int e = tid + 128 * i;
+      int n, k;
+      if (!tb) { n = e / GBK; k = e % GBK; } else { k = e / GBN; n = e % GBN; }
+      const int gn = n0 + n, gk = k0 + k;
+      float v = 0.0f;
+      if (gn < N && gk < kend) v = tb ? B[size_t(gk) * ldb + gn] : B[size_t(gn) * ldb + gk];
+      Bs[n][k] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < GBK; ks += 16) {
+      uint32_t af[2][4], bf[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + g;
+        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * t]);
+        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * t]);
+        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * t + 8]);
+        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cn = wn + j * 8 + g;
+        bf[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[cn][ks + 2 * t]);
+        bf[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[cn][ks + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bf[j]);
+    }
+    __syncthreads();
+  }
+  float* Cz = ksplit > 1 ? C + size_t(blockIdx.z) * M * N : C;
+  const int ld = ksplit > 1 ? N : ldc;
+  const float sc = ksplit > 1 ? 1.0f : alpha;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gm = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
+        const int gn = n0 + wn + j * 8 + 2 * t + (r & 1);
+        if (gm < M && gn < N) Cz[size_t(gm) * ld + gn] = sc * acc[i][j][r];
+      }
+}
+
+// sum of split-K partials in split order (deterministic); C[m*ldc + n] = alpha * sum
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, int M, int N,
+                                     float* __restrict__ C, int ldc, float alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  float s = 0.0f;
+  for (int z = 0; z < splits; ++z) s += part[size_t(z) * M * N + i];
+  C[size_t(i / N) * ldc + (i % N)] = alpha * s;
+}
+
+// ---------------------------------------------------------------------------------------
+// elementwise kernels of the training step
+// ---------------------------------------------------------------------------------------
+// Z += b (row broadcast); Hh = GELU(Z) if act, else Hh = Z (Hh may alias Z only when !act)
+__global__ void bias_act_kernel(float* Z, const float* __restrict__ b, float* Hh, int64_t rows, int n, int act) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= rows * n) return;
+  const float z = Z[i] + b[i % n];
+  Z[i] = z;
+  Hh[i] = act ? gelu_f(z) : z;
+}
+
+__global__ void gelu_back_kernel(float* __restrict__ dH, const float* __restrict__ Z, int64_t count) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < count) dH[i] *= gelu_grad_f(Z[i]);
+}
+
+// loss = (1/B) sum_rows sum_c w_c (Y - T)^2; dY = 2 w_c (Y - T) / B; per-block partial sums
+__global__ void loss_grad_kernel(const float* __restrict__ Y, const float* __restrict__ T, int64_t rows,
+                                 float w0, float w1, float w2, float* __restrict__ dY,
+                                 float* __restrict__ partial) {
+  __shared__ float red[256];
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (i < rows * 3) {
+    const int c = int(i % 3);
+    const float w = c == 0 ? w0 : (c == 1 ? w1 : w2);
+    const float d = Y[i] - T[i];
+    dY[i] = 2.0f * w * d / float(rows);
+    l = w * d * d / float(rows);
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_kernel(const float* __restrict__ x, int n, float* __restrict__ out) {
+  __shared__ float red[256];
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// column sums of dZ [rows][n] -> db [n], one block per column, fixed tree order
+__global__ void colsum_kernel(const float* __restrict__ dZ, int64_t rows, int n, float* __restrict__ db) {
+  __shared__ float red[256];
+  const int c = blockIdx.x;
+  float s = 0.0f;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += dZ[r * n + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] = red[0];
+}
+
+// AdamW (decoupled weight decay) on the FP32 masters
+__global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                             float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float wd,
+                             float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] = p[i] * (1.0f - lr * wd) - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ X, const float* __restrict__ T,
+                                   const int32_t* __restrict__ idx, int64_t rows, float* __restrict__ Xb,
+                                   float* __restrict__ Tb) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int64_t s = idx[r];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) Xb[r * 6 + j] = X[s * 6 + j];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Tb[r * 3 + j] = T[s * 3 + j];
+}
+
+// local frame of an independent pair [x, y, v0x, v0y, v1x, v1y, v2x, v2y] (double and float)
+__device__ __forceinline__ void pair_local(const double* q, double invH, double* ld, float* lf) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    ld[2 * j] = (q[2 + 2 * j] - q[0]) * invH;
+    ld[2 * j + 1] = (q[3 + 2 * j] - q[1]) * invH;
+    lf[2 * j] = float(ld[2 * j]);
+    lf[2 * j + 1] = float(ld[2 * j + 1]);
+  }
+}
+
+// training data: analytic (gamma, grad) [P][3] in world units for pairs [P][8] -> canonical
+// inputs X [P][6], targets T [P][3] = (gamma, canonical local-frame grad) / area, guard flags
+__global__ void canon_training_kernel(const double* __restrict__ pairs, const double* __restrict__ ana,
+                                      int64_t P, double invH, double H, float* __restrict__ X,
+                                      float* __restrict__ T, int32_t* __restrict__ ok) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  double ld[6];
+  float v[6];
+  pair_local(pairs + 8 * i, invH, ld, v);
+  const Canon c = canonicalize(v);
+  const double* a = ana + 3 * i;
+  // local-frame gradient = H * world gradient; rotate (then reflect) into the canonical frame
+  const float gx = float(a[1] * H), gy = float(a[2] * H);
+  const float gxc = c.cs * gx + c.sn * gy;
+  const float gyc = c.refl * (-c.sn * gx + c.cs * gy);
+  const float ia = c.area > 0.0f ? 1.0f / c.area : 0.0f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) X[6 * i + j] = c.x[j];
+  T[3 * i] = float(a[0]) * ia;
+  T[3 * i + 1] = gxc * ia;
+  T[3 * i + 2] = gyc * ia;
+  ok[i] = c.accept ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// inference: the network on register-resident fragments
+// ---------------------------------------------------------------------------------------
+constexpr int kW1Stride = kSurK1 + 8;     // padded bf16 row strides (conflict-free fragments)
+constexpr int kWStride = kSurHid + 8;
+constexpr int kXStride = kSurK1 + 8;
+struct SurSmem {
+  __nv_bfloat16 w1[kSurHid][kW1Stride];
+  __nv_bfloat16 w2[kSurHid][kWStride];
+  __nv_bfloat16 w3[kSurHid][kWStride];
+  __nv_bfloat16 w4[kSurN4][kWStride];
+  float b1[kSurHid], b2[kSurHid], b3[kSurHid], b4[kSurN4];
+  __nv_bfloat16 xin[4][32][kXStride];      // per-warp staged inputs
+  float yout[4][32][kSurN4];               // per-warp outputs
+};
+
+__device__ void load_sur_weights(SurSmem& s, const float* __restrict__ prm) {
+  for (int i = threadIdx.x; i < kSurHid * kW1Stride; i += blockDim.x) {
+    const int n = i / kW1Stride, k = i % kW1Stride;
+    s.w1[n][k] = __float2bfloat16_rn(k < kSurIn ? prm[kOffW1 + n * kSurIn + k] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < kSurHid * kWStride; i += blockDim.x) {
+    const int n = i / kWStride, k = i % kWStride;
+    s.w2[n][k] = __float2bfloat16_rn(k < kSurHid ? prm[kOffW2 + n * kSurHid + k] : 0.0f);
+    s.w3[n][k] = __float2bfloat16_rn(k < kSurHid ? prm[kOffW3 + n * kSurHid + k] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < kSurN4 * kWStride; i += blockDim.x) {
+    const int n = i / kWStride, k = i % kWStride;
+    s.w4[n][k] = __float2bfloat16_rn(n < kSurOut && k < kSurHid ? prm[kOffW4 + n * kSurHid + k] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < kSurHid; i += blockDim.x) {
+    s.b1[i] = prm[kOffB1 + i];
+    s.b2[i] = prm[kOffB2 + i];
+    s.b3[i] = prm[kOffB3 + i];
+  }
+  for (int i = threadIdx.x; i < kSurN4; i += blockDim.x) s.b4[i] = i < kSurOut ? prm[kOffB4 + i] : 0.0f;
+}
+
+// one layer on a 16-row tile: A fragments a[KBLOCKS][4] in, acc[NTILES][4] = bias + a W^T
+template <int KBLOCKS, int WSTRIDE, int NTILES>
+__device__ __forceinline__ void layer_mma(const __nv_bfloat16 (*w)[WSTRIDE], const float* b, const uint32_t (*a)[4],
+                                          float (*acc)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < NTILES; ++j) {
+    const float bx = b[j * 8 + 2 * t], by = b[j * 8 + 2 * t + 1];
+    acc[j][0] = bx;
+    acc[j][1] = by;
+    acc[j][2] = bx;
+    acc[j][3] = by;
+#pragma unroll
+    for (int kb = 0; kb < KBLOCKS; ++kb) {
+      uint32_t bf[2];
+      bf[0] = *reinterpret_cast<const uint32_t*>(&w[j * 8 + g][kb * 16 + 2 * t]);
+      bf[1] = *reinterpret_cast<const uint32_t*>(&w[j * 8 + g][kb * 16 + 2 * t + 8]);
+      mma_bf16_16816(acc[j], a[kb], bf);
+    }
+  }
+}
+
+// GELU on the accumulators, repacked as the next layer's A fragments (k16 block kb takes the
+// n8 tiles 2kb and 2kb+1)
+__device__ __forceinline__ void act_to_a(const float (*acc)[4], uint32_t (*a)[4]) {
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb) {
+    a[kb][0] = pack_bf16(gelu_f(acc[2 * kb][0]), gelu_f(acc[2 * kb][1]));
+    a[kb][1] = pack_bf16(gelu_f(acc[2 * kb][2]), gelu_f(acc[2 * kb][3]));
+    a[kb][2] = pack_bf16(gelu_f(acc[2 * kb + 1][0]), gelu_f(acc[2 * kb + 1][1]));
+    a[kb][3] = pack_bf16(gelu_f(acc[2 * kb + 1][2]), gelu_f(acc[2 * kb + 1][3]));
+  }
+}
+
+// the network on the warp's 32 staged rows (xin -> yout).  All 32 lanes must call it.
+__device__ void mlp_warp32(SurSmem& s, int warp) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const __nv_bfloat16 (*xin)[kXStride] = s.xin[warp];
+  float (*yout)[kSurN4] = s.yout[warp];
+#pragma unroll 1
+  for (int tile = 0; tile < 2; ++tile) {
+    const int r0 = tile * 16;
+    uint32_t a[4][4];
+    a[0][0] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g][2 * t]);
+    a[0][1] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g + 8][2 * t]);
+    a[0][2] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g][2 * t + 8]);
+    a[0][3] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g + 8][2 * t + 8]);
+    float acc[8][4];
+    layer_mma<1, kW1Stride, 8>(s.w1, s.b1, a, acc);
+    act_to_a(acc, a);
+    layer_mma<4, kWStride, 8>(s.w2, s.b2, a, acc);
+    act_to_a(acc, a);
+    layer_mma<4, kWStride, 8>(s.w3, s.b3, a, acc);
+    act_to_a(acc, a);
+    layer_mma<4, kWStride, 1>(s.w4, s.b4, a, acc);
+    yout[r0 + g][2 * t] = acc[0][0];
+    yout[r0 + g][2 * t + 1] = acc[0][1];
+    yout[r0 + g + 8][2 * t] = acc[0][2];
+    yout[r0 + g + 8][2 * t + 1] = acc[0][3];
+  }
+  __syncwarp();
+}
+
+// stage one lane's canonical input row (zeros when the lane has no accepted pair)
+__device__ __forceinline__ void stage_row(SurSmem& s, int warp, int lane, const float* x, bool use) {
+  __nv_bfloat16* row = s.xin[warp][lane];
+#pragma unroll
+  for (int j = 0; j < kSurK1; j += 2) {
+    const float lo = (j < kSurIn && use) ? x[j] : 0.0f;
+    const float hi = (j + 1 < kSurIn && use) ? x[j + 1] : 0.0f;
+    *reinterpret_cast<uint32_t*>(row + j) = pack_bf16(lo, hi);
+  }
+}
+
+// raw network on canonical inputs X [B][6] -> Y [B][3] (tests and diagnostics)
+__global__ void __launch_bounds__(128) surrogate_forward_kernel(const float* __restrict__ prm,
+                                                                const float* __restrict__ X, int64_t B,
+                                                                float* __restrict__ Y) {
+  __shared__ __align__(16) SurSmem s;
+  load_sur_weights(s, prm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nch = (B + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += nw) {
+    const int64_t i = ch * 32 + lane;
+    float x[6] = {0, 0, 0, 0, 0, 0};
+    if (i < B) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) x[j] = X[6 * i + j];
+    }
+    stage_row(s, warp, lane, x, i < B);
+    __syncwarp();
+    mlp_warp32(s, warp);
+    if (i < B) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Y[3 * i + j] = s.yout[warp][lane][j];
+    }
+    __syncwarp();
+  }
+}
+
+struct SurArgs {
+  const float* prm;               // FP32 master parameters
+  double C, H, invH;
+  float* vals;                    // per-pair (gamma, dgamma/dx, dgamma/dy), world units [P][3]
+  int32_t* accepted;              // optional per-pair guard result [P]
+  int64_t* fb_list;               // fallback pair indices (capacity P)
+  unsigned long long* fb_count;   // number of entries in fb_list
+};
+
+// per-pair FP32 local frame for the two pair sources: independent pairs (double [P][8]) or
+// the culled pair list (FP32 particles and triangles, same arithmetic as the analytic kernel)
+template <bool LIST>
+__device__ __forceinline__ void load_local(const IntArgs& a, const double* pairs, int64_t q, float* lf) {
+  if (LIST) {
+    const float4 p = a.parts[__ldg(a.pair_pid + q)];
+    const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
+    const float ih = float(a.invH);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+      lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+    }
+  } else {
+    double ld[6];
+    pair_local(pairs + 8 * q, a.invH, ld, lf);
+  }
+}
+
+template <int KID, bool LIST>
+__global__ void __launch_bounds__(128) surrogate_values_kernel(IntArgs a, const double* __restrict__ pairs,
+                                                               SurArgs sa) {
+  __shared__ __align__(16) SurSmem s;
+  load_sur_weights(s, sa.prm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nch = (a.P + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const float ih = float(a.invH);
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += nw) {
+    const int64_t q = ch * 32 + lane;
+    float lf[6] = {0, 0, 0, 0, 0, 0};
+    if (q < a.P) load_local<LIST>(a, pairs, q, lf);
+    const Canon c = canonicalize(lf);
+    const bool use = (q < a.P) && c.accept;
+    stage_row(s, warp, lane, c.x, use);
+    __syncwarp();
+    mlp_warp32(s, warp);
+    if (use) {
+      const float* y = s.yout[warp][lane];
+      float lx, ly;
+      uncanonicalize_grad(c, c.area * y[1], c.area * y[2], lx, ly);
+      sa.vals[3 * q] = c.area * y[0];
+      sa.vals[3 * q + 1] = lx * ih;
+      sa.vals[3 * q + 2] = ly * ih;
+    }
+    if (sa.accepted && q < a.P) sa.accepted[q] = use ? 1 : 0;
+    // append the rejected pairs to the fallback list, one atomic per warp
+    const unsigned rej = __ballot_sync(0xffffffffu, (q < a.P) && !use);
+    if (rej) {
+      unsigned long long base = 0;
+      const int leader = __ffs(rej) - 1;
+      if (lane == leader) base = atomicAdd(sa.fb_count, (unsigned long long)__popc(rej));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if ((q < a.P) && !use) sa.fb_list[base + __popc(rej & ((1u << lane) - 1u))] = q;
+    }
+    __syncwarp();
+  }
+}
+
+// analytic FP32 path (with the FP64 fix-up for far or non-finite geometry) over the list
+template <int KID, bool LIST>
+__global__ void __launch_bounds__(128) surrogate_fallback_kernel(IntArgs a, const double* __restrict__ pairs,
+                                                                 SurArgs sa) {
+  const int64_t n = int64_t(*sa.fb_count);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t q = sa.fb_list[i];
+    float v[3];
+    if (LIST) {
+      eval_pair<float, KID, false>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
+    } else {
+      double ld[6];
+      float lf[6];
+      pair_local(pairs + 8 * q, a.invH, ld, lf);
+      eval_mode<float, KID, false>(ld, a.C, a.invH, v);
+    }
+    sa.vals[3 * q] = v[0];
+    sa.vals[3 * q + 1] = v[1];
+    sa.vals[3 * q + 2] = v[2];
+  }
+}
+
+// per-particle sums of the per-pair values in pair order (chunk reduction + crossing slots,
+// completed by finalize_kernel)
+__global__ void __launch_bounds__(128) reduce_vals_kernel(IntArgs a, const float* __restrict__ vals) {
+  constexpr int NV = 3;
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+    const int64_t q = ch * 32 + lane;
+    int pid = -1;
+    float v[NV] = {0.0f, 0.0f, 0.0f};
+    if (q < a.P) {
+      pid = __ldg(a.pair_pid + q);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = vals[3 * q + i];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int pn = __shfl_down_sync(0xffffffffu, pid, o);
+      const bool same = (lane + o < 32) && (pn == pid);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const float tv = __shfl_down_sync(0xffffffffu, v[i], o);
+        if (same) v[i] += tv;
+      }
+    }
+    const int pprev = __shfl_up_sync(0xffffffffu, pid, 1);
+    const bool head = pid >= 0 && (lane == 0 || pprev != pid);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int last_head = 31 - __clz(heads);
+    if (head) {
+      const int64_t cs = ch * 32;
+      const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
+      if (s0 >= cs && s1 <= cs + 32) write_particle<float, false>(a, pid, v);
+      float* slots = static_cast<float*>(a.slots);
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) slots[(ch * 2) * NV + i] = v[i];
+      }
+      if (lane == last_head) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) slots[(ch * 2 + 1) * NV + i] = v[i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+static unsigned nblk(int64_t n, int b = 256) { return unsigned((n + b - 1) / b); }
+
+// occupancy-limited persistent grid of 128-thread blocks, no larger than the work needs
+template <typename K>
+static unsigned persistent_grid(Ctx* c, K kern, int64_t blocks_wanted) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  const int64_t want = blocks_wanted > 0 ? blocks_wanted : 1;
+  return unsigned(want < cap ? want : cap);
+}
+
+static sph2d_status gemm(Ctx* c, int M, int N, int K, const float* A, int lda, int ta, const float* B,
+                         int ldb, int tb, float* C, int ldc) {
+  // split K when the output tile grid is small and K is long (weight gradients over the batch)
+  const int tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+  int splits = 1;
+  if (K >= 4096 && tiles < 64) splits = std::min(64, K / 1024);
+  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, splits);
+  if (splits == 1) {
+    SPH2D_LAUNCH(c, (gemm_bf16_kernel), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0f, 1);
+    return SPH2D_OK;
+  }
+  sph2d_status s = ensure(c, c->sur_split, size_t(splits) * M * N * sizeof(float));
+  if (s != SPH2D_OK) return s;
+  float* part = static_cast<float*>(c->sur_split.ptr);
+  SPH2D_LAUNCH(c, (gemm_bf16_kernel), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, part, N, 1.0f, splits);
+  SPH2D_LAUNCH(c, (splitk_reduce_kernel), nblk(int64_t(M) * N), 256, part, splits, M, N, C, ldc, 1.0f);
+  return SPH2D_OK;
+}
+
+// one forward + backward over a batch (Xb [B][6], Tb [B][3]) -> grad (flat parameter layout)
+// and the batch loss (device scalar)
+static sph2d_status sur_grad_batch(Ctx* c, const float* prm, const float* Xb, const float* Tb, int64_t B,
+                                   float* grad, float* loss_dev) {
+  const int Hd = kSurHid;
+  const int64_t lb = (B * 3 + 255) / 256;
+  sph2d_status s = ensure(c, c->sur_act, size_t(B * (6 * Hd + 6) + lb) * sizeof(float));
+  if (s != SPH2D_OK) return s;
+  float* base = static_cast<float*>(c->sur_act.ptr);
+  float *Z1 = base, *H1 = Z1 + B * Hd, *Z2 = H1 + B * Hd, *H2 = Z2 + B * Hd, *Z3 = H2 + B * Hd;
+  float *H3 = Z3 + B * Hd, *Y = H3 + B * Hd, *dY = Y + B * 3, *part = dY + B * 3;
+  const int iB = int(B);
+#define SUR_GEMM(...)                                      \
+  do {                                                     \
+    if ((s = gemm(c, __VA_ARGS__)) != SPH2D_OK) return s;  \
+  } while (0)
+  // forward: Z = H_prev W^T + b, H = GELU(Z)
+  SUR_GEMM(iB, Hd, kSurIn, Xb, kSurIn, 0, prm + kOffW1, kSurIn, 0, Z1, Hd);
+  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * Hd), 256, Z1, prm + kOffB1, H1, B, Hd, 1);
+  SUR_GEMM(iB, Hd, Hd, H1, Hd, 0, prm + kOffW2, Hd, 0, Z2, Hd);
+  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * Hd), 256, Z2, prm + kOffB2, H2, B, Hd, 1);
+  SUR_GEMM(iB, Hd, Hd, H2, Hd, 0, prm + kOffW3, Hd, 0, Z3, Hd);
+  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * Hd), 256, Z3, prm + kOffB3, H3, B, Hd, 1);
+  SUR_GEMM(iB, kSurOut, Hd, H3, Hd, 0, prm + kOffW4, Hd, 0, Y, kSurOut);
+  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * 3), 256, Y, prm + kOffB4, Y, B, kSurOut, 0);
+  SPH2D_LAUNCH(c, (loss_grad_kernel), unsigned(lb), 256, Y, Tb, B, c->sur_w[0], c->sur_w[1], c->sur_w[2], dY,
+               part);
+  SPH2D_LAUNCH(c, (sum_kernel), 1, 256, part, int(lb), loss_dev);
+  // backward.  dW = dZ^T H_prev, db = column sums of dZ, dH_prev = dZ W; each dZ overwrites a
+  // buffer whose last reader has run: dZ3 -> H3, dZ2 -> Z3, dZ1 -> Z2.
+  SUR_GEMM(kSurOut, Hd, iB, dY, kSurOut, 1, H3, Hd, 1, grad + kOffW4, Hd);
+  SPH2D_LAUNCH(c, (colsum_kernel), kSurOut, 256, dY, B, kSurOut, grad + kOffB4);
+  float* dZ3 = H3;
+  SUR_GEMM(iB, Hd, kSurOut, dY, kSurOut, 0, prm + kOffW4, Hd, 1, dZ3, Hd);
+  SPH2D_LAUNCH(c, (gelu_back_kernel), nblk(B * Hd), 256, dZ3, Z3, B * Hd);
+  SUR_GEMM(Hd, Hd, iB, dZ3, Hd, 1, H2, Hd, 1, grad + kOffW3, Hd);
+  SPH2D_LAUNCH(c, (colsum_kernel), Hd, 256, dZ3, B, Hd, grad + kOffB3);
+  float* dZ2 = Z3;
+  SUR_GEMM(iB, Hd, Hd, dZ3, Hd, 0, prm + kOffW3, Hd, 1, dZ2, Hd);
+  SPH2D_LAUNCH(c, (gelu_back_kernel), nblk(B * Hd), 256, dZ2, Z2, B * Hd);
+  SUR_GEMM(Hd, Hd, iB, dZ2, Hd, 1, H1, Hd, 1, grad + kOffW2, Hd);
+  SPH2D_LAUNCH(c, (colsum_kernel), Hd, 256, dZ2, B, Hd, grad + kOffB2);
+  float* dZ1 = Z2;
+  SUR_GEMM(iB, Hd, Hd, dZ2, Hd, 0, prm + kOffW2, Hd, 1, dZ1, Hd);
+  SPH2D_LAUNCH(c, (gelu_back_kernel), nblk(B * Hd), 256, dZ1, Z1, B * Hd);
+  SUR_GEMM(Hd, kSurIn, iB, dZ1, Hd, 1, Xb, kSurIn, 1, grad + kOffW1, kSurIn);
+  SPH2D_LAUNCH(c, (colsum_kernel), Hd, 256, dZ1, B, Hd, grad + kOffB1);
+#undef SUR_GEMM
+  return SPH2D_OK;
+}
+
+// deterministic Glorot-uniform initialisation (host generator), biases zero
+static void init_params(std::vector<float>& p, uint64_t seed) {
+  std::mt19937_64 rng(seed);
+  p.assign(kSurParams, 0.0f);
+  auto fill = [&](int off, int fan_out, int fan_in) {
+    const double lim = std::sqrt(6.0 / double(fan_in + fan_out));
+    for (int i = 0; i < fan_out * fan_in; ++i) {
+      const double u = double(rng() >> 11) * (1.0 / 9007199254740992.0);   // [0, 1)
+      p[off + i] = float((2.0 * u - 1.0) * lim);
+    }
+  };
+  fill(kOffW1, kSurHid, kSurIn);
+  fill(kOffW2, kSurHid, kSurHid);
+  fill(kOffW3, kSurHid, kSurHid);
+  fill(kOffW4, kSurOut, kSurHid);
+}
+
+sph2d_status surrogate_init(Ctx* c, int kernel, uint64_t seed) {
+  // masters, Adam first and second moments, one spare block
+  sph2d_status s = ensure(c, c->sur_prm, 4 * size_t(kSurParams) * sizeof(float));
+  if (s != SPH2D_OK) return s;
+  std::vector<float> p;
+  init_params(p, seed);
+  float* prm = static_cast<float*>(c->sur_prm.ptr);
+  cudaError_t e = cudaMemcpyAsync(prm, p.data(), kSurParams * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(prm + kSurParams, 0, 3 * size_t(kSurParams) * sizeof(float), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate init");
+  c->sur_kernel = kernel;
+  c->sur_ready = true;
+  c->sur_step = 0;
+  // loss weights 1/scale^2: the averaged kernel is at most C, the averaged gradient about 2C
+  const double C = kernel_C(kernel);
+  c->sur_w[0] = float(1.0 / (C * C));
+  c->sur_w[1] = c->sur_w[2] = float(1.0 / (4.0 * C * C));
+  return SPH2D_OK;
+}
+
+sph2d_status surrogate_set_params(Ctx* c, const float* host) {
+  cudaError_t e = cudaMemcpyAsync(c->sur_prm.ptr, host, kSurParams * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate params");
+  return SPH2D_OK;
+}
+
+sph2d_status surrogate_get_params(Ctx* c, float* host) {
+  cudaError_t e = cudaMemcpyAsync(host, c->sur_prm.ptr, kSurParams * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate params");
+  return SPH2D_OK;
+}
+
+sph2d_status surrogate_grad(Ctx* c, const float* X, const float* T, int64_t B, float* grad, float* loss) {
+  return sur_grad_batch(c, static_cast<const float*>(c->sur_prm.ptr), X, T, B, grad, loss);
+}
+
+sph2d_status surrogate_forward(Ctx* c, const float* X, int64_t B, float* Y) {
+  if (B == 0) return SPH2D_OK;
+  const unsigned g = persistent_grid(c, surrogate_forward_kernel, ((B + 31) / 32 + 3) / 4);
+  SPH2D_LAUNCH(c, (surrogate_forward_kernel), g, 128, static_cast<const float*>(c->sur_prm.ptr), X, B, Y);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate forward");
+  return SPH2D_OK;
+}
+
+sph2d_status surrogate_train(Ctx* c, const double* pairs, int64_t P, double H, int epochs, int batch,
+                             double lr, double wd, uint64_t seed, double* final_loss, int64_t* used) {
+  cudaStream_t st = c->stream;
+  // analytic labels in FP64: the closed form is the ground truth the network learns
+  sph2d_status s = ensure(c, c->sur_data, size_t(P) * (3 * sizeof(double) + 9 * sizeof(float) + sizeof(int32_t)));
+  if (s != SPH2D_OK) return s;
+  double* ana = static_cast<double*>(c->sur_data.ptr);
+  float* X = reinterpret_cast<float*>(ana + 3 * P);
+  float* T = X + 6 * P;
+  int32_t* ok = reinterpret_cast<int32_t*>(T + 3 * P);
+  s = launch_pair_integrals(c, pairs, P, c->sur_kernel, H, -1, SPH2D_FP64, ana);
+  if (s != SPH2D_OK) return s;
+  SPH2D_LAUNCH(c, (canon_training_kernel), nblk(P), 256, pairs, ana, P, 1.0 / H, H, X, T, ok);
+  // keep the rows inside the guard's domain
+  std::vector<int32_t> okh(P);
+  cudaError_t e = cudaMemcpyAsync(okh.data(), ok, P * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(c, e, "training labels");
+  std::vector<int32_t> rows;
+  rows.reserve(P);
+  for (int64_t i = 0; i < P; ++i)
+    if (okh[i]) rows.push_back(int32_t(i));
+  const int64_t R = int64_t(rows.size());
+  if (used) *used = R;
+  if (R < batch) return set_err(c, SPH2D_ERR_INVALID_ARG, "fewer in-domain training pairs than one batch");
+  s = ensure(c, c->sur_idx, size_t(R) * sizeof(int32_t) + size_t(batch) * 9 * sizeof(float) +
+                                size_t(kSurParams + 64) * sizeof(float));
+  if (s != SPH2D_OK) return s;
+  int32_t* idx = static_cast<int32_t*>(c->sur_idx.ptr);
+  float* Xb = reinterpret_cast<float*>(idx + R);
+  float* Tb = Xb + size_t(batch) * 6;
+  float* grad = Tb + size_t(batch) * 3;
+  float* loss = grad + kSurParams;
+  float* prm = static_cast<float*>(c->sur_prm.ptr);
+  float *m = prm + kSurParams, *v = m + kSurParams;
+  std::mt19937_64 rng(seed);
+  const int64_t steps_per = R / batch;
+  const int64_t total = steps_per * epochs;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  int64_t step = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    // Fisher-Yates with the context's own generator (identical on every platform)
+    for (int64_t i = R - 1; i > 0; --i) std::swap(rows[i], rows[int64_t(rng() % uint64_t(i + 1))]);
+    e = cudaMemcpyAsync(idx, rows.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // rows is reshuffled next epoch
+    if (e != cudaSuccess) return cuda_err(c, e, "training indices");
+    for (int64_t b = 0; b < steps_per; ++b, ++step) {
+      SPH2D_LAUNCH(c, (gather_rows_kernel), nblk(batch), 256, X, T, idx + b * batch, int64_t(batch), Xb, Tb);
+      s = sur_grad_batch(c, prm, Xb, Tb, batch, grad, loss);
+      if (s != SPH2D_OK) return s;
+      // warm-up from lr/10 over the first 5% of the steps, then cosine decay to lr/100
+      const double f = double(step) / double(total);
+      const double lr_t = f < 0.05 ? lr * (0.1 + 0.9 * f / 0.05)
+                                   : lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(3.141592653589793 * (f - 0.05) / 0.95)));
+      const int64_t tt = ++c->sur_step;
+      SPH2D_LAUNCH(c, (adamw_kernel), nblk(kSurParams), 256, prm, grad, m, v, kSurParams, float(lr_t), b1, b2,
+                   eps, float(wd), float(1.0 - std::pow(double(b1), double(tt))),
+                   float(1.0 - std::pow(double(b2), double(tt))));
+    }
+  }
+  float lh = 0.0f;
+  e = cudaMemcpyAsync(&lh, loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(c, e, "training");
+  if (final_loss) *final_loss = lh;
+  return SPH2D_OK;
+}
+
+// the values and fallback kernels for one pair source (fb_count already cleared)
+template <int KID, bool LIST>
+static void launch_serving(Ctx* c, const IntArgs& a, const double* pairs, const SurArgs& sa) {
+  const int64_t nch = (a.P + 31) / 32;
+  const unsigned g1 = persistent_grid(c, surrogate_values_kernel<KID, LIST>, (nch + 3) / 4);
+  SPH2D_LAUNCH(c, (surrogate_values_kernel<KID, LIST>), g1, 128, a, pairs, sa);
+  // the list length is only known on the device: a persistent grid strides over it
+  const unsigned g2 = persistent_grid(c, surrogate_fallback_kernel<KID, LIST>, (a.P + 127) / 128);
+  SPH2D_LAUNCH(c, (surrogate_fallback_kernel<KID, LIST>), g2, 128, a, pairs, sa);
+}
+
+template <bool LIST>
+static void dispatch_serving(Ctx* c, const IntArgs& a, const double* pairs, const SurArgs& sa) {
+  switch (c->sur_kernel) {
+    case KID_WC2: launch_serving<KID_WC2, LIST>(c, a, pairs, sa); break;
+    case KID_WC4: launch_serving<KID_WC4, LIST>(c, a, pairs, sa); break;
+    case KID_WC6: launch_serving<KID_WC6, LIST>(c, a, pairs, sa); break;
+    default: launch_serving<KID_CUBIC, LIST>(c, a, pairs, sa); break;
+  }
+}
+
+static sph2d_status serving_setup(Ctx* c, int64_t P, SurArgs& sa) {
+  sph2d_status s = ensure(c, c->sur_fb, size_t(P > 0 ? P : 1) * sizeof(int64_t));
+  if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
+  if (s != SPH2D_OK) return s;
+  sa.prm = static_cast<const float*>(c->sur_prm.ptr);
+  sa.fb_list = static_cast<int64_t*>(c->sur_fb.ptr);
+  sa.fb_count = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 2;
+  cudaError_t e = cudaMemsetAsync(sa.fb_count, 0, sizeof(unsigned long long), c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "memset");
+  return SPH2D_OK;
+}
+
+static sph2d_status serving_finish(Ctx* c, const SurArgs& sa, int64_t P) {
+  cudaError_t e = cudaMemcpyAsync(c->pinned + 10, sa.fb_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fallback count copy");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate launch");
+  c->stats.n_pairs = P;
+  c->stats.n_fixup = 0;
+  c->fixup_pending = false;
+  c->fallback_pending = true;
+  return SPH2D_OK;
+}
+
+sph2d_status surrogate_pairs(Ctx* c, const double* pairs, int64_t P, double H, float* out, int32_t* accepted) {
+  SurArgs sa{};
+  sph2d_status s = serving_setup(c, P, sa);
+  if (s != SPH2D_OK) return s;
+  sa.C = kernel_C(c->sur_kernel);
+  sa.H = H;
+  sa.invH = 1.0 / H;
+  sa.vals = out;
+  sa.accepted = accepted;
+  IntArgs a{};
+  a.P = P;
+  a.H = H;
+  a.invH = 1.0 / H;
+  a.C = sa.C;
+  c->stats = sph2d_stats{};
+  if (P > 0) dispatch_serving<false>(c, a, pairs, sa);
+  return serving_finish(c, sa, P);
+}
+
+// serving over the context's pair list: per-particle gamma and grad gamma (float)
+sph2d_status surrogate_integrals(Ctx* c, void* gamma, void* grad) {
+  const Cells& cl = c->cells;
+  IntArgs a{};
+  a.parts = reinterpret_cast<const float4*>(cl.particles);
+  a.tris = cl.tris;
+  a.pair_tri = static_cast<const int32_t*>(c->pair_tri.ptr);
+  a.pair_pid = static_cast<const int32_t*>(c->pair_pid.ptr);
+  a.pair_off = static_cast<const int64_t*>(c->pair_off.ptr);
+  a.P = cl.P;
+  a.N = cl.N;
+  a.H = cl.H;
+  a.invH = 1.0 / cl.H;
+  a.C = kernel_C(c->sur_kernel);
+  a.gamma = gamma;
+  a.grad = grad;
+  a.mom = nullptr;
+  a.nm = 0;
+  SurArgs sa{};
+  sph2d_status s = serving_setup(c, a.P, sa);
+  if (s == SPH2D_OK) s = ensure(c, c->sur_vals, size_t(a.P > 0 ? a.P : 1) * 3 * sizeof(float));
+  if (s == SPH2D_OK) s = ensure(c, c->slots, size_t(((a.P + 31) >> 5) * 2 * 3 + 1) * sizeof(float));
+  if (s != SPH2D_OK) return s;
+  a.slots = c->slots.ptr;
+  a.nfix = sa.fb_count;
+  sa.C = a.C;
+  sa.H = a.H;
+  sa.invH = a.invH;
+  sa.vals = static_cast<float*>(c->sur_vals.ptr);
+  sa.accepted = nullptr;
+  if (a.P > 0) {
+    dispatch_serving<true>(c, a, nullptr, sa);
+    const unsigned g = persistent_grid(c, reduce_vals_kernel, ((a.P + 31) / 32 + 3) / 4);
+    SPH2D_LAUNCH(c, (reduce_vals_kernel), g, 128, a, sa.vals);
+  }
+  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<float, false>), nblk(a.N), 256, a);
+  return serving_finish(c, sa, cl.P);
+}
+
+// versioned binary checkpoint: header, FP32 masters + Adam moments, FNV-1a checksum
+struct SurHeader {
+  char magic[8];
+  uint32_t version, kernel, in, hidden, out, reserved;
+  uint64_t nparams, step, checksum;
+};
+
+static uint64_t fnv1a(const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+sph2d_status surrogate_save(Ctx* c, const char* path) {
+  std::vector<float> buf(3 * size_t(kSurParams));
+  cudaError_t e = cudaMemcpyAsync(buf.data(), c->sur_prm.ptr, buf.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate save");
+  SurHeader h{};
+  memcpy(h.magic, "SPH2DSUR", 8);
+  h.version = 1;
+  h.kernel = uint32_t(c->sur_kernel);
+  h.in = kSurIn;
+  h.hidden = kSurHid;
+  h.out = kSurOut;
+  h.nparams = kSurParams;
+  h.step = uint64_t(c->sur_step);
+  h.checksum = fnv1a(buf.data(), buf.size() * sizeof(float));
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_err(c, SPH2D_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  const bool closed = fclose(f) == 0;
+  return ok && closed ? SPH2D_OK : set_err(c, SPH2D_ERR_INVALID_ARG, "short write");
+}
+
+sph2d_status surrogate_load(Ctx* c, const char* path) {
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_err(c, SPH2D_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  SurHeader h{};
+  std::vector<float> buf(3 * size_t(kSurParams));
+  bool ok = fread(&h, sizeof(h), 1, f) == 1 && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = ok && fgetc(f) == EOF;
+  fclose(f);
+  if (!ok || memcmp(h.magic, "SPH2DSUR", 8) != 0 || h.version != 1 || h.nparams != uint64_t(kSurParams) ||
+      h.in != uint32_t(kSurIn) || h.hidden != uint32_t(kSurHid) || h.out != uint32_t(kSurOut) || h.kernel > 3)
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "not a compatible surrogate checkpoint");
+  if (fnv1a(buf.data(), buf.size() * sizeof(float)) != h.checksum)
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "checkpoint checksum mismatch");
+  sph2d_status s = surrogate_init(c, int(h.kernel), 0);
+  if (s != SPH2D_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(c->sur_prm.ptr, buf.data(), buf.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "surrogate load");
+  c->sur_step = int64_t(h.step);
+  return SPH2D_OK;
+}
+
+}  // namespace sph2d

@@ -1,0 +1,149 @@
+// Learned surrogate for the per-pair integrals (gamma, grad gamma) with a guarded analytic
+// fallback.  This part has no counterpart in the paper: it is a small MLP evaluated on BF16
+// tensor cores (FP32 accumulation) that replaces the closed form for pairs inside the domain
+// it was trained on; every other pair goes to the analytic path.
+//
+// Canonical frame.  The pair's triangle in the particle frame (H = 1) is rotated so that its
+// centroid lies on the +x axis and reflected (y -> -y) if its vertex closest to the particle
+// then lies below the axis; its vertices are listed counter-clockwise starting from that
+// closest one.  The result depends on the triangle as a point set only.  gamma is invariant
+// under the rotation and the reflection; the gradient is mapped back by their inverses.
+//
+// Network.  6 inputs (canonical vertices) -> 64 -> 64 -> 64 -> 3, tanh-GELU, predicting the
+// triangle-averaged kernel and kernel gradient (gamma/area, grad/area); multiplying by the
+// exactly computed area removes most of the dynamic range the network would otherwise have to
+// learn.  Parameters are FP32 masters; tensor-core operands are BF16.
+//
+// Guard.  A pair is evaluated by the network only if its canonical triangle lies in the
+// training domain: largest edge in [kSurMinSize, kSurMaxSize] H, smallest angle >= 15 deg,
+// centroid at least kSurMinCentroid H from the particle (the canonical rotation is unstable
+// near the centroid), all vertices within kSurMaxRadius H.  Everything else is analytic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "pair_math.cuh"
+
+namespace sph2d {
+
+constexpr int kSurIn = 6, kSurHid = 64, kSurOut = 3;
+constexpr int kSurK1 = 16;     // layer-1 reduction padded to one k16 step
+constexpr int kSurN4 = 8;      // output layer padded to one n8 tile
+// FP32 master parameter layout (flat): W1[64][6] b1[64] W2[64][64] b2[64] W3[64][64] b3[64]
+// W4[3][64] b4[3]
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kSurHid * kSurIn;
+constexpr int kOffW2 = kOffB1 + kSurHid, kOffB2 = kOffW2 + kSurHid * kSurHid;
+constexpr int kOffW3 = kOffB2 + kSurHid, kOffB3 = kOffW3 + kSurHid * kSurHid;
+constexpr int kOffW4 = kOffB3 + kSurHid, kOffB4 = kOffW4 + kSurOut * kSurHid;
+constexpr int kSurParams = kOffB4 + kSurOut;   // 8963
+
+constexpr float kSurMinSize = 0.1f, kSurMaxSize = 0.45f;
+constexpr float kSurMinCentroid = 0.2f, kSurMaxRadius = 1.5f;
+constexpr float kSurSinMinAngle = 0.25881904510252074f;   // sin 15 deg
+
+struct Canon {
+  float x[6];          // canonical vertices
+  float cs, sn;        // rotation taking the centroid direction to +x
+  float refl;          // +1 or -1 (reflection y -> -y applied after the rotation)
+  float area;
+  bool accept;         // inside the surrogate's domain
+};
+
+SPH2D_HD Canon canonicalize(const float* v) {
+  Canon c;
+  const float cx = (v[0] + v[2] + v[4]) * (1.0f / 3.0f), cy = (v[1] + v[3] + v[5]) * (1.0f / 3.0f);
+  const float r = sqrt(cx * cx + cy * cy);
+  c.cs = r > 0.0f ? cx / r : 1.0f;
+  c.sn = r > 0.0f ? cy / r : 0.0f;
+  float q[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    q[2 * j] = c.cs * v[2 * j] + c.sn * v[2 * j + 1];
+    q[2 * j + 1] = -c.sn * v[2 * j] + c.cs * v[2 * j + 1];
+  }
+  const float cr = diff_of_products(q[2] - q[0], q[5] - q[1], q[3] - q[1], q[4] - q[0]);
+  // closest vertex to the particle (lowest index on ties); the mirror image y -> -y is taken
+  // when that vertex lies below the axis, so the canonical triangle depends on the geometry
+  // only, not on how its vertices are labelled
+  const float d0 = q[0] * q[0] + q[1] * q[1], d1 = q[2] * q[2] + q[3] * q[3], d2 = q[4] * q[4] + q[5] * q[5];
+  const int k = (d1 < d0 && d1 <= d2) ? 1 : ((d2 < d0 && d2 < d1) ? 2 : 0);
+  c.refl = q[2 * k + 1] < 0.0f ? -1.0f : 1.0f;
+  // counter-clockwise order from the closest vertex: forward if the (reflected) labelled
+  // order is counter-clockwise, backward otherwise
+  const int step = (c.refl * cr < 0.0f) ? 2 : 1;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int s = (k + step * j) % 3;
+    c.x[2 * j] = q[2 * s];
+    c.x[2 * j + 1] = c.refl * q[2 * s + 1];
+  }
+  c.area = 0.5f * fabs(cr);
+  // domain guard
+  float lmax = 0.0f, l[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int b = e == 2 ? 0 : e + 1;
+    const float ex = c.x[2 * b] - c.x[2 * e], ey = c.x[2 * b + 1] - c.x[2 * e + 1];
+    l[e] = sqrt(ex * ex + ey * ey);
+    lmax = fmax(lmax, l[e]);
+  }
+  // sin of the angle at vertex j is 2 area / (product of its two edges)
+  const float s0 = 2.0f * c.area / fmax(l[0] * l[2], 1e-30f);
+  const float s1 = 2.0f * c.area / fmax(l[0] * l[1], 1e-30f);
+  const float s2 = 2.0f * c.area / fmax(l[1] * l[2], 1e-30f);
+  const float smin = fmin(s0, fmin(s1, s2));
+  const float rmax = sqrt(fmax(d0, fmax(d1, d2)));
+  c.accept = c.area > 0.0f && lmax >= kSurMinSize && lmax <= kSurMaxSize && smin >= kSurSinMinAngle &&
+             r >= kSurMinCentroid && rmax <= kSurMaxRadius && isfinite(c.area) && isfinite(r);
+  return c;
+}
+
+// canonical gradient -> particle frame
+SPH2D_HD void uncanonicalize_grad(const Canon& c, float gx_c, float gy_c, float& gx, float& gy) {
+  const float gy_r = c.refl * gy_c;
+  gx = c.cs * gx_c - c.sn * gy_r;
+  gy = c.sn * gx_c + c.cs * gy_r;
+}
+
+// tanh-form GELU and its derivative.  On the device tanh is the hardware approximation
+// (tanh.approx.f32, relative error about 2^-11), well below the BF16 rounding that follows it;
+// training and inference use the same function.
+SPH2D_HD float tanh_act(float u) {
+#if defined(__CUDA_ARCH__)
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return t;
+#else
+  return tanhf(u);
+#endif
+}
+SPH2D_HD float gelu_f(float z) {
+  const float k = 0.7978845608028654f;   // sqrt(2/pi)
+  const float u = k * z * (1.0f + 0.044715f * z * z);
+  const float h = 0.5f * z;
+  return h + h * tanh_act(u);
+}
+SPH2D_HD float gelu_grad_f(float z) {
+  const float k = 0.7978845608028654f;
+  const float u = k * z * (1.0f + 0.044715f * z * z);
+  const float t = tanh_act(u);
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * z * z);
+}
+
+#if defined(__CUDACC__)
+// m16n8k16 BF16 x BF16 -> FP32 tensor-core MMA (row.col)
+__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+#endif
+
+}  // namespace sph2d

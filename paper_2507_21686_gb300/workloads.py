@@ -173,6 +173,18 @@ def _place_within_support(rng, shapes):
     return out
 
 
+def surrogate_training_pairs(count: int, rng: np.random.Generator, lo: float = 0.08,
+                             hi: float = 0.5) -> np.ndarray:
+    """Training and test pairs for the learned surrogate (local frame, H = 1): generic
+    triangles (all angles >= 15 deg) with longest edge logU[lo, hi], placed uniformly over
+    the region where they overlap the support.  float64 [count, 8] (particle at 0)."""
+    size = np.exp(rng.uniform(math.log(lo), math.log(hi), size=count))
+    shapes = _random_shape(rng, count, "generic") * size[:, None]
+    pairs = np.zeros((count, 8))
+    pairs[:, 2:] = _place_within_support(rng, shapes)
+    return pairs
+
+
 def stress_pairs(count: int, rng: np.random.Generator) -> tuple[np.ndarray, np.ndarray]:
     """Precision-stress pairs in the local frame (H = 1, particle at the origin).
 

@@ -302,3 +302,16 @@ def test_pair_list_capacity_status(ctx):
     req = ctypes.c_int64()
     st = ctx.lib.sph2d_pair_list(ctx.h, _ptr(off), _ptr(tri), P - 1, ctypes.byref(req))
     assert st == 3 and req.value == P
+
+
+@pytest.mark.parametrize("kernel", ["wendland_c2", "wendland_c4", "wendland_c6"])
+def test_stress_pairs_full_size(ctx, kernel):
+    """All 262,144 precision-stress pairs (generic / sliver / near-singular), every output."""
+    w = W.precision_stress()
+    ref = oracle_per_pair(oracle.pairs(kernel, 1.0, w.pairs), 10)
+    sc = scales(kernel, 1.0, 10)
+    for mode, tol in (("fp64", TOL_FP64), ("fp32_fixup", TOL_FP32)):
+        out = ctx.pair_integrals(_t(w.pairs), kernel, 1.0, 3, mode).cpu().numpy()
+        err = rel_err(out, ref, sc).max(axis=1)
+        for c in range(3):
+            assert err[w.labels == c].max() <= tol, f"{kernel} {mode} class {c}: {err[w.labels == c].max():.3e}"
