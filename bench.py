@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--only-surrogate", action="store_true",
+                    help="run only the surrogate leg and print its JSON (profiling aid)")
+    ap.add_argument("--surrogate-n", type=int, default=2048,
+                    help="particles per side of the surrogate serving box (obstacle scales with it)")
+    ap.add_argument("--surrogate-train-pairs", type=int, default=8_000_000)
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: timed FP32 path only (no FP64 leg, e2e, CPU baseline, L2 flush)")
     return ap.parse_args()
@@ -274,6 +279,13 @@ def run_ours(args):
             kms = [[t[i][0].elapsed_time(t[i][1]) for t in kt] for i in range(len(KERNELS) + 1)]
         return ms, kms, launches, clocks
 
+    if args.only_surrogate:
+        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        res = run_surrogate(ctx, dev, stream, flush, n=args.surrogate_n, train_pairs=args.surrogate_train_pairs)
+        if rank == 0:
+            print(json.dumps({"surrogate": res}), flush=True)
+        return
+
     # ---- pairs and their op counts
     ctx.build_cells(parts, tris, w.H)
     P = ctx.pair_count()
@@ -353,7 +365,8 @@ def run_ours(args):
     adjoint = run_adjoint(ctx, dev, stream, flush)
 
     # ---- learned surrogate: train, then serve the 4M x 1M box against the analytic paths
-    surrogate = None if args.no_surrogate else run_surrogate(ctx, dev, stream, flush)
+    surrogate = None if args.no_surrogate else run_surrogate(ctx, dev, stream, flush, n=args.surrogate_n,
+                                                             train_pairs=args.surrogate_train_pairs)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -446,26 +459,27 @@ def run_adjoint(ctx, dev, stream, flush, steps=3):
     return out
 
 
-def run_surrogate(ctx, dev, stream, flush, reps=3):
+def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3):
     """Train the surrogate on analytic pairs, then time gamma + grad gamma over the pair list
-    of the 2048^2-particle box (surrogate with guarded fallback vs FP32 + fix-up vs FP64)."""
+    of the n^2-particle box with an obstacle of 0.322 n cells (n = 2048: 4,194,304 particles x
+    1,002,784 triangles), surrogate with guarded fallback vs FP32 + fix-up vs FP64."""
     import torch
     from paper_2507_21686_gb300 import workloads as W
     from tests.helpers import rel_err, scales
     k = "wendland_c2"
     t0 = time.time()
-    tp = W.surrogate_training_pairs(2_000_000, np.random.default_rng(55))
+    tp = W.surrogate_training_pairs(train_pairs, np.random.default_rng(55))
     gen_s = time.time() - t0
     tpd = torch.from_numpy(tp).to(dev)
     ctx.surrogate_init(k, 5)
-    epochs, batch = 8, 4096
+    epochs, batch, lr = 60, 16384, 5e-3
     torch.cuda.synchronize()
     t0 = time.time()
-    loss, used = ctx.surrogate_train(tpd, 1.0, epochs=epochs, batch=batch, lr=3e-3, seed=5)
+    loss, used = ctx.surrogate_train(tpd, 1.0, epochs=epochs, batch=batch, lr=lr, seed=5)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     del tpd
-    w = W.surrogate_box()
+    w = W.surrogate_box(n=n, obstacle_cells=(660 * n) // 2048)
     parts = torch.from_numpy(w.particles).to(dev)
     tris = torch.from_numpy(w.triangles).to(dev)
     ctx.build_cells(parts, tris, w.H)
@@ -493,7 +507,7 @@ def run_surrogate(ctx, dev, stream, flush, reps=3):
                                                   "max": float(e.max())}
     del outs
     return {"workload": w.name, "kernel": k, "pairs": P,
-            "train": {"pairs": len(tp), "in_domain": used, "epochs": epochs, "batch": batch,
+            "train": {"pairs": len(tp), "in_domain": used, "epochs": epochs, "batch": batch, "lr": lr,
                       "steps": epochs * (used // batch), "seconds": train_s, "final_batch_loss": loss,
                       "data_generation_s_host": gen_s},
             "speedup_vs_fp32_fixup": res["fp32_fixup"]["ms"] / res["surrogate"]["ms"],

@@ -241,8 +241,9 @@ sph2d_status sph2d_pair_list_integrals_noalloc(const float* particles, int64_t N
 /*
  * ---- Learned surrogate -------------------------------------------------------------------
  * The paper has no counterpart: a small network that replaces the closed form for pairs
- * inside a trained domain, evaluated on BF16 tensor cores with FP32 accumulation; every other
- * pair takes the analytic path (SPH2D_FP32_FIXUP arithmetic).  Outputs are gamma and grad
+ * inside a trained domain, evaluated on tensor cores (FP16 operands, FP32 accumulation; the
+ * training backward pass uses BF16 operands); every other pair takes the analytic path
+ * (SPH2D_FP32_FIXUP arithmetic).  Outputs are gamma and grad
  * gamma only, always float.
  *
  * Canonical frame (H = 1): the pair's triangle, relative to the particle, is rotated so that
@@ -257,8 +258,8 @@ sph2d_status sph2d_pair_list_integrals_noalloc(const float* particles, int64_t N
  * SPH2D_SURROGATE_MAX_RADIUS H, non-zero finite area.  The guard is evaluated in FP32 on the
  * FP32 local frame.
  * Parameters: SPH2D_SURROGATE_PARAMS FP32 values in the order W1[64][6] b1[64] W2[64][64]
- * b2[64] W3[64][64] b3[64] W4[3][64] b4[3] (W[out][in], row-major); tensor-core operands are
- * their BF16 roundings.
+ * b2[64] W3[64][64] b3[64] W4[3][64] b4[3] (W[out][in], row-major); forward tensor-core
+ * operands are their FP16 roundings, and the GELU is evaluated in packed FP16 arithmetic.
  */
 #define SPH2D_SURROGATE_PARAMS 8963
 #define SPH2D_SURROGATE_MIN_SIZE 0.1

@@ -10,9 +10,11 @@ What it restates, in plain array code:
     on ties), and the guard that decides whether the network may be used;
   * the network 6 -> 64 -> 64 -> 64 -> 3 with the tanh form of GELU between layers, its
     loss (1/B) sum_rows sum_c w_c (y_c - t_c)^2 and that loss's gradient by backpropagation;
-  * optional BF16 emulation: every matrix-product operand rounded float64 -> float32 ->
-    bfloat16 (round to nearest even), the points where the tensor-core path rounds, so that
-    GPU and reference differ only in accumulation order and the tanh approximation.
+  * optional emulation of the tensor-core operand roundings (float64 -> float32 -> operand
+    type, round to nearest even): forward products take FP16 operands and the GELU between
+    them is evaluated step by step in FP16 as the GPU does, backward products take BF16
+    operands, so that GPU and reference differ only in accumulation order and in the GPU's
+    hardware tanh approximation.
 Parameter layout (flat float): W1[64][6] b1[64] W2[64][64] b2[64] W3[64][64] b3[64]
 W4[3][64] b4[3], W[out][in].
 
@@ -63,8 +65,33 @@ def bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def f16(x):
+    """Round to IEEE half (via float32, round to nearest even), returned as float64."""
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
+def _exact(a):
+    return np.asarray(a, dtype=np.float64)
+
+
 def gelu(z):
     return 0.5 * z * (1.0 + np.tanh(GELU_K * (z + GELU_A * z ** 3)))
+
+
+def gelu_f16(z):
+    """The GELU as the GPU evaluates it on FP16 pairs: z rounded to FP16, then
+    u = (z*z rounded) * ka + k (one rounding, a fused multiply-add), u = u * z (rounded),
+    t = tanh(u) rounded (the GPU's hardware approximation is within about one FP16 step of
+    it), h = z / 2, result = h * t + h (one rounding).  Products of FP16 values are exact in
+    float64, so each rounded step is one rounding of the exact value."""
+    K = f16(GELU_K)
+    KA = f16(np.float32(GELU_K) * np.float32(GELU_A))
+    with np.errstate(over="ignore", invalid="ignore"):
+        z = f16(z)
+        u = f16(f16(f16(z * z) * KA + K) * z)
+        t = f16(np.tanh(u))
+        h = f16(0.5 * z)
+        return f16(h * t + h)
 
 
 def gelu_grad(z):
@@ -156,31 +183,32 @@ def canonical_targets(cn, gamma, grad_local):
 # ---------------------------------------------------------------------------------------
 # network, loss, gradient
 # ---------------------------------------------------------------------------------------
-def forward(params, X, emulate_bf16=False):
+def forward(params, X, emulate_tc=False):
     """X [B, 6] -> (Y [B, 3], cache)."""
     p = unpack(params)
-    rnd = bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    rnd = f16 if emulate_tc else _exact
+    act = gelu_f16 if emulate_tc else gelu
     H0 = np.asarray(X, dtype=np.float64)
     Z1 = rnd(H0) @ rnd(p["W1"]).T + p["b1"]
-    H1 = gelu(Z1)
+    H1 = act(Z1)
     Z2 = rnd(H1) @ rnd(p["W2"]).T + p["b2"]
-    H2 = gelu(Z2)
+    H2 = act(Z2)
     Z3 = rnd(H2) @ rnd(p["W3"]).T + p["b3"]
-    H3 = gelu(Z3)
+    H3 = act(Z3)
     Y = rnd(H3) @ rnd(p["W4"]).T + p["b4"]
     return Y, dict(H0=H0, Z1=Z1, H1=H1, Z2=Z2, H2=H2, Z3=Z3, H3=H3)
 
 
-def loss(params, X, T, w, emulate_bf16=False):
-    Y, _ = forward(params, X, emulate_bf16)
+def loss(params, X, T, w, emulate_tc=False):
+    Y, _ = forward(params, X, emulate_tc)
     return float(np.mean(np.sum(np.asarray(w)[None, :] * (Y - T) ** 2, axis=1)))
 
 
-def loss_and_grad(params, X, T, w, emulate_bf16=False):
+def loss_and_grad(params, X, T, w, emulate_tc=False):
     """(loss, flat gradient) by backpropagation through the four layers."""
     p = unpack(params)
-    rnd = bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
-    Y, k = forward(params, X, emulate_bf16)
+    rnd = bf16 if emulate_tc else _exact
+    Y, k = forward(params, X, emulate_tc)
     B = Y.shape[0]
     w = np.asarray(w, dtype=np.float64)
     D = Y - T
@@ -206,11 +234,11 @@ def loss_weights(C):
     return np.array([1.0 / C ** 2, 1.0 / (4 * C ** 2), 1.0 / (4 * C ** 2)])
 
 
-def surrogate_local(params, local, emulate_bf16=True):
+def surrogate_local(params, local, emulate_tc=True):
     """Network prediction for particle-frame pairs (H = 1): (gamma, local-frame gradient)
     [P, 3] and the guard result; rows the guard rejects are NaN (the analytic path's)."""
     cn = canonicalize(local)
-    Y, _ = forward(params, cn["x"], emulate_bf16)
+    Y, _ = forward(params, cn["x"], emulate_tc)
     a = cn["area"][:, None]
     g = uncanonicalize_grad(cn, a * Y[:, 1:3])
     out = np.concatenate([a * Y[:, :1], g], axis=1)

@@ -1,5 +1,6 @@
-// Learned surrogate: BF16 tensor-core (mma.sync m16n8k16, FP32 accumulation) training and
-// inference of the 6-64-64-64-3 MLP of surrogate.cuh, with the guarded analytic fallback.
+// Learned surrogate: tensor-core (mma.sync m16n8k16, FP32 accumulation) training and
+// inference of the 6-64-64-64-3 MLP of surrogate.cuh (FP16 forward operands, BF16 backward
+// operands), with the guarded analytic fallback.
 // This part has no counterpart in the paper.
 //
 // Training runs entirely in this file's kernels: canonicalisation of analytic training pairs,
@@ -12,7 +13,8 @@
 //   values   one warp per 32 pairs: every lane canonicalises its pair and applies the guard;
 //            the 32 rows go through the network as two m16 tiles with the layer outputs kept
 //            in registers and fed back as the next layer's A operand (the accumulator fragment
-//            of two adjacent n8 tiles is exactly the A fragment of one k16 step).  Accepted
+//            of two adjacent n8 tiles is exactly the A fragment of one k16 step); weight
+//            fragments come from shared memory by ldmatrix.  Accepted
 //            pairs write their value; rejected pairs are appended to a fallback list (one
 //            atomic per warp).
 //   fallback the analytic FP32 path (with its FP64 fix-up) over the compacted list, so a
@@ -43,7 +45,8 @@ static_assert(kSurMinSize == float(SPH2D_SURROGATE_MIN_SIZE) && kSurMaxSize == f
               "guard constants differ from the header");
 
 // ---------------------------------------------------------------------------------------
-// generic GEMM: C[M][N] = alpha * op(A) op(B)   (FP32 in/out, BF16 operands, FP32 accumulate)
+// generic GEMM: C[M][N] = alpha * op(A) op(B)   (FP32 in/out, T = FP16 or BF16 operands rounded
+// to nearest even on the way into shared memory, FP32 accumulation)
 //   op(A) is M x K: ta=0 -> A[m*lda + k], ta=1 -> A[k*lda + m]
 //   op(B) is K x N: tb=0 -> B[n*ldb + k],  tb=1 -> B[k*ldb + n]
 // Block tile 64 x 64 x 32, 4 warps of 32 x 32.  blockIdx.z splits K; with ksplit > 1 each
@@ -51,12 +54,13 @@ static_assert(kSurMinSize == float(SPH2D_SURROGATE_MIN_SIZE) && kSurMaxSize == f
 // ---------------------------------------------------------------------------------------
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
 
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A,
-                                                        int lda, int ta, const float* __restrict__ B, int ldb,
-                                                        int tb, float* __restrict__ C, int ldc, float alpha,
-                                                        int ksplit) {
-  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+template <typename T>
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                      int lda, int ta, const float* __restrict__ B, int ldb,
+                                                      int tb, float* __restrict__ C, int ldc, float alpha,
+                                                      int ksplit) {
+  __shared__ __align__(16) T As[GBM][GBK + GPAD];
+  __shared__ __align__(16) T Bs[GBN][GBK + GPAD];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
       const int gm = m0 + m, gk = k0 + k;
       float v = 0.0f;
       if (gm < M && gk < kend) v = ta ? A[size_t(gk) * lda + gm] : A[size_t(gm) * lda + gk];
-      As[m][k] = __float2bfloat16_rn(v);
+      As[m][k] = to_op(v, T());
     }
 #pragma unroll
     for (int i = 0; i < (GBN * GBK) / 128; ++i) {
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
       const int gn = n0 + n, gk = k0 + k;
       float v = 0.0f;
       if (gn < N && gk < kend) v = tb ? B[size_t(gk) * ldb + gn] : B[size_t(gn) * ldb + gk];
-      Bs[n][k] = __float2bfloat16_rn(v);
+      Bs[n][k] = to_op(v, T());
     }
     __syncthreads();
 #pragma unroll
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, con
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bf[j]);
+        for (int j = 0; j < 4; ++j) mma_16816(acc[i][j], af[i], bf[j], T());
     }
     __syncthreads();
   }
@@ -144,13 +148,24 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits,
 // ---------------------------------------------------------------------------------------
 // elementwise kernels of the training step
 // ---------------------------------------------------------------------------------------
-// Z += b (row broadcast); Hh = GELU(Z) if act, else Hh = Z (Hh may alias Z only when !act)
-__global__ void bias_act_kernel(float* Z, const float* __restrict__ b, float* Hh, int64_t rows, int n, int act) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// Z += b (row broadcast, n even); H = GELU(Z) in packed FP16 arithmetic (exactly the
+// inference activation), stored as FP32
+__global__ void bias_gelu_kernel(float* __restrict__ Z, const float* __restrict__ b, float* __restrict__ Hh,
+                                 int64_t rows, int n) {
+  const int64_t i = 2 * (int64_t(blockIdx.x) * blockDim.x + threadIdx.x);
   if (i >= rows * n) return;
-  const float z = Z[i] + b[i % n];
-  Z[i] = z;
-  Hh[i] = act ? gelu_f(z) : z;
+  const int col = int(i % n);
+  const float z0 = Z[i] + b[col], z1 = Z[i + 1] + b[col + 1];
+  Z[i] = z0;
+  Z[i + 1] = z1;
+  const float2 g = __half22float2(gelu_h2(__floats2half2_rn(z0, z1)));
+  Hh[i] = g.x;
+  Hh[i + 1] = g.y;
+}
+
+__global__ void bias_kernel(float* __restrict__ Z, const float* __restrict__ b, int64_t rows, int n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < rows * n) Z[i] += b[i % n];
 }
 
 __global__ void gelu_back_kernel(float* __restrict__ dH, const float* __restrict__ Z, int64_t count) {
@@ -274,32 +289,32 @@ __global__ void canon_training_kernel(const double* __restrict__ pairs, const do
 // ---------------------------------------------------------------------------------------
 // inference: the network on register-resident fragments
 // ---------------------------------------------------------------------------------------
-constexpr int kW1Stride = kSurK1 + 8;     // padded bf16 row strides (conflict-free fragments)
-constexpr int kWStride = kSurHid + 8;
+constexpr int kW1Stride = kSurK1 + 8;     // padded FP16 row strides: 16-byte aligned rows whose
+constexpr int kWStride = kSurHid + 8;     // 8-row ldmatrix groups hit distinct bank quads
 constexpr int kXStride = kSurK1 + 8;
 struct SurSmem {
-  __nv_bfloat16 w1[kSurHid][kW1Stride];
-  __nv_bfloat16 w2[kSurHid][kWStride];
-  __nv_bfloat16 w3[kSurHid][kWStride];
-  __nv_bfloat16 w4[kSurN4][kWStride];
+  __half w1[kSurHid][kW1Stride];           // W[out][in], FP16
+  __half w2[kSurHid][kWStride];
+  __half w3[kSurHid][kWStride];
+  __half w4[kSurN4][kWStride];
   float b1[kSurHid], b2[kSurHid], b3[kSurHid], b4[kSurN4];
-  __nv_bfloat16 xin[4][32][kXStride];      // per-warp staged inputs
-  float yout[4][32][kSurN4];               // per-warp outputs
+  alignas(16) __half xin[4][32][kXStride];   // per-warp staged inputs
+  float yout[4][32][kSurN4];                 // per-warp outputs
 };
 
 __device__ void load_sur_weights(SurSmem& s, const float* __restrict__ prm) {
   for (int i = threadIdx.x; i < kSurHid * kW1Stride; i += blockDim.x) {
     const int n = i / kW1Stride, k = i % kW1Stride;
-    s.w1[n][k] = __float2bfloat16_rn(k < kSurIn ? prm[kOffW1 + n * kSurIn + k] : 0.0f);
+    s.w1[n][k] = __float2half_rn(k < kSurIn ? prm[kOffW1 + n * kSurIn + k] : 0.0f);
   }
   for (int i = threadIdx.x; i < kSurHid * kWStride; i += blockDim.x) {
     const int n = i / kWStride, k = i % kWStride;
-    s.w2[n][k] = __float2bfloat16_rn(k < kSurHid ? prm[kOffW2 + n * kSurHid + k] : 0.0f);
-    s.w3[n][k] = __float2bfloat16_rn(k < kSurHid ? prm[kOffW3 + n * kSurHid + k] : 0.0f);
+    s.w2[n][k] = __float2half_rn(k < kSurHid ? prm[kOffW2 + n * kSurHid + k] : 0.0f);
+    s.w3[n][k] = __float2half_rn(k < kSurHid ? prm[kOffW3 + n * kSurHid + k] : 0.0f);
   }
   for (int i = threadIdx.x; i < kSurN4 * kWStride; i += blockDim.x) {
     const int n = i / kWStride, k = i % kWStride;
-    s.w4[n][k] = __float2bfloat16_rn(n < kSurOut && k < kSurHid ? prm[kOffW4 + n * kSurHid + k] : 0.0f);
+    s.w4[n][k] = __float2half_rn(n < kSurOut && k < kSurHid ? prm[kOffW4 + n * kSurHid + k] : 0.0f);
   }
   for (int i = threadIdx.x; i < kSurHid; i += blockDim.x) {
     s.b1[i] = prm[kOffB1 + i];
@@ -309,61 +324,79 @@ __device__ void load_sur_weights(SurSmem& s, const float* __restrict__ prm) {
   for (int i = threadIdx.x; i < kSurN4; i += blockDim.x) s.b4[i] = i < kSurOut ? prm[kOffB4 + i] : 0.0f;
 }
 
-// one layer on a 16-row tile: A fragments a[KBLOCKS][4] in, acc[NTILES][4] = bias + a W^T
-template <int KBLOCKS, int WSTRIDE, int NTILES>
-__device__ __forceinline__ void layer_mma(const __nv_bfloat16 (*w)[WSTRIDE], const float* b, const uint32_t (*a)[4],
-                                          float (*acc)[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+// hidden layer on a 16-row tile: acc[8 n8 tiles][4] = bias + a W^T.  One ldmatrix.x4 gives the
+// B fragments of two n8 tiles for one k16 block (matrices: tile j k0-7, tile j k8-15,
+// tile j+1 k0-7, tile j+1 k8-15).
+template <int KBLOCKS, int WSTRIDE>
+__device__ __forceinline__ void layer_hidden(const __half (*w)[WSTRIDE], const float* b, const uint32_t (*a)[4],
+                                             float (*acc)[4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3, mat = lane >> 3, r = lane & 7;
 #pragma unroll
-  for (int j = 0; j < NTILES; ++j) {
+  for (int j = 0; j < 8; ++j) {
     const float bx = b[j * 8 + 2 * t], by = b[j * 8 + 2 * t + 1];
     acc[j][0] = bx;
     acc[j][1] = by;
     acc[j][2] = bx;
     acc[j][3] = by;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
 #pragma unroll
     for (int kb = 0; kb < KBLOCKS; ++kb) {
-      uint32_t bf[2];
-      bf[0] = *reinterpret_cast<const uint32_t*>(&w[j * 8 + g][kb * 16 + 2 * t]);
-      bf[1] = *reinterpret_cast<const uint32_t*>(&w[j * 8 + g][kb * 16 + 2 * t + 8]);
-      mma_bf16_16816(acc[j], a[kb], bf);
+      uint32_t f[4];
+      ldsm_x4(f, &w[(j + (mat >> 1)) * 8 + r][kb * 16 + (mat & 1) * 8]);
+      mma_16816(acc[j], a[kb], f, __half());
+      mma_16816(acc[j + 1], a[kb], f + 2, __half());
     }
   }
 }
 
-// GELU on the accumulators, repacked as the next layer's A fragments (k16 block kb takes the
-// n8 tiles 2kb and 2kb+1)
+// output layer (one n8 tile, four k16 blocks): one ldmatrix.x4 covers two k16 blocks
+__device__ __forceinline__ void layer_out(const __half (*w)[kWStride], const float* b, const uint32_t (*a)[4],
+                                          float* acc) {
+  const int lane = threadIdx.x & 31, t = lane & 3, mat = lane >> 3, r = lane & 7;
+  acc[0] = acc[2] = b[2 * t];
+  acc[1] = acc[3] = b[2 * t + 1];
+#pragma unroll
+  for (int kb = 0; kb < 4; kb += 2) {
+    uint32_t f[4];
+    ldsm_x4(f, &w[r][kb * 16 + mat * 8]);
+    mma_16816(acc, a[kb], f, __half());
+    mma_16816(acc, a[kb + 1], f + 2, __half());
+  }
+}
+
+// GELU on the accumulators (rounded to FP16, packed arithmetic), repacked as the next
+// layer's A fragments: k16 block kb takes the n8 tiles 2kb and 2kb+1
 __device__ __forceinline__ void act_to_a(const float (*acc)[4], uint32_t (*a)[4]) {
 #pragma unroll
   for (int kb = 0; kb < 4; ++kb) {
-    a[kb][0] = pack_bf16(gelu_f(acc[2 * kb][0]), gelu_f(acc[2 * kb][1]));
-    a[kb][1] = pack_bf16(gelu_f(acc[2 * kb][2]), gelu_f(acc[2 * kb][3]));
-    a[kb][2] = pack_bf16(gelu_f(acc[2 * kb + 1][0]), gelu_f(acc[2 * kb + 1][1]));
-    a[kb][3] = pack_bf16(gelu_f(acc[2 * kb + 1][2]), gelu_f(acc[2 * kb + 1][3]));
+    a[kb][0] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb][0], acc[2 * kb][1])));
+    a[kb][1] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb][2], acc[2 * kb][3])));
+    a[kb][2] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb + 1][0], acc[2 * kb + 1][1])));
+    a[kb][3] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb + 1][2], acc[2 * kb + 1][3])));
   }
 }
 
 // the network on the warp's 32 staged rows (xin -> yout).  All 32 lanes must call it.
 __device__ void mlp_warp32(SurSmem& s, int warp) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const __nv_bfloat16 (*xin)[kXStride] = s.xin[warp];
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, mat = lane >> 3, r = lane & 7;
   float (*yout)[kSurN4] = s.yout[warp];
 #pragma unroll 1
   for (int tile = 0; tile < 2; ++tile) {
     const int r0 = tile * 16;
     uint32_t a[4][4];
-    a[0][0] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g][2 * t]);
-    a[0][1] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g + 8][2 * t]);
-    a[0][2] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g][2 * t + 8]);
-    a[0][3] = *reinterpret_cast<const uint32_t*>(&xin[r0 + g + 8][2 * t + 8]);
+    // A fragment of the input tile (matrices: rows 0-7 k0-7, rows 8-15 k0-7, rows 0-7 k8-15,
+    // rows 8-15 k8-15)
+    ldsm_x4(a[0], &s.xin[warp][r0 + (mat & 1) * 8 + r][(mat >> 1) * 8]);
     float acc[8][4];
-    layer_mma<1, kW1Stride, 8>(s.w1, s.b1, a, acc);
+    layer_hidden<1, kW1Stride>(s.w1, s.b1, a, acc);
     act_to_a(acc, a);
-    layer_mma<4, kWStride, 8>(s.w2, s.b2, a, acc);
+    layer_hidden<4, kWStride>(s.w2, s.b2, a, acc);
     act_to_a(acc, a);
-    layer_mma<4, kWStride, 8>(s.w3, s.b3, a, acc);
+    layer_hidden<4, kWStride>(s.w3, s.b3, a, acc);
     act_to_a(acc, a);
-    layer_mma<4, kWStride, 1>(s.w4, s.b4, a, acc);
+    layer_out(s.w4, s.b4, a, acc[0]);
     yout[r0 + g][2 * t] = acc[0][0];
     yout[r0 + g][2 * t + 1] = acc[0][1];
     yout[r0 + g + 8][2 * t] = acc[0][2];
@@ -374,12 +407,12 @@ __device__ void mlp_warp32(SurSmem& s, int warp) {
 
 // stage one lane's canonical input row (zeros when the lane has no accepted pair)
 __device__ __forceinline__ void stage_row(SurSmem& s, int warp, int lane, const float* x, bool use) {
-  __nv_bfloat16* row = s.xin[warp][lane];
+  __half* row = s.xin[warp][lane];
 #pragma unroll
   for (int j = 0; j < kSurK1; j += 2) {
     const float lo = (j < kSurIn && use) ? x[j] : 0.0f;
     const float hi = (j + 1 < kSurIn && use) ? x[j + 1] : 0.0f;
-    *reinterpret_cast<uint32_t*>(row + j) = pack_bf16(lo, hi);
+    *reinterpret_cast<uint32_t*>(row + j) = pack_f16(lo, hi);
   }
 }
 
@@ -440,7 +473,7 @@ __device__ __forceinline__ void load_local(const IntArgs& a, const double* pairs
 }
 
 template <int KID, bool LIST>
-__global__ void __launch_bounds__(128) surrogate_values_kernel(IntArgs a, const double* __restrict__ pairs,
+__global__ void __launch_bounds__(128, 6) surrogate_values_kernel(IntArgs a, const double* __restrict__ pairs,
                                                                SurArgs sa) {
   __shared__ __align__(16) SurSmem s;
   load_sur_weights(s, sa.prm);
@@ -565,6 +598,7 @@ static unsigned persistent_grid(Ctx* c, K kern, int64_t blocks_wanted) {
   return unsigned(want < cap ? want : cap);
 }
 
+template <typename T>
 static sph2d_status gemm(Ctx* c, int M, int N, int K, const float* A, int lda, int ta, const float* B,
                          int ldb, int tb, float* C, int ldc) {
   // split K when the output tile grid is small and K is long (weight gradients over the batch)
@@ -573,13 +607,13 @@ static sph2d_status gemm(Ctx* c, int M, int N, int K, const float* A, int lda, i
   if (K >= 4096 && tiles < 64) splits = std::min(64, K / 1024);
   dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, splits);
   if (splits == 1) {
-    SPH2D_LAUNCH(c, (gemm_bf16_kernel), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0f, 1);
+    SPH2D_LAUNCH(c, (gemm_tc_kernel<T>), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0f, 1);
     return SPH2D_OK;
   }
   sph2d_status s = ensure(c, c->sur_split, size_t(splits) * M * N * sizeof(float));
   if (s != SPH2D_OK) return s;
   float* part = static_cast<float*>(c->sur_split.ptr);
-  SPH2D_LAUNCH(c, (gemm_bf16_kernel), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, part, N, 1.0f, splits);
+  SPH2D_LAUNCH(c, (gemm_tc_kernel<T>), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, part, N, 1.0f, splits);
   SPH2D_LAUNCH(c, (splitk_reduce_kernel), nblk(int64_t(M) * N), 256, part, splits, M, N, C, ldc, 1.0f);
   return SPH2D_OK;
 }
@@ -596,42 +630,47 @@ static sph2d_status sur_grad_batch(Ctx* c, const float* prm, const float* Xb, co
   float *Z1 = base, *H1 = Z1 + B * Hd, *Z2 = H1 + B * Hd, *H2 = Z2 + B * Hd, *Z3 = H2 + B * Hd;
   float *H3 = Z3 + B * Hd, *Y = H3 + B * Hd, *dY = Y + B * 3, *part = dY + B * 3;
   const int iB = int(B);
-#define SUR_GEMM(...)                                      \
-  do {                                                     \
-    if ((s = gemm(c, __VA_ARGS__)) != SPH2D_OK) return s;  \
+#define SUR_FWD(...)                                                   \
+  do {                                                                 \
+    if ((s = gemm<__half>(c, __VA_ARGS__)) != SPH2D_OK) return s;      \
   } while (0)
-  // forward: Z = H_prev W^T + b, H = GELU(Z)
-  SUR_GEMM(iB, Hd, kSurIn, Xb, kSurIn, 0, prm + kOffW1, kSurIn, 0, Z1, Hd);
-  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * Hd), 256, Z1, prm + kOffB1, H1, B, Hd, 1);
-  SUR_GEMM(iB, Hd, Hd, H1, Hd, 0, prm + kOffW2, Hd, 0, Z2, Hd);
-  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * Hd), 256, Z2, prm + kOffB2, H2, B, Hd, 1);
-  SUR_GEMM(iB, Hd, Hd, H2, Hd, 0, prm + kOffW3, Hd, 0, Z3, Hd);
-  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * Hd), 256, Z3, prm + kOffB3, H3, B, Hd, 1);
-  SUR_GEMM(iB, kSurOut, Hd, H3, Hd, 0, prm + kOffW4, Hd, 0, Y, kSurOut);
-  SPH2D_LAUNCH(c, (bias_act_kernel), nblk(B * 3), 256, Y, prm + kOffB4, Y, B, kSurOut, 0);
+#define SUR_BWD(...)                                                   \
+  do {                                                                 \
+    if ((s = gemm<__nv_bfloat16>(c, __VA_ARGS__)) != SPH2D_OK) return s; \
+  } while (0)
+  // forward (FP16 operands): Z = H_prev W^T + b, H = GELU(Z)
+  SUR_FWD(iB, Hd, kSurIn, Xb, kSurIn, 0, prm + kOffW1, kSurIn, 0, Z1, Hd);
+  SPH2D_LAUNCH(c, (bias_gelu_kernel), nblk(B * Hd / 2), 256, Z1, prm + kOffB1, H1, B, Hd);
+  SUR_FWD(iB, Hd, Hd, H1, Hd, 0, prm + kOffW2, Hd, 0, Z2, Hd);
+  SPH2D_LAUNCH(c, (bias_gelu_kernel), nblk(B * Hd / 2), 256, Z2, prm + kOffB2, H2, B, Hd);
+  SUR_FWD(iB, Hd, Hd, H2, Hd, 0, prm + kOffW3, Hd, 0, Z3, Hd);
+  SPH2D_LAUNCH(c, (bias_gelu_kernel), nblk(B * Hd / 2), 256, Z3, prm + kOffB3, H3, B, Hd);
+  SUR_FWD(iB, kSurOut, Hd, H3, Hd, 0, prm + kOffW4, Hd, 0, Y, kSurOut);
+  SPH2D_LAUNCH(c, (bias_kernel), nblk(B * 3), 256, Y, prm + kOffB4, B, kSurOut);
   SPH2D_LAUNCH(c, (loss_grad_kernel), unsigned(lb), 256, Y, Tb, B, c->sur_w[0], c->sur_w[1], c->sur_w[2], dY,
                part);
   SPH2D_LAUNCH(c, (sum_kernel), 1, 256, part, int(lb), loss_dev);
-  // backward.  dW = dZ^T H_prev, db = column sums of dZ, dH_prev = dZ W; each dZ overwrites a
-  // buffer whose last reader has run: dZ3 -> H3, dZ2 -> Z3, dZ1 -> Z2.
-  SUR_GEMM(kSurOut, Hd, iB, dY, kSurOut, 1, H3, Hd, 1, grad + kOffW4, Hd);
+  // backward (BF16 operands).  dW = dZ^T H_prev, db = column sums of dZ, dH_prev = dZ W; each
+  // dZ overwrites a buffer whose last reader has run: dZ3 -> H3, dZ2 -> Z3, dZ1 -> Z2.
+  SUR_BWD(kSurOut, Hd, iB, dY, kSurOut, 1, H3, Hd, 1, grad + kOffW4, Hd);
   SPH2D_LAUNCH(c, (colsum_kernel), kSurOut, 256, dY, B, kSurOut, grad + kOffB4);
   float* dZ3 = H3;
-  SUR_GEMM(iB, Hd, kSurOut, dY, kSurOut, 0, prm + kOffW4, Hd, 1, dZ3, Hd);
+  SUR_BWD(iB, Hd, kSurOut, dY, kSurOut, 0, prm + kOffW4, Hd, 1, dZ3, Hd);
   SPH2D_LAUNCH(c, (gelu_back_kernel), nblk(B * Hd), 256, dZ3, Z3, B * Hd);
-  SUR_GEMM(Hd, Hd, iB, dZ3, Hd, 1, H2, Hd, 1, grad + kOffW3, Hd);
+  SUR_BWD(Hd, Hd, iB, dZ3, Hd, 1, H2, Hd, 1, grad + kOffW3, Hd);
   SPH2D_LAUNCH(c, (colsum_kernel), Hd, 256, dZ3, B, Hd, grad + kOffB3);
   float* dZ2 = Z3;
-  SUR_GEMM(iB, Hd, Hd, dZ3, Hd, 0, prm + kOffW3, Hd, 1, dZ2, Hd);
+  SUR_BWD(iB, Hd, Hd, dZ3, Hd, 0, prm + kOffW3, Hd, 1, dZ2, Hd);
   SPH2D_LAUNCH(c, (gelu_back_kernel), nblk(B * Hd), 256, dZ2, Z2, B * Hd);
-  SUR_GEMM(Hd, Hd, iB, dZ2, Hd, 1, H1, Hd, 1, grad + kOffW2, Hd);
+  SUR_BWD(Hd, Hd, iB, dZ2, Hd, 1, H1, Hd, 1, grad + kOffW2, Hd);
   SPH2D_LAUNCH(c, (colsum_kernel), Hd, 256, dZ2, B, Hd, grad + kOffB2);
   float* dZ1 = Z2;
-  SUR_GEMM(iB, Hd, Hd, dZ2, Hd, 0, prm + kOffW2, Hd, 1, dZ1, Hd);
+  SUR_BWD(iB, Hd, Hd, dZ2, Hd, 0, prm + kOffW2, Hd, 1, dZ1, Hd);
   SPH2D_LAUNCH(c, (gelu_back_kernel), nblk(B * Hd), 256, dZ1, Z1, B * Hd);
-  SUR_GEMM(Hd, kSurIn, iB, dZ1, Hd, 1, Xb, kSurIn, 1, grad + kOffW1, kSurIn);
+  SUR_BWD(Hd, kSurIn, iB, dZ1, Hd, 1, Xb, kSurIn, 1, grad + kOffW1, kSurIn);
   SPH2D_LAUNCH(c, (colsum_kernel), Hd, 256, dZ1, B, Hd, grad + kOffB1);
-#undef SUR_GEMM
+#undef SUR_FWD
+#undef SUR_BWD
   return SPH2D_OK;
 }
 

@@ -12,7 +12,11 @@
 // Network.  6 inputs (canonical vertices) -> 64 -> 64 -> 64 -> 3, tanh-GELU, predicting the
 // triangle-averaged kernel and kernel gradient (gamma/area, grad/area); multiplying by the
 // exactly computed area removes most of the dynamic range the network would otherwise have to
-// learn.  Parameters are FP32 masters; tensor-core operands are BF16.
+// learn.  Parameters are FP32 masters.  Forward tensor-core operands (inference and the
+// training forward) are FP16 and the GELU between layers is evaluated in packed FP16
+// arithmetic on the FP32 accumulators rounded to FP16, so training sees exactly the function
+// inference evaluates; the backward GEMMs use BF16 operands (gradients span many decades).
+// All accumulation is FP32.
 //
 // Guard.  A pair is evaluated by the network only if its canonical triangle lies in the
 // training domain: largest edge in [kSurMinSize, kSurMaxSize] H, smallest angle >= 15 deg,
@@ -22,6 +26,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "pair_math.cuh"
 
@@ -106,9 +111,8 @@ SPH2D_HD void uncanonicalize_grad(const Canon& c, float gx_c, float gy_c, float&
   gy = c.sn * gx_c + c.cs * gy_r;
 }
 
-// tanh-form GELU and its derivative.  On the device tanh is the hardware approximation
-// (tanh.approx.f32, relative error about 2^-11), well below the BF16 rounding that follows it;
-// training and inference use the same function.
+// derivative of the tanh-form GELU (backward pass, FP32).  On the device tanh is the hardware
+// approximation tanh.approx.f32 (relative error about 2^-11).
 SPH2D_HD float tanh_act(float u) {
 #if defined(__CUDA_ARCH__)
   float t;
@@ -118,12 +122,6 @@ SPH2D_HD float tanh_act(float u) {
   return tanhf(u);
 #endif
 }
-SPH2D_HD float gelu_f(float z) {
-  const float k = 0.7978845608028654f;   // sqrt(2/pi)
-  const float u = k * z * (1.0f + 0.044715f * z * z);
-  const float h = 0.5f * z;
-  return h + h * tanh_act(u);
-}
 SPH2D_HD float gelu_grad_f(float z) {
   const float k = 0.7978845608028654f;
   const float u = k * z * (1.0f + 0.044715f * z * z);
@@ -132,17 +130,47 @@ SPH2D_HD float gelu_grad_f(float z) {
 }
 
 #if defined(__CUDACC__)
-// m16n8k16 BF16 x BF16 -> FP32 tensor-core MMA (row.col)
-__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b) {
+// m16n8k16 tensor-core MMA, FP32 accumulation (row.col), BF16 or FP16 operands
+__device__ __forceinline__ void mma_16816(float* d, const uint32_t* a, const uint32_t* b, __nv_bfloat16) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
+__device__ __forceinline__ void mma_16816(float* d, const uint32_t* a, const uint32_t* b, __half) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ __nv_bfloat16 to_op(float v, __nv_bfloat16) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ __half to_op(float v, __half) { return __float2half_rn(v); }
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) { return *reinterpret_cast<const uint32_t*>(&v); }
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) { return h2_bits(__floats2half2_rn(lo, hi)); }
+
+// four 8x8 b16 matrices from shared memory; lane l gives the address of row (l & 7) of
+// matrix (l >> 3); register i of every lane receives its fragment of matrix i
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* smem_row) {
+  const unsigned addr = static_cast<unsigned>(__cvta_generic_to_shared(smem_row));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// tanh-form GELU on a packed FP16 pair: g = h + h tanh(u), h = z/2, u = k z (1 + a z^2).
+// For |z| > 255, z^2 overflows to inf, tanh(u) = +-1 and g is z or 0 as the limit requires.
+__device__ __forceinline__ __half2 gelu_h2(__half2 z) {
+  const __half2 k = __float2half2_rn(0.7978845608028654f);
+  const __half2 ka = __float2half2_rn(0.7978845608028654f * 0.044715f);
+  const __half2 half = __float2half2_rn(0.5f);
+  const __half2 u = __hmul2(__hfma2(__hmul2(z, z), ka, k), z);
+  uint32_t t;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h2_bits(u)));
+  const __half2 h = __hmul2(z, half);
+  return __hfma2(h, *reinterpret_cast<const __half2*>(&t), h);
 }
 #endif
 

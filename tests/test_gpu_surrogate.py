@@ -1,5 +1,6 @@
 """Learned surrogate through the C-ABI against the FP64 references: the network and its
-gradient against oracle/surrogate.py (BF16 operand rounding emulated), the guard and the
+gradient against oracle/surrogate.py (tensor-core operand roundings emulated: FP16 forward,
+BF16 backward), the guard and the
 canonical frame, the analytic fallback against the quadrature oracle, training
 determinism, checkpoint round trip and resume, the accuracy a trained network reaches on
 held-out pairs, and serving over a culled pair list."""
@@ -68,15 +69,16 @@ def test_forward_matches_reference(ctx):
     ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
     X = canonical_inputs(3001, 22)                       # ragged: 93 full 32-row chunks + 25
     y = ctx.surrogate_forward(_t(X)).cpu().numpy().astype(np.float64)
-    ref, _ = S.forward(prm, X.astype(np.float64), emulate_bf16=True)
+    ref, _ = S.forward(prm, X.astype(np.float64), emulate_tc=True)
     scale = np.sqrt(np.mean(ref ** 2, axis=0))
     err = np.abs(y - ref) / scale
-    # FP32 accumulation order and the hardware tanh (rel. error ~2^-11) can move a BF16
-    # rounding by one step (2^-8 relative) for a few activations per row
-    assert np.median(err) < 2e-3, np.median(err)
-    assert err.max() < 2e-2, err.max()
-    # without the BF16 emulation the reference is visibly farther: the emulation is real
-    ref64, _ = S.forward(prm, X.astype(np.float64), emulate_bf16=False)
+    # the reference follows the GPU's FP16 roundings step by step; what remains is FP32
+    # accumulation order and the hardware tanh, each able to move an FP16 rounding by one step
+    # (2^-11 relative) in a few activations per row
+    assert np.median(err) < 5e-4, np.median(err)
+    assert err.max() < 1e-2, err.max()
+    # without the operand rounding the reference is visibly farther: the emulation is real
+    ref64, _ = S.forward(prm, X.astype(np.float64), emulate_tc=False)
     assert np.median(np.abs(ref64 - ref) / scale) > 2 * np.median(err)
 
 
@@ -90,7 +92,7 @@ def test_grad_matches_reference(ctx, B):
     g, loss = ctx.surrogate_grad(_t(X), _t(T))
     g = g.cpu().numpy().astype(np.float64)
     w = S.loss_weights(C2)
-    L, gref = S.loss_and_grad(prm, X.astype(np.float64), T.astype(np.float64), w, emulate_bf16=True)
+    L, gref = S.loss_and_grad(prm, X.astype(np.float64), T.astype(np.float64), w, emulate_tc=True)
     assert abs(float(loss.item()) - L) <= 1e-2 * L
     o = 0
     for name, shape in S.SHAPES:
@@ -140,7 +142,7 @@ def test_network_values_and_frame(ctx):
     pairs, H = _world_pairs(20000, 52)
     out, acc = ctx.surrogate_pairs(_t(pairs), H)
     out, acc = out.cpu().numpy().astype(np.float64), acc.cpu().numpy().astype(bool)
-    ref, cn = S.surrogate_local(prm, _local(pairs, H), emulate_bf16=True)
+    ref, cn = S.surrogate_local(prm, _local(pairs, H), emulate_tc=True)
     ok = acc & cn["accept"] & (S.frame_margin(cn) > 1e-4) & (S.guard_margin(cn) > 1e-5)
     assert ok.sum() > 5000
     # compare the raw network outputs: divide the area back out, gradient to H = 1 units
@@ -149,8 +151,8 @@ def test_network_values_and_frame(ctx):
     want = ref[ok] / a
     scale = np.sqrt(np.mean(want ** 2, axis=0))
     err = np.abs(got - want) / scale
-    assert np.median(err) < 2e-3, np.median(err)
-    assert err.max() < 2e-2, err.max()
+    assert np.median(err) < 5e-4, np.median(err)
+    assert err.max() < 1e-2, err.max()
 
 
 def test_training_is_deterministic_and_learns(ctx):
@@ -234,9 +236,9 @@ def test_error_statuses(ctx):
 @pytest.fixture(scope="module")
 def trained(ctx):
     rng = np.random.default_rng(81)
-    pairs = W.surrogate_training_pairs(1_000_000, rng)
+    pairs = W.surrogate_training_pairs(4_000_000, rng)
     ctx.surrogate_init(KERNEL, 5)
-    loss, used = ctx.surrogate_train(_t(pairs), 1.0, epochs=12, batch=4096, lr=3e-3, seed=5)
+    loss, used = ctx.surrogate_train(_t(pairs), 1.0, epochs=40, batch=16384, lr=5e-3, seed=5)
     return ctx.surrogate_params().numpy().copy(), loss, used
 
 
@@ -254,8 +256,8 @@ def test_trained_accuracy_on_held_out_pairs(ctx, trained):
           f"accepted {acc.mean():.3f}; err p50 {np.median(ea):.2e} p99 {np.percentile(ea, 99):.2e} "
           f"max {ea.max():.2e}; fallback max {err[~acc].max():.2e}")
     assert err[~acc].max() <= TOL_FP32
-    assert np.percentile(ea, 99) < 5e-3
-    assert ea.max() < 2e-2
+    assert np.percentile(ea, 99) < 1e-3
+    assert ea.max() < 5e-3
 
 
 def test_serving_over_pair_list(ctx, trained):

@@ -76,12 +76,30 @@ def test_gelu_derivative_matches_differences():
     assert abs(S.gelu(np.array([-10.0]))[0]) < 1e-12
 
 
+def test_f16_gelu_follows_gelu():
+    """the stepwise FP16 GELU stays within a few FP16 steps of the exact one (relative, plus
+    an absolute |z| 2^-12 where tanh rounds to -1 and the tail becomes 0), and has the exact
+    limits (0 for very negative z, z for large z, including z^2 overflow)."""
+    z = np.linspace(-12, 12, 4001)
+    g, e = S.gelu_f16(z), S.gelu(S.f16(z))
+    assert np.all(np.abs(g - e) <= 4e-3 * np.abs(e) + np.abs(z) * 2.0 ** -11)
+    big = np.array([-300.0, -20.0, 20.0, 300.0, 1000.0])
+    assert S.gelu_f16(big).tolist() == [0.0, 0.0, 20.0, 300.0, 1000.0]
+
+
 def test_zero_weights_give_output_bias():
     p = S.unpack(np.zeros(S.N_PARAMS))
     p["b4"] = np.array([0.5, -1.25, 2.0])
     p["b1"] = np.full(64, 3.0)
     Y, _ = S.forward(S.pack(p), np.random.default_rng(0).normal(size=(5, 6)))
     assert np.array_equal(Y, np.tile(p["b4"], (5, 1)))
+
+
+def test_f16_rounding_by_hand():
+    # 11 significant bits: 2049 lies halfway between 2048 and 2050 -> even 2048
+    assert S.f16(2049.0) == 2048.0 and S.f16(2051.0) == 2052.0
+    assert S.f16(1.0 + 2.0 ** -11) == 1.0 and S.f16(1.0 + 2.0 ** -11 + 2.0 ** -20) == 1.0 + 2.0 ** -10
+    assert S.f16(65504.0) == 65504.0 and S.f16(-0.5) == -0.5
 
 
 def test_bf16_rounding_by_hand():
