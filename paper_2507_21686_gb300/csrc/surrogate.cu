@@ -302,6 +302,8 @@ struct SurSmem {
   float yout[4][32][kSurN4];                 // per-warp outputs
 };
 
+// The hidden activations are carried as 2 GELU(z) (one FP16 operation less per pair of
+// values), so the weights that consume them, W2, W3 and W4, are stored halved: exact in FP16.
 __device__ void load_sur_weights(SurSmem& s, const float* __restrict__ prm) {
   for (int i = threadIdx.x; i < kSurHid * kW1Stride; i += blockDim.x) {
     const int n = i / kW1Stride, k = i % kW1Stride;
@@ -309,12 +311,13 @@ __device__ void load_sur_weights(SurSmem& s, const float* __restrict__ prm) {
   }
   for (int i = threadIdx.x; i < kSurHid * kWStride; i += blockDim.x) {
     const int n = i / kWStride, k = i % kWStride;
-    s.w2[n][k] = __float2half_rn(k < kSurHid ? prm[kOffW2 + n * kSurHid + k] : 0.0f);
-    s.w3[n][k] = __float2half_rn(k < kSurHid ? prm[kOffW3 + n * kSurHid + k] : 0.0f);
+    s.w2[n][k] = __hmul(__float2half_rn(k < kSurHid ? prm[kOffW2 + n * kSurHid + k] : 0.0f), __float2half(0.5f));
+    s.w3[n][k] = __hmul(__float2half_rn(k < kSurHid ? prm[kOffW3 + n * kSurHid + k] : 0.0f), __float2half(0.5f));
   }
   for (int i = threadIdx.x; i < kSurN4 * kWStride; i += blockDim.x) {
     const int n = i / kWStride, k = i % kWStride;
-    s.w4[n][k] = __float2half_rn(n < kSurOut && k < kSurHid ? prm[kOffW4 + n * kSurHid + k] : 0.0f);
+    s.w4[n][k] = __hmul(__float2half_rn(n < kSurOut && k < kSurHid ? prm[kOffW4 + n * kSurHid + k] : 0.0f),
+                        __float2half(0.5f));
   }
   for (int i = threadIdx.x; i < kSurHid; i += blockDim.x) {
     s.b1[i] = prm[kOffB1 + i];
@@ -326,27 +329,26 @@ __device__ void load_sur_weights(SurSmem& s, const float* __restrict__ prm) {
 
 // hidden layer on a 16-row tile: acc[8 n8 tiles][4] = bias + a W^T.  One ldmatrix.x4 gives the
 // B fragments of two n8 tiles for one k16 block (matrices: tile j k0-7, tile j k8-15,
-// tile j+1 k0-7, tile j+1 k8-15).
+// tile j+1 k0-7, tile j+1 k8-15); the first k16 block takes the bias as its accumulator input.
 template <int KBLOCKS, int WSTRIDE>
 __device__ __forceinline__ void layer_hidden(const __half (*w)[WSTRIDE], const float* b, const uint32_t (*a)[4],
                                              float (*acc)[4]) {
   const int lane = threadIdx.x & 31, t = lane & 3, mat = lane >> 3, r = lane & 7;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float bx = b[j * 8 + 2 * t], by = b[j * 8 + 2 * t + 1];
-    acc[j][0] = bx;
-    acc[j][1] = by;
-    acc[j][2] = bx;
-    acc[j][3] = by;
-  }
-#pragma unroll
   for (int j = 0; j < 8; j += 2) {
+    const float2 b0 = *reinterpret_cast<const float2*>(&b[j * 8 + 2 * t]);
+    const float2 b1 = *reinterpret_cast<const float2*>(&b[(j + 1) * 8 + 2 * t]);
 #pragma unroll
     for (int kb = 0; kb < KBLOCKS; ++kb) {
       uint32_t f[4];
       ldsm_x4(f, &w[(j + (mat >> 1)) * 8 + r][kb * 16 + (mat & 1) * 8]);
-      mma_16816(acc[j], a[kb], f, __half());
-      mma_16816(acc[j + 1], a[kb], f + 2, __half());
+      if (kb == 0) {
+        mma_16816_bias(acc[j], a[0], f, b0.x, b0.y);
+        mma_16816_bias(acc[j + 1], a[0], f + 2, b1.x, b1.y);
+      } else {
+        mma_16816(acc[j], a[kb], f, __half());
+        mma_16816(acc[j + 1], a[kb], f + 2, __half());
+      }
     }
   }
 }
@@ -355,26 +357,26 @@ __device__ __forceinline__ void layer_hidden(const __half (*w)[WSTRIDE], const f
 __device__ __forceinline__ void layer_out(const __half (*w)[kWStride], const float* b, const uint32_t (*a)[4],
                                           float* acc) {
   const int lane = threadIdx.x & 31, t = lane & 3, mat = lane >> 3, r = lane & 7;
-  acc[0] = acc[2] = b[2 * t];
-  acc[1] = acc[3] = b[2 * t + 1];
+  const float2 bb = *reinterpret_cast<const float2*>(&b[2 * t]);
 #pragma unroll
   for (int kb = 0; kb < 4; kb += 2) {
     uint32_t f[4];
     ldsm_x4(f, &w[r][kb * 16 + mat * 8]);
-    mma_16816(acc, a[kb], f, __half());
+    if (kb == 0) mma_16816_bias(acc, a[0], f, bb.x, bb.y);
+    else mma_16816(acc, a[kb], f, __half());
     mma_16816(acc, a[kb + 1], f + 2, __half());
   }
 }
 
-// GELU on the accumulators (rounded to FP16, packed arithmetic), repacked as the next
+// 2 GELU on the accumulators (rounded to FP16, packed arithmetic), repacked as the next
 // layer's A fragments: k16 block kb takes the n8 tiles 2kb and 2kb+1
 __device__ __forceinline__ void act_to_a(const float (*acc)[4], uint32_t (*a)[4]) {
 #pragma unroll
   for (int kb = 0; kb < 4; ++kb) {
-    a[kb][0] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb][0], acc[2 * kb][1])));
-    a[kb][1] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb][2], acc[2 * kb][3])));
-    a[kb][2] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb + 1][0], acc[2 * kb + 1][1])));
-    a[kb][3] = h2_bits(gelu_h2(__floats2half2_rn(acc[2 * kb + 1][2], acc[2 * kb + 1][3])));
+    a[kb][0] = h2_bits(gelu2x_h2(__floats2half2_rn(acc[2 * kb][0], acc[2 * kb][1])));
+    a[kb][1] = h2_bits(gelu2x_h2(__floats2half2_rn(acc[2 * kb][2], acc[2 * kb][3])));
+    a[kb][2] = h2_bits(gelu2x_h2(__floats2half2_rn(acc[2 * kb + 1][0], acc[2 * kb + 1][1])));
+    a[kb][3] = h2_bits(gelu2x_h2(__floats2half2_rn(acc[2 * kb + 1][2], acc[2 * kb + 1][3])));
   }
 }
 
@@ -456,11 +458,10 @@ struct SurArgs {
 // per-pair FP32 local frame for the two pair sources: independent pairs (double [P][8]) or
 // the culled pair list (FP32 particles and triangles, same arithmetic as the analytic kernel)
 template <bool LIST>
-__device__ __forceinline__ void load_local(const IntArgs& a, const double* pairs, int64_t q, float* lf) {
+__device__ __forceinline__ void load_local(const IntArgs& a, const double* pairs, int64_t q, float ih, float* lf) {
   if (LIST) {
     const float4 p = a.parts[__ldg(a.pair_pid + q)];
     const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-    const float ih = float(a.invH);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(128, 6) surrogate_values_kernel(IntArgs a, con
   for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += nw) {
     const int64_t q = ch * 32 + lane;
     float lf[6] = {0, 0, 0, 0, 0, 0};
-    if (q < a.P) load_local<LIST>(a, pairs, q, lf);
+    if (q < a.P) load_local<LIST>(a, pairs, q, ih, lf);
     const Canon c = canonicalize(lf);
     const bool use = (q < a.P) && c.accept;
     stage_row(s, warp, lane, c.x, use);

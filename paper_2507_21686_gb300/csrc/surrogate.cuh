@@ -55,12 +55,21 @@ struct Canon {
   bool accept;         // inside the surrogate's domain
 };
 
+SPH2D_HD float rsqrt_canon(float x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
+
 SPH2D_HD Canon canonicalize(const float* v) {
   Canon c;
   const float cx = (v[0] + v[2] + v[4]) * (1.0f / 3.0f), cy = (v[1] + v[3] + v[5]) * (1.0f / 3.0f);
-  const float r = sqrt(cx * cx + cy * cy);
-  c.cs = r > 0.0f ? cx / r : 1.0f;
-  c.sn = r > 0.0f ? cy / r : 0.0f;
+  const float r2 = cx * cx + cy * cy;
+  const float rinv = r2 > 0.0f ? rsqrt_canon(r2) : 0.0f;
+  c.cs = r2 > 0.0f ? cx * rinv : 1.0f;
+  c.sn = r2 > 0.0f ? cy * rinv : 0.0f;
   float q[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -83,24 +92,23 @@ SPH2D_HD Canon canonicalize(const float* v) {
     c.x[2 * j] = q[2 * s];
     c.x[2 * j + 1] = c.refl * q[2 * s + 1];
   }
-  c.area = 0.5f * fabs(cr);
-  // domain guard
-  float lmax = 0.0f, l[3];
+  c.area = 0.5f * fabsf(cr);
+  // domain guard on squared quantities (no division or square root): edge lengths L_e^2,
+  // and sin(angle at a vertex) = 2 area / (product of its edges), compared squared
+  float L[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int b = e == 2 ? 0 : e + 1;
     const float ex = c.x[2 * b] - c.x[2 * e], ey = c.x[2 * b + 1] - c.x[2 * e + 1];
-    l[e] = sqrt(ex * ex + ey * ey);
-    lmax = fmax(lmax, l[e]);
+    L[e] = ex * ex + ey * ey;
   }
-  // sin of the angle at vertex j is 2 area / (product of its two edges)
-  const float s0 = 2.0f * c.area / fmax(l[0] * l[2], 1e-30f);
-  const float s1 = 2.0f * c.area / fmax(l[0] * l[1], 1e-30f);
-  const float s2 = 2.0f * c.area / fmax(l[1] * l[2], 1e-30f);
-  const float smin = fmin(s0, fmin(s1, s2));
-  const float rmax = sqrt(fmax(d0, fmax(d1, d2)));
-  c.accept = c.area > 0.0f && lmax >= kSurMinSize && lmax <= kSurMaxSize && smin >= kSurSinMinAngle &&
-             r >= kSurMinCentroid && rmax <= kSurMaxRadius && isfinite(c.area) && isfinite(r);
+  const float lmax2 = fmaxf(L[0], fmaxf(L[1], L[2]));
+  const float cr2 = cr * cr, sm2 = kSurSinMinAngle * kSurSinMinAngle;
+  const bool angles = cr2 >= sm2 * (L[0] * L[2]) && cr2 >= sm2 * (L[0] * L[1]) && cr2 >= sm2 * (L[1] * L[2]);
+  const float rmax2 = fmaxf(d0, fmaxf(d1, d2));
+  c.accept = c.area > 0.0f && lmax2 >= kSurMinSize * kSurMinSize && lmax2 <= kSurMaxSize * kSurMaxSize &&
+             angles && r2 >= kSurMinCentroid * kSurMinCentroid && rmax2 <= kSurMaxRadius * kSurMaxRadius &&
+             isfinite(c.area) && isfinite(r2);
   return c;
 }
 
@@ -162,15 +170,31 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* smem_row) {
 
 // tanh-form GELU on a packed FP16 pair: g = h + h tanh(u), h = z/2, u = k z (1 + a z^2).
 // For |z| > 255, z^2 overflows to inf, tanh(u) = +-1 and g is z or 0 as the limit requires.
-__device__ __forceinline__ __half2 gelu_h2(__half2 z) {
+__device__ __forceinline__ __half2 tanh_u_h2(__half2 z) {
   const __half2 k = __float2half2_rn(0.7978845608028654f);
   const __half2 ka = __float2half2_rn(0.7978845608028654f * 0.044715f);
-  const __half2 half = __float2half2_rn(0.5f);
   const __half2 u = __hmul2(__hfma2(__hmul2(z, z), ka, k), z);
   uint32_t t;
   asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h2_bits(u)));
-  const __half2 h = __hmul2(z, half);
-  return __hfma2(h, *reinterpret_cast<const __half2*>(&t), h);
+  return *reinterpret_cast<const __half2*>(&t);
+}
+__device__ __forceinline__ __half2 gelu_h2(__half2 z) {
+  const __half2 h = __hmul2(z, __float2half2_rn(0.5f));
+  return __hfma2(h, tanh_u_h2(z), h);
+}
+// 2 GELU(z) = z + z tanh(u): the same value times two, exactly (scaling by 2 commutes with
+// every FP16 rounding above, outside the subnormal range); inference folds the 1/2 into the
+// next layer's weights
+__device__ __forceinline__ __half2 gelu2x_h2(__half2 z) { return __hfma2(z, tanh_u_h2(z), z); }
+
+// m16n8k16 FP16 MMA whose accumulator input is a per-column bias (bx, by) of the lane's two
+// columns, for both of its rows
+__device__ __forceinline__ void mma_16816_bias(float* d, const uint32_t* a, const uint32_t* b, float bx, float by) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%10,%11};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(bx), "f"(by));
 }
 #endif
 
