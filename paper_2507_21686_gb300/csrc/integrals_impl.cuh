@@ -219,6 +219,253 @@ __global__ void __launch_bounds__(128) integrals_kernel(IntArgs a) {
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
 
+// ---------------------------------------------------------------------------------------
+// cubic spline in three launches.  k = 2 (1-q)^3_+ - (1-2q)^3_+ (scaled as in tri_raw): the
+// second piece has support H/2 and is exactly zero for a triangle at distance >= H/2, which
+// holds for most pairs; evaluated in place it would still run on every lane of a warp that
+// holds one near pair.  So: (1) every pair's first piece into a per-pair value buffer, pairs
+// within H/2 appended to a list; (2) the second piece over the compacted list, added to the
+// pair's value; (3) per-particle sums over the per-pair values in pair order (chunk
+// reduction and crossing slots as integrals_kernel).  Each pair's value is piece1 + piece2 in
+// that order, so results do not depend on the list order.
+// ---------------------------------------------------------------------------------------
+// origin within 1/2 (+ a small margin) of the local triangle: inside, or an edge segment
+// closer than that (no division)
+template <typename R>
+__device__ __forceinline__ bool near_half(const R* l) {
+  const R lim2 = R(0.501) * R(0.501);
+  bool pos = false, neg = false, near = false;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int b = e == 2 ? 0 : e + 1;
+    const R ax = l[2 * e], ay = l[2 * e + 1], bx = l[2 * b], by = l[2 * b + 1];
+    const R ex = bx - ax, ey = by - ay;
+    const R cr = ax * ey - ay * ex;
+    pos = pos || cr > R(0);
+    neg = neg || cr < R(0);
+    const R l2 = ex * ex + ey * ey, tn = -(ax * ex + ay * ey);
+    const bool n = tn <= R(0) ? (ax * ax + ay * ay < lim2)
+                              : (tn >= l2 ? (bx * bx + by * by < lim2) : (cr * cr < lim2 * l2));
+    near = near || n;
+  }
+  return near || (pos != neg);
+}
+
+// one piece of the cubic spline for a local triangle of orientation s != 0 -> v (scaled)
+template <typename R, bool MOM>
+__device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double C, double invH, R* v) {
+  const R sc = piece ? R(2) : R(1);
+  PairOut<R> h;
+  clear(h);
+  tri_poly<R, PolyCube, MOM, true>(sc * l[0], sc * l[1], sc * l[2], sc * l[3], sc * l[4], sc * l[5], h);
+  const R k = R(C) * R(s);
+  const R wg = piece ? R(-0.25) : R(2), wd = piece ? R(-0.5) : R(2);
+  v[0] = (k * wg) * h.g;
+  v[1] = (-k * R(invH) * wd) * h.gx;
+  v[2] = (-k * R(invH) * wd) * h.gy;
+  if (MOM) {
+    const R w1 = piece ? R(-0.125) : R(2), w2 = piece ? R(-0.0625) : R(2), w3 = piece ? R(-0.03125) : R(2);
+    v[3] = (k * wg) * h.m[0];
+#pragma unroll
+    for (int i = 1; i < 3; ++i) v[3 + i] = (k * w1) * h.m[i];
+#pragma unroll
+    for (int i = 3; i < 6; ++i) v[3 + i] = (k * w2) * h.m[i];
+#pragma unroll
+    for (int i = 6; i < 10; ++i) v[3 + i] = (k * w3) * h.m[i];
+  }
+}
+
+template <typename OT, bool MOM>
+__global__ void __launch_bounds__(128) cubic_first_kernel(IntArgs a, OT* __restrict__ vals,
+                                                          int64_t* __restrict__ list,
+                                                          unsigned long long* __restrict__ count) {
+  constexpr int NV = MOM ? 13 : 3;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  unsigned long long fixes = 0;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < a.P; base += stride) {
+    const int64_t q = base + lane;
+    bool need = false;
+    int fix = 0;
+    if (q < a.P) {
+      const int pid = __ldg(a.pair_pid + q);
+      const float4 p = a.parts[pid];
+      const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
+      OT v[NV];
+      bool done = false;
+      if (sizeof(OT) == sizeof(float)) {
+        const float ih = float(a.invH);
+        float lf[6];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+          lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+          ok = ok && fabsf(lf[2 * j]) <= kFixupCoordLimit && fabsf(lf[2 * j + 1]) <= kFixupCoordLimit;
+        }
+        if (ok) {
+          const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
+          float w[13];
+          if (s == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) w[i] = 0.0f;
+          } else {
+            cubic_piece<float, MOM>(lf, 0, s, a.C, a.invH, w);
+            need = near_half<float>(lf);
+          }
+#pragma unroll
+          for (int i = 0; i < NV; ++i) ok = ok && isfinite(w[i]);
+          if (ok) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
+            done = true;
+          }
+        }
+      }
+      if (!done) {
+        double ld[6], w[13];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+          ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+        }
+        if (sizeof(OT) == sizeof(double)) {
+          const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+          if (s == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) w[i] = 0.0;
+            need = false;
+          } else {
+            cubic_piece<double, MOM>(ld, 0, s, a.C, a.invH, w);
+            need = near_half<double>(ld);
+          }
+        } else {
+          // FP64 fix-up of an FP32 pair: both pieces here, nothing left for the list
+          eval_local<double, KID_CUBIC, MOM>(ld, a.C, a.invH, w);
+          need = false;
+          fix = 1;
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
+      }
+      OT* out = vals + q * NV;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) out[i] = v[i];
+    }
+    fixes += __popc(__ballot_sync(0xffffffffu, fix));
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+      unsigned long long b = 0;
+      const int leader = __ffs(m) - 1;
+      if (lane == leader) b = atomicAdd(count, (unsigned long long)__popc(m));
+      b = __shfl_sync(0xffffffffu, b, leader);
+      if (need) list[b + __popc(m & ((1u << lane) - 1u))] = q;
+    }
+  }
+  if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
+}
+
+template <typename OT, bool MOM>
+__global__ void __launch_bounds__(128) cubic_second_kernel(IntArgs a, OT* __restrict__ vals,
+                                                           const int64_t* __restrict__ list,
+                                                           const unsigned long long* __restrict__ count) {
+  constexpr int NV = MOM ? 13 : 3;
+  const int64_t n = int64_t(*count);
+  unsigned long long fixes = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t q = list[i];
+    const float4 p = a.parts[__ldg(a.pair_pid + q)];
+    const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
+    OT v[NV];
+    bool done = false;
+    if (sizeof(OT) == sizeof(float)) {
+      const float ih = float(a.invH);
+      float lf[6], w[13];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+        lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+      }
+      const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
+      cubic_piece<float, MOM>(lf, 1, s, a.C, a.invH, w);
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) ok = ok && isfinite(w[k]);
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
+        done = true;
+      }
+    }
+    if (!done) {
+      double ld[6], w[13];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+        ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+      }
+      const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+      cubic_piece<double, MOM>(ld, 1, s, a.C, a.invH, w);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
+      if (sizeof(OT) == sizeof(float)) ++fixes;
+    }
+    OT* out = vals + q * NV;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = out[k] + v[k];
+  }
+  if (fixes) atomicAdd(a.nfix, fixes);
+}
+
+// per-particle sums of per-pair values [P][NV] in pair order
+template <typename OT, bool MOM>
+__global__ void __launch_bounds__(128) reduce_pairs_kernel(IntArgs a, const OT* __restrict__ vals) {
+  constexpr int NV = MOM ? 13 : 3;
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+    const int64_t q = ch * 32 + lane;
+    int pid = -1;
+    OT v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = OT(0);
+    if (q < a.P) {
+      pid = __ldg(a.pair_pid + q);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = vals[q * NV + i];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int pn = __shfl_down_sync(0xffffffffu, pid, o);
+      const bool same = (lane + o < 32) && (pn == pid);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const OT t = __shfl_down_sync(0xffffffffu, v[i], o);
+        if (same) v[i] += t;
+      }
+    }
+    const int pprev = __shfl_up_sync(0xffffffffu, pid, 1);
+    const bool head = pid >= 0 && (lane == 0 || pprev != pid);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int last_head = 31 - __clz(heads);
+    if (head) {
+      const int64_t cs = ch * 32;
+      const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
+      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, MOM>(a, pid, v);
+      OT* slots = static_cast<OT*>(a.slots);
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) slots[(ch * 2) * NV + i] = v[i];
+      }
+      if (lane == last_head) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) slots[(ch * 2 + 1) * NV + i] = v[i];
+      }
+    }
+  }
+}
+
 // particles without pairs get zeros; particles whose pairs span chunks add their partials
 template <typename OT, bool MOM>
 __global__ void finalize_kernel(IntArgs a) {
@@ -282,8 +529,49 @@ __global__ void __launch_bounds__(256) pair_entry_kernel(const double* __restric
 // ---------------------------------------------------------------------------------------
 // host launchers for one output precision
 // ---------------------------------------------------------------------------------------
+template <typename K>
+static unsigned resident_blocks(Ctx* c, K kern, int64_t wanted) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
+}
+
+template <typename OT, bool MOM>
+static sph2d_status run_cubic(Ctx* c, IntArgs a) {
+  constexpr int NV = MOM ? 13 : 3;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(a.P > 0 ? a.P : 1) * NV * sizeof(OT));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, size_t(a.P > 0 ? a.P : 1) * sizeof(int64_t) + 64);
+  if (s != SPH2D_OK) return s;
+  a.slots = c->slots.ptr;
+  OT* vals = static_cast<OT*>(c->pair_vals.ptr);
+  int64_t* list = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
+  auto* count = static_cast<unsigned long long*>(c->pair_list2.ptr);
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "memset");
+  if (a.P > 0) {
+    const int64_t blocks = (a.P + 127) / 128;
+    SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MOM>), resident_blocks(c, cubic_first_kernel<OT, MOM>, blocks), 128,
+                 a, vals, list, count);
+    SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MOM>), resident_blocks(c, cubic_second_kernel<OT, MOM>, blocks), 128,
+                 a, vals, list, count);
+    SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MOM>), resident_blocks(c, reduce_pairs_kernel<OT, MOM>, (nchunks + 3) / 4),
+                 128, a, vals);
+  }
+  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MOM>), unsigned((a.N + 255) / 256), 256, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
+  return SPH2D_OK;
+}
+
 template <typename OT, int KID, bool MOM>
 static sph2d_status run_integrals(Ctx* c, IntArgs a) {
+  if constexpr (KID == KID_CUBIC) {
+    return run_cubic<OT, MOM>(c, a);
+  } else {
   static int grid_blocks = 0;
   if (grid_blocks == 0) {
     int per_sm = 0, sms = 0;
@@ -305,6 +593,7 @@ static sph2d_status run_integrals(Ctx* c, IntArgs a) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
   return SPH2D_OK;
+  }
 }
 
 template <typename OT>

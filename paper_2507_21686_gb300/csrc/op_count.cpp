@@ -114,13 +114,47 @@ template <> struct Acc<Counted<double>> {
 template <> struct Acc<Counted<float>> : AccFF<Counted<float>> {};
 template <> struct AccSel<Counted<double>, PolyWC6> { using type = AccDD<Counted<double>>; };
 
+// distance from the particle to the local triangle below 1/2: the cubic spline's second piece
+// (support H/2) is non-zero only then (plain double; the decision is not counted as work)
+static bool within_half(const double* l) {
+  bool pos = false, neg = false, near = false;
+  for (int e = 0; e < 3; ++e) {
+    const int b = e == 2 ? 0 : e + 1;
+    const double ax = l[2 * e], ay = l[2 * e + 1], bx = l[2 * b], by = l[2 * b + 1];
+    const double ex = bx - ax, ey = by - ay, cr = ax * ey - ay * ex;
+    pos = pos || cr > 0;
+    neg = neg || cr < 0;
+    const double l2 = ex * ex + ey * ey, tn = -(ax * ex + ay * ey);
+    const double d2 = tn <= 0 ? ax * ax + ay * ay : (tn >= l2 ? bx * bx + by * by : cr * cr / l2);
+    near = near || d2 < 0.25;
+  }
+  return near || (pos != neg);
+}
+
 template <typename R, int KID, bool MOM>
 static void count_one(const double* l) {
   R v[6];
   for (int j = 0; j < 6; ++j) v[j] = R(l[j]);
   PairOut<R> o;
   (void)tri_orientation<R>(v[0], v[1], v[2], v[3], v[4], v[5]);
-  tri_raw<R, KID, MOM>(v[0], v[1], v[2], v[3], v[4], v[5], o);
+  if (KID == KID_CUBIC) {
+    // first piece always, second piece only where it is non-zero, as the kernels evaluate it
+    clear(o);
+    tri_poly<R, PolyCube, MOM, true>(v[0], v[1], v[2], v[3], v[4], v[5], o);
+    if (within_half(l)) {
+      PairOut<R> h;
+      clear(h);
+      const R sc(2.0);
+      tri_poly<R, PolyCube, MOM, true>(sc * v[0], sc * v[1], sc * v[2], sc * v[3], sc * v[4], sc * v[5], h);
+      o.g = o.g + h.g;
+      o.gx = o.gx + h.gx;
+      o.gy = o.gy + h.gy;
+      if (MOM)
+        for (int m = 0; m < 10; ++m) o.m[m] = o.m[m] + h.m[m];
+    }
+  } else {
+    tri_raw<R, KID, MOM>(v[0], v[1], v[2], v[3], v[4], v[5], o);
+  }
   // constants and orientation applied per output, as in the kernels
   const R k(1.0);
   R s = k * o.g;

@@ -196,7 +196,7 @@ sph2d_status sph2d_destroy(sph2d_ctx* h) {
   DevBuf* bufs[] = {&c.cell_start, &c.cell_cursor, &c.cell_tris, &c.block_tmp, &c.scan_tmp,
                     &c.pair_off,  &c.pair_tri,    &c.pair_pid,  &c.counts,    &c.slots,
                     &c.host_flags_dev, &c.misc, &c.tri_off, &c.tri_pid, &c.tri_cursor,
-                    &c.bwd_g, &c.bwd_grad, &c.sur_prm, &c.sur_split, &c.sur_act,
+                    &c.bwd_g, &c.bwd_grad, &c.pair_vals, &c.pair_list2, &c.sur_prm, &c.sur_split, &c.sur_act,
                     &c.sur_data, &c.sur_idx, &c.sur_vals, &c.sur_fb};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);

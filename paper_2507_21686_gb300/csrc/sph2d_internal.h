@@ -39,7 +39,8 @@ struct Ctx {
   Cells cells;
   // scratch buffers (named slots)
   DevBuf cell_start, cell_cursor, cell_tris, block_tmp, scan_tmp, pair_off, pair_tri, pair_pid,
-      counts, slots, host_flags_dev, misc, tri_off, tri_pid, tri_cursor, bwd_g, bwd_grad;
+      counts, slots, host_flags_dev, misc, tri_off, tri_pid, tri_cursor, bwd_g, bwd_grad,
+      pair_vals, pair_list2;   // per-pair values and second-piece list of the cubic spline
   // learned surrogate: parameters (+ Adam state), training data and scratch, serving scratch
   DevBuf sur_prm, sur_split, sur_act, sur_data, sur_idx, sur_vals, sur_fb;
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
