@@ -148,6 +148,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the launches one integral pass of each kernel makes (FP32 + fix-up, moments)
+KERNEL_LAUNCHES = {
+    "wendland_c2": "integrals_kernel<float,wendland_c2,moments> + finalize_kernel",
+    "wendland_c4": "integrals_kernel<float,wendland_c4,moments> + finalize_kernel",
+    "wendland_c6": "integrals_kernel<float,wendland_c6,moments> + finalize_kernel",
+    "cubic_spline": "cubic_first_kernel + cubic_second_kernel + reduce_pairs_kernel + finalize_kernel (float, moments)",
+}
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic.json")
+
+
+def dram_traffic(kernel: str, digest: str) -> dict:
+    """DRAM bytes (read + write) of one integral pass of `kernel`, summed over its launches,
+    from the committed ncu capture, if that capture was taken of the sources being run."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return {"bytes": None, "note": "no ncu traffic capture committed"}
+    if rec.get("source_digest") != digest:
+        return {"bytes": None, "note": "kernels changed since the ncu traffic capture"}
+    k = rec.get("per_pass", {}).get(kernel)
+    if k is None:
+        return {"bytes": None, "note": f"no capture for {kernel}"}
+    return {"bytes": k["bytes"], "note": f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {rec.get('command')}"}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -385,6 +411,7 @@ def run_ours(args):
                          f"Wendland C2, brute-force cull + gamma/grad/10 moments in FP64, {secs:.1f} s"}
 
     peaks = measured_peaks()
+    traffic = dram_traffic(dom_k, B.source_digest())
     if rank != 0:
         return
     line = {
@@ -398,8 +425,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved_tops / peak, "traffic": None,
-                     "kernel": f"integrals_kernel<float,{dom_k},moments>",
+                     "frac": achieved_tops / peak, "traffic": traffic["bytes"], "traffic_note": traffic["note"],
+                     "kernel": KERNEL_LAUNCHES[dom_k],
                      "ops_per_pair": ops32[dom_k], "flops_per_pair": flops32[dom_k],
                      "kernel_ms": kmeans[dom],
                      "peak_basis": "FP32 lane-ops: 152 SMs x 128 FP32 lanes x 2070 MHz (unit counts and max clock)",

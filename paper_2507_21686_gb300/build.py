@@ -31,6 +31,11 @@ def nvcc() -> str:
     return cand
 
 
+def source_digest() -> str:
+    """SHA-256 over the library's sources, headers and flags (the build stamp)."""
+    return _digest()
+
+
 def _digest() -> str:
     h = hashlib.sha256()
     for d in (CSRC, os.path.join(ROOT, "include")):
