@@ -324,6 +324,17 @@ def run_ours(args):
     loc = (w.triangles[ptri_c[qs]].astype(np.float64).reshape(-1, 3, 2)
            - w.particles[pid, None, :2].astype(np.float64)) / w.H
     loc = loc.reshape(-1, 6)
+    # case histogram over a larger sample: vertices inside the support, particle inside
+    qh = rng.choice(P, min(P, 200000), replace=False)
+    ph = np.searchsorted(off_c, qh, side="right") - 1
+    lh = (w.triangles[ptri_c[qh]].astype(np.float64).reshape(-1, 3, 2)
+          - w.particles[ph, None, :2].astype(np.float64)) / w.H
+    n_in = (np.hypot(lh[..., 0], lh[..., 1]) < 1.0).sum(axis=1)
+    crs = [lh[:, j, 0] * lh[:, (j + 1) % 3, 1] - lh[:, j, 1] * lh[:, (j + 1) % 3, 0] for j in range(3)]
+    inside = ((crs[0] > 0) & (crs[1] > 0) & (crs[2] > 0)) | ((crs[0] < 0) & (crs[1] < 0) & (crs[2] < 0))
+    case_hist = {"sample_pairs": int(len(qh)),
+                 "vertices_inside_support": {str(k): float(np.mean(n_in == k)) for k in range(4)},
+                 "particle_inside_triangle": float(np.mean(inside))}
     flops32 = {k: PM.mean_flops_per_pair(k, True, True, loc) for k in KERNELS}
     ops32 = {k: PM.mean_ops_per_pair(k, True, True, loc) for k in KERNELS}
     flops64 = {k: PM.mean_flops_per_pair(k, True, False, loc) for k in KERNELS}
@@ -443,6 +454,8 @@ def run_ours(args):
         "speedup_vs_fp64_path": agg["value"] / value64,
         "max_rel_err_vs_fp64_path": max_err,
         "fixup_pairs_per_step": fix,
+        "fixup_rate": fix / max(P * len(KERNELS), 1),
+        "case_histogram": case_hist,
         "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
         "gamma_grad_only": gamma_grad_only,
         "adjoint": adjoint,
