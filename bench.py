@@ -454,7 +454,7 @@ def run_ours(args):
         "speedup_vs_fp64_path": agg["value"] / value64,
         "max_rel_err_vs_fp64_path": max_err,
         "fixup_pairs_per_step": fix,
-        "fixup_rate": fix / max(P * len(KERNELS), 1),
+        "fixup_rate": fix / max(P, 1),   # of the last pass of the step (cubic spline)
         "case_histogram": case_hist,
         "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
         "gamma_grad_only": gamma_grad_only,
