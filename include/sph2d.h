@@ -239,6 +239,30 @@ sph2d_status sph2d_pair_list_integrals_noalloc(const float* particles, int64_t N
                                                void* gamma, void* grad_gamma, void* stream);
 
 /*
+ * Piecewise-linear boundary fields (Sec. 3, Eq. taus and basicdiff) over the pair list in the
+ * context (sph2d_build_cells first; the particle and triangle arrays of that build must still
+ * hold the same data).  Each triangle carries per-vertex values A_j of nf fields, interpolated
+ * barycentrically (linear on the triangle); for every particle and field
+ *   value[i][f]   = sum_T int_T A_T(x') W(x_i - x', H) dx'
+ *   grad[i][f][:] = sum_T int_T A_T(x') grad_x W(x_i - x', H) dx'     (d value / d x_i)
+ * Per pair the value is A_T's constant part times gamma plus its gradient dotted with the first
+ * moments; the gradient is the constant-gradient area term minus the boundary term
+ * sum_j A_j d gamma / d nu_j (integration by parts; the edge integrals are those of
+ * sph2d_boundary_integrals_backward).  Difference and symmetric gradient forms and divergence
+ * or curl are linear in the per-vertex values: evaluate fields such as rho A and rho and
+ * combine per particle.
+ *   vertex_values  device float [M][3][nf] (triangle, vertex in input order, field)
+ *   nf             1..SPH2D_MAX_FIELDS
+ *   value          device real [N][nf]; grad device real [N][nf][2] or NULL (then the
+ *                  vertex-gradient work is skipped)
+ *   mode           SPH2D_FP64 (double outputs) or SPH2D_FP32_FIXUP (float outputs)
+ * Does not synchronise.  Errors: NOT_BUILT, INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA.
+ */
+#define SPH2D_MAX_FIELDS 4
+sph2d_status sph2d_field_integrals(sph2d_ctx* ctx, int kernel, int mode, const float* vertex_values,
+                                   int nf, void* value, void* grad);
+
+/*
  * ---- Learned surrogate -------------------------------------------------------------------
  * The paper has no counterpart: a small network that replaces the closed form for pairs
  * inside a trained domain, evaluated on tensor cores (FP16 operands, FP32 accumulation; the

@@ -6,6 +6,10 @@ imports it, and it never imports the product path.  It computes every result fro
 plain definition (Sec. 2 Eq. sphintegral / nablaIntegral, Sec. 3 Eq. singleSpherical) by
 quadrature, in ``sph2d_oracle.c``; this module only builds and marshals.
 
+``pair_field`` / ``pairs_field`` / ``particle_field_sums``: piecewise-linear boundary fields
+(Sec. 3, Eq. singleSpherical and basicdiff) by polar quadrature of the barycentric field times
+W and grad W.
+
 Outputs of ``pairs`` (per pair, 16 doubles):
   0 gamma | 1,2 grad gamma (divergence theorem) | 3,4 grad gamma (polar route, k')
   5..14 moments M00 M10 M01 M20 M11 M02 M30 M21 M12 M03 | 15 quadrature flag
@@ -61,6 +65,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.orc_particle_sums.argtypes = [Ci, D, P, I64, Ci, P, P, P, Ci, P, P, P, P]
     lib.orc_pairs.argtypes = [Ci, D, P, I64, P]
     lib.orc_pairs_vertex_grad.argtypes = [Ci, D, P, I64, P]
+    lib.orc_pair_field.argtypes = [Ci, D, P, P, P, P]
+    lib.orc_pairs_field.argtypes = [Ci, D, P, P, I64, P]
     lib.orc_kernel_C.argtypes = [Ci]
     lib.orc_kernel_C.restype = D
     lib.orc_kernel_k.argtypes = [Ci, D]
@@ -69,7 +75,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.orc_kernel_dk.restype = D
     lib.orc_gauss_legendre.argtypes = [Ci, P, P]
     for f in ("orc_pair", "orc_vertex_grad", "orc_cull", "orc_particle_sums", "orc_pairs",
-              "orc_pairs_vertex_grad", "orc_num_threads", "orc_version"):
+              "orc_pairs_vertex_grad", "orc_num_threads", "orc_version", "orc_pair_field",
+              "orc_pairs_field"):
         getattr(lib, f).restype = ctypes.c_int if f != "orc_kernel_C" else D
     _libs[mutant] = lib
     return lib
@@ -141,6 +148,56 @@ def pairs_vertex_grad(kernel, H: float, pairs_arr: np.ndarray) -> np.ndarray:
     out = np.zeros((len(p), 6))
     _lib().orc_pairs_vertex_grad(_kid(kernel), float(H), _ptr(p), len(p), _ptr(out))
     return out
+
+
+def pair_field(kernel, H: float, xp, tri, values, mutant: int = 0) -> np.ndarray:
+    """Linear boundary field on one triangle (vertex values [3], caller's vertex order) ->
+    [<A>, <grad A>_x, <grad A>_y] by polar quadrature of the field times W and grad W."""
+    xp = np.ascontiguousarray(xp, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.float64).reshape(6)
+    a = np.ascontiguousarray(values, dtype=np.float64).reshape(3)
+    out = np.zeros(3)
+    rc = _lib(mutant).orc_pair_field(_kid(kernel), float(H), _ptr(xp), _ptr(tri), _ptr(a), _ptr(out))
+    if rc < 0:
+        raise ValueError("oracle: bad arguments")
+    return out
+
+
+def pairs_field(kernel, H: float, pairs_arr: np.ndarray, values: np.ndarray, mutant: int = 0) -> np.ndarray:
+    """Many pairs [P, 8] with vertex values [P, 3] -> [P, 3] (<A>, <grad A>)."""
+    p = np.ascontiguousarray(pairs_arr, dtype=np.float64).reshape(-1, 8)
+    a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((len(p), 3))
+    rc = _lib(mutant).orc_pairs_field(_kid(kernel), float(H), _ptr(p), _ptr(a), len(p), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle: bad arguments")
+    return out
+
+
+def particle_field_sums(kernel, H: float, particles: np.ndarray, triangles: np.ndarray, off, pair_tri,
+                        vertex_values: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Per-particle sums of linear boundary fields: vertex_values [M, 3, nf] ->
+    value [N, nf], grad [N, nf, 2] (pairs in ascending triangle id per particle)."""
+    parts = np.asarray(particles, dtype=np.float32)
+    tris = np.asarray(triangles, dtype=np.float32).reshape(-1, 6)
+    vv = np.asarray(vertex_values, dtype=np.float32)
+    if vv.ndim == 2:
+        vv = vv[:, :, None]
+    nf = vv.shape[2]
+    off = np.asarray(off, dtype=np.int64)
+    pt = np.asarray(pair_tri, dtype=np.int64)
+    pid = np.repeat(np.arange(len(parts)), np.diff(off))
+    pr = np.zeros((len(pt), 8))
+    pr[:, :2] = parts[pid, :2]
+    pr[:, 2:] = tris[pt]
+    val = np.zeros((len(parts), nf))
+    grad = np.zeros((len(parts), nf, 2))
+    for f in range(nf):
+        r = pairs_field(kernel, H, pr, vv[pt, :, f].astype(np.float64))
+        np.add.at(val[:, f], pid, r[:, 0])
+        np.add.at(grad[:, f, 0], pid, r[:, 1])
+        np.add.at(grad[:, f, 1], pid, r[:, 2])
+    return val, grad
 
 
 def cull(particles: np.ndarray, triangles: np.ndarray, H: float):

@@ -164,8 +164,9 @@ void orc_gauss_legendre(int n, double* x, double* w) { gauss_legendre(n, x, w); 
 /*   out[0]          = int k(r) r dr                    (gamma density)                  */
 /*   out[1]          = int k'(r) r dr                   (polar gradient density)         */
 /*   out[2 + m]      = int k(r) r^(1+m) dr, m = 0..3   (moment densities)               */
+/*   out[6]          = int k'(r) r^2 dr                  (gradient density, linear field) */
 /* ------------------------------------------------------------------------------------ */
-#define NRAD 6
+#define NRAD 7
 static void radial_piece(int kid, double r0, double r1, double* out) {
   double h = 0.5 * (r1 - r0), c = 0.5 * (r1 + r0);
   for (int i = 0; i < GL_RAD; ++i) {
@@ -177,6 +178,11 @@ static void radial_piece(int kid, double r0, double r1, double* out) {
     out[0] += w * k * r;
 #endif
     out[1] += w * dk * r;
+#if ORC_MUTANT == 5
+    out[6] += w * dk * r;         /* lost a power of r in the linear-field gradient density */
+#else
+    out[6] += w * dk * r * r;
+#endif
     double rm = r;                                   /* r^(1+m) */
     for (int m = 0; m < 4; ++m) { out[2 + m] += w * k * rm; rm *= r; }
   }
@@ -337,8 +343,18 @@ static double wrap2pi(double a) {
   return a;
 }
 
+/* integrate the angular density fn over the triangle's angles, split at the breakpoints below */
+static void polar_integrate(int kid, const tri_t* t, vec_fn fn, const void* ctx, int nout, double* out,
+                            quad_stats* st);
+
 /* raw area integrals (without the constant C): out[NOUT] */
 static void area_integrals(int kid, const tri_t* t, double* out, quad_stats* st) {
+  polar_ctx pc = {kid, t};
+  polar_integrate(kid, t, polar_fn, &pc, NOUT, out, st);
+}
+
+static void polar_integrate(int kid, const tri_t* t, vec_fn fn, const void* ctx, int nout, double* out,
+                            quad_stats* st) {
   double bp[512];
   int nb = 0;
   double radii[2];
@@ -369,13 +385,34 @@ static void area_integrals(int kid, const tri_t* t, double* out, quad_stats* st)
     }
   }
   qsort(bp, nb, sizeof(double), cmp_dbl);
-  for (int j = 0; j < NOUT; ++j) out[j] = 0.0;
-  polar_ctx pc = {kid, t};
+  for (int j = 0; j < nout; ++j) out[j] = 0.0;
   const double tol = 1e-17;
   for (int i = 0; i < nb; ++i) {
     double a = bp[i], b = (i + 1 < nb) ? bp[i + 1] : bp[0] + 2.0 * M_PI;
-    integrate(polar_fn, &pc, NOUT, a, b, tol, out, st);
+    integrate(fn, ctx, nout, a, b, tol, out, st);
   }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* linear boundary field A(p) = a0 + ax p_x + ay p_y over the triangle (local frame):     */
+/*   f[0] = int A(r u) k(r) r dr,  f[1..2] = u int A(r u) k'(r) r dr                      */
+/* along the ray of direction u, clipped to the triangle and the support                 */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { int kid; const tri_t* t; double a0, ax, ay; } field_ctx;
+
+static void field_fn(const void* ctx, double th, double* f) {
+  const field_ctx* fc = (const field_ctx*)ctx;
+  f[0] = f[1] = f[2] = 0.0;
+  double ux = cos(th), uy = sin(th), r0, r1;
+  if (!ray_clip(fc->t, ux, uy, &r0, &r1)) return;
+  if (r0 >= 1.0) return;
+  double rad[NRAD];
+  radial(fc->kid, r0, r1, rad);
+  double au = fc->ax * ux + fc->ay * uy;          /* A(r u) = a0 + r (a . u) */
+  f[0] = fc->a0 * rad[0] + au * rad[3];            /* rad[3] = int k r^2 dr */
+  double g = fc->a0 * rad[1] + au * rad[6];        /* int A k'(r) r dr */
+  f[1] = g * ux;
+  f[2] = g * uy;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -505,6 +542,42 @@ int orc_vertex_grad(int kid, double H, const double* xp, const double* tri, doub
   return 0;
 }
 
+/* Piecewise-linear field on one triangle (Sec. 3, Eq. singleSpherical and basicdiff): vertex
+ * values A[3] in the caller's vertex order, interpolated barycentrically.
+ *   out[0] = int_T A(x') W(x - x') dx'                   <A>
+ *   out[1..2] = int_T A(x') grad_x W(x - x') dx'         <grad A> = -(C/H) int A k'(|p|) p/|p|
+ * by polar quadrature of the field times the kernel (no moments, no integration by parts). */
+int orc_pair_field(int kid, double H, const double* xp, const double* tri, const double* A, double* out) {
+  if (!kernel_ok(kid) || !(H > 0.0)) return -1;
+  gl_init();
+  out[0] = out[1] = out[2] = 0.0;
+  double p[6];
+  for (int j = 0; j < 3; ++j) {
+    p[2 * j] = (tri[2 * j] - xp[0]) / H;
+    p[2 * j + 1] = (tri[2 * j + 1] - xp[1]) / H;
+  }
+  tri_t t;
+  if (tri_setup(p, &t) == 0) return 0;
+  /* barycentric weights (Sec. 3): D = (y1-y2)(x0-x2) + (x2-x1)(y0-y2),
+   * lambda0 = ((y1-y2)(x-x2) + (x2-x1)(y-y2)) / D, lambda1 = ((y2-y0)(x-x2) + (x0-x2)(y-y2)) / D,
+   * lambda2 = 1 - lambda0 - lambda1; A = A2 + lambda0 (A0 - A2) + lambda1 (A1 - A2).
+   * Written as A(p) = a0 + ax p_x + ay p_y. */
+  double x0 = p[0], y0 = p[1], x1 = p[2], y1 = p[3], x2 = p[4], y2 = p[5];
+  double D = (y1 - y2) * (x0 - x2) + (x2 - x1) * (y0 - y2);
+  double l0x = (y1 - y2) / D, l0y = (x2 - x1) / D, l0c = -(l0x * x2 + l0y * y2);
+  double l1x = (y2 - y0) / D, l1y = (x0 - x2) / D, l1c = -(l1x * x2 + l1y * y2);
+  double d0 = A[0] - A[2], d1 = A[1] - A[2];
+  field_ctx fc = {kid, &t, A[2] + l0c * d0 + l1c * d1, l0x * d0 + l1x * d1, l0y * d0 + l1y * d1};
+  quad_stats st = {0, 0};
+  double q[3];
+  polar_integrate(kid, &t, field_fn, &fc, 3, q, &st);
+  double C = orc_kernel_C(kid);
+  out[0] = C * q[0];
+  out[1] = -(C / H) * q[1];
+  out[2] = -(C / H) * q[2];
+  return st.max_depth_hit ? 1 : 0;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* culling predicate: the operation order is part of the interface (include/sph2d.h)    */
 /* ------------------------------------------------------------------------------------ */
@@ -612,6 +685,15 @@ int orc_pairs_vertex_grad(int kid, double H, const double* pairs, int64_t P, dou
   gl_init();
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t q = 0; q < P; ++q) orc_vertex_grad(kid, H, pairs + 8 * q, pairs + 8 * q + 2, out + 6 * q);
+  return 0;
+}
+
+int orc_pairs_field(int kid, double H, const double* pairs, const double* A, int64_t P,
+                    double* out /*[P][3]*/) {
+  if (!kernel_ok(kid) || !(H > 0.0)) return -1;
+  gl_init();
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t q = 0; q < P; ++q) orc_pair_field(kid, H, pairs + 8 * q, pairs + 8 * q + 2, A + 3 * q, out + 3 * q);
   return 0;
 }
 

@@ -169,6 +169,23 @@ class Context:
             _mode_id(mode), _ptr(out)))
         return out
 
+    def field_integrals(self, vertex_values, kernel, mode="fp64", want_grad: bool = True):
+        """Piecewise-linear fields over the pair list of the last build: vertex_values
+        [M, 3, nf] (or [M, 3]) -> value [N, nf], grad [N, nf, 2] (or None)."""
+        vv = torch.as_tensor(vertex_values)
+        if vv.dim() == 2:
+            vv = vv[:, :, None]
+        nf = vv.shape[2]
+        vv = vv.to(device=self._dev(), dtype=torch.float32).contiguous()
+        n = self._keep[0].shape[0] if hasattr(self, "_keep") else 0
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        val = torch.empty((n, nf), dtype=dt, device=self._dev())
+        gr = torch.empty((n, nf, 2), dtype=dt, device=self._dev()) if want_grad else None
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_field_integrals(
+            self.h, _kernel_id(kernel), _mode_id(mode), _ptr(vv), int(nf), _ptr(val), _ptr(gr)))
+        return val, gr
+
     # -- adjoint -----------------------------------------------------------------------
     def backward(self, particles, tris, kernel, H: float, d_gamma, mode="fp64"):
         """dL/dx [N, 2] and dL/dvertices [M, 6] from dL/dgamma [N]."""

@@ -28,53 +28,7 @@ struct BwdArgs {
 // d gamma / d vertices of one pair in the mode's precision; returns 1 if FP64 was used
 template <typename OT, int KID>
 __device__ __forceinline__ int pair_vertex_grad(const BwdArgs& a, int pid, const float* t, OT* g) {
-  const float4 p = a.parts[pid];
-  if (sizeof(OT) == sizeof(float)) {
-    const float ih = float(a.invH);
-    float v[6];
-    float pmax = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      v[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
-      v[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
-      pmax = fmaxf(pmax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
-    }
-    // FP32 geometry is trusted when the vertices are near the particle and the triangle's
-    // smallest height is at least |p|max/64 (thinner slivers can flip orientation under
-    // FP32 rounding, which flips their vertex gradients)
-    const float a2 = fabsf(diff_of_products(v[2] - v[0], v[5] - v[1], v[3] - v[1], v[4] - v[0]));
-    float lmax = 0.0f;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const int b = e == 2 ? 0 : e + 1;
-      const float ex = v[2 * b] - v[2 * e], ey = v[2 * b + 1] - v[2 * e + 1];
-      lmax = fmaxf(lmax, sqrtf(ex * ex + ey * ey));
-    }
-    if (pmax <= kFixupCoordLimit && (a2 == 0.0f || 64.0f * a2 >= lmax * pmax)) {
-      float w[6];
-      tri_vertex_grad<float, KID>(v, w);
-      bool ok = true;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) ok = ok && isfinite(w[i]);
-      if (ok) {
-        const float k = float(a.C * a.invH);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = OT(k * w[i]);
-        return 0;
-      }
-    }
-  }
-  double v[6], w[6];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    v[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-    v[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-  }
-  tri_vertex_grad<double, KID>(v, w);
-  const double k = a.C * a.invH;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) g[i] = OT(k * w[i]);
-  return sizeof(OT) == sizeof(float) ? 1 : 0;
+  return vertex_grad_pair<OT, KID>(a.parts[pid], t, a.invH, a.C, g);
 }
 
 template <typename OT, int KID>

@@ -5,8 +5,8 @@
 
 namespace sph2d {
 
-sph2d_status integrals_fp64(Ctx* c, int kernel, bool mom, const IntArgs& a);
-sph2d_status integrals_fp32(Ctx* c, int kernel, bool mom, const IntArgs& a);
+sph2d_status integrals_fp64(Ctx* c, int kernel, int md, const IntArgs& a);
+sph2d_status integrals_fp32(Ctx* c, int kernel, int md, const IntArgs& a);
 sph2d_status pairs_fp64(Ctx* c, const double* pairs, int64_t P, int kernel, double H, int deg,
                         unsigned long long* nfix, void* out);
 sph2d_status pairs_fp32(Ctx* c, const double* pairs, int64_t P, int kernel, double H, int deg,
@@ -36,8 +36,8 @@ sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, v
   a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr);
   cudaError_t e = cudaMemsetAsync(a.nfix, 0, sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
-  const bool mom = moment_degree >= 1;
-  s = mode == SPH2D_FP64 ? integrals_fp64(c, kernel, mom, a) : integrals_fp32(c, kernel, mom, a);
+  const int md = md_for(moment_degree);
+  s = mode == SPH2D_FP64 ? integrals_fp64(c, kernel, md, a) : integrals_fp32(c, kernel, md, a);
   if (s != SPH2D_OK) return s;
   e = cudaMemcpyAsync(c->pinned + 8, a.nfix, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                       c->stream);

@@ -3,8 +3,8 @@
 
 namespace sph2d {
 
-sph2d_status integrals_fp32(Ctx* c, int kernel, bool mom, const IntArgs& a) {
-  return dispatch_integrals<float>(c, kernel, mom, a);
+sph2d_status integrals_fp32(Ctx* c, int kernel, int md, const IntArgs& a) {
+  return dispatch_integrals<float>(c, kernel, md, a);
 }
 
 sph2d_status pairs_fp32(Ctx* c, const double* pairs, int64_t P, int kernel, double H, int deg,

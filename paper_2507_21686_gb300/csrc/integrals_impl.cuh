@@ -24,7 +24,12 @@
 
 namespace sph2d {
 
-constexpr float kFixupCoordLimit = 16.0f;   // |p| in units of H beyond which FP32 is not used
+constexpr float kFixupCoordLimit = 16.0f;
+
+// moments carried per pair for moment degree MD (0: none, 1: M00 M10 M01, 3: all ten), and
+// values per pair including gamma and grad gamma
+constexpr int nmom_of(int MD) { return MD >= 3 ? 10 : (MD >= 1 ? 3 : 0); }
+constexpr int nv_of(int MD) { return 3 + nmom_of(MD); }   // |p| in units of H beyond which FP32 is not used
 
 struct IntArgs {
   const float4* parts;
@@ -43,36 +48,34 @@ struct IntArgs {
 };
 
 // raw integrals of one local-frame triangle -> v = (gamma, grad x, grad y, M00..M03)
-template <typename R, int KID, bool MOM>
+template <typename R, int KID, int MD>
 __device__ __forceinline__ void eval_local(const R* l, double C, double invH, R* v) {
   const int s = tri_orientation<R>(l[0], l[1], l[2], l[3], l[4], l[5]);
   if (s == 0) {
 #pragma unroll
-    for (int i = 0; i < (MOM ? 13 : 3); ++i) v[i] = R(0);
+    for (int i = 0; i < nv_of(MD); ++i) v[i] = R(0);
     return;
   }
   PairOut<R> o;
-  tri_raw<R, KID, MOM>(l[0], l[1], l[2], l[3], l[4], l[5], o);
+  tri_raw<R, KID, MD>(l[0], l[1], l[2], l[3], l[4], l[5], o);
   const R k = R(C) * R(s);
   const R kg = -k * R(invH);
   v[0] = k * o.g;
   v[1] = kg * o.gx;
   v[2] = kg * o.gy;
-  if (MOM) {
 #pragma unroll
-    for (int m = 0; m < 10; ++m) v[3 + m] = k * o.m[m];
-  }
+  for (int m = 0; m < nmom_of(MD); ++m) v[3 + m] = k * o.m[m];
 }
 
 // evaluate from double-precision local coordinates in the mode's precision; returns 1 if the
 // FP64 fix-up path was taken
-template <typename OT, int KID, bool MOM>
+template <typename OT, int KID, int MD>
 __device__ __forceinline__ int eval_mode(const double* ld, double C, double invH, OT* v) {
   if (sizeof(OT) == sizeof(double)) {
     double w[13];
-    eval_local<double, KID, MOM>(ld, C, invH, w);
+    eval_local<double, KID, MD>(ld, C, invH, w);
 #pragma unroll
-    for (int i = 0; i < (MOM ? 13 : 3); ++i) v[i] = OT(w[i]);
+    for (int i = 0; i < nv_of(MD); ++i) v[i] = OT(w[i]);
     return 0;
   } else {
     float lf[6];
@@ -84,24 +87,24 @@ __device__ __forceinline__ int eval_mode(const double* ld, double C, double invH
     }
     if (ok) {
       float w[13];
-      eval_local<float, KID, MOM>(lf, C, invH, w);
+      eval_local<float, KID, MD>(lf, C, invH, w);
 #pragma unroll
-      for (int i = 0; i < (MOM ? 13 : 3); ++i) ok = ok && isfinite(w[i]);
+      for (int i = 0; i < nv_of(MD); ++i) ok = ok && isfinite(w[i]);
       if (ok) {
 #pragma unroll
-        for (int i = 0; i < (MOM ? 13 : 3); ++i) v[i] = OT(w[i]);
+        for (int i = 0; i < nv_of(MD); ++i) v[i] = OT(w[i]);
         return 0;
       }
     }
     double w[13];
-    eval_local<double, KID, MOM>(ld, C, invH, w);
+    eval_local<double, KID, MD>(ld, C, invH, w);
 #pragma unroll
-    for (int i = 0; i < (MOM ? 13 : 3); ++i) v[i] = OT(w[i]);
+    for (int i = 0; i < nv_of(MD); ++i) v[i] = OT(w[i]);
     return 1;
   }
 }
 
-template <typename OT, int KID, bool MOM>
+template <typename OT, int KID, int MD>
 __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT* v) {
   const float4 p = a.parts[pid];
   const float* t = a.tris + 6 * int64_t(tid);
@@ -113,7 +116,7 @@ __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT*
       ld[2 * j] = (double(__ldg(t + 2 * j)) - px) * a.invH;
       ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - py) * a.invH;
     }
-    return eval_mode<OT, KID, MOM>(ld, a.C, a.invH, v);
+    return eval_mode<OT, KID, MD>(ld, a.C, a.invH, v);
   } else {
     // FP32 local frame straight from the FP32 inputs
     const float ih = float(a.invH);
@@ -127,12 +130,12 @@ __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT*
     }
     if (ok) {
       float w[13];
-      eval_local<float, KID, MOM>(lf, a.C, a.invH, w);
+      eval_local<float, KID, MD>(lf, a.C, a.invH, w);
 #pragma unroll
-      for (int i = 0; i < (MOM ? 13 : 3); ++i) ok = ok && isfinite(w[i]);
+      for (int i = 0; i < nv_of(MD); ++i) ok = ok && isfinite(w[i]);
       if (ok) {
 #pragma unroll
-        for (int i = 0; i < (MOM ? 13 : 3); ++i) v[i] = OT(w[i]);
+        for (int i = 0; i < nv_of(MD); ++i) v[i] = OT(w[i]);
         return 0;
       }
     }
@@ -143,14 +146,67 @@ __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT*
       ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
     }
     double w[13];
-    eval_local<double, KID, MOM>(ld, a.C, a.invH, w);
+    eval_local<double, KID, MD>(ld, a.C, a.invH, w);
 #pragma unroll
-    for (int i = 0; i < (MOM ? 13 : 3); ++i) v[i] = OT(w[i]);
+    for (int i = 0; i < nv_of(MD); ++i) v[i] = OT(w[i]);
     return 1;
   }
 }
 
-template <typename OT, bool MOM>
+// d gamma / d (x0, y0, x1, y1, x2, y2) of one culled pair in world units (transport-theorem
+// edge integrals of pair_math.cuh, times C/H) in the mode's precision; returns 1 if the FP64
+// path was used
+template <typename OT, int KID>
+__device__ __forceinline__ int vertex_grad_pair(const float4 p, const float* t, double invH, double C, OT* g) {
+  if (sizeof(OT) == sizeof(float)) {
+    const float ih = float(invH);
+    float v[6];
+    float pmax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      v[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+      v[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+      pmax = fmaxf(pmax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+    }
+    // FP32 geometry is trusted when the vertices are near the particle and the triangle's
+    // smallest height is at least |p|max/64 (thinner slivers can flip orientation under
+    // FP32 rounding, which flips their vertex gradients)
+    const float a2 = fabsf(diff_of_products(v[2] - v[0], v[5] - v[1], v[3] - v[1], v[4] - v[0]));
+    float lmax = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int b = e == 2 ? 0 : e + 1;
+      const float ex = v[2 * b] - v[2 * e], ey = v[2 * b + 1] - v[2 * e + 1];
+      lmax = fmaxf(lmax, sqrtf(ex * ex + ey * ey));
+    }
+    if (pmax <= kFixupCoordLimit && (a2 == 0.0f || 64.0f * a2 >= lmax * pmax)) {
+      float w[6];
+      tri_vertex_grad<float, KID>(v, w);
+      bool ok = true;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) ok = ok && isfinite(w[i]);
+      if (ok) {
+        const float k = float(C * invH);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = OT(k * w[i]);
+        return 0;
+      }
+    }
+  }
+  double v[6], w[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    v[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * invH;
+    v[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * invH;
+  }
+  tri_vertex_grad<double, KID>(v, w);
+  const double k = C * invH;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) g[i] = OT(k * w[i]);
+  return sizeof(OT) == sizeof(float) ? 1 : 0;
+}
+
+template <typename OT, int MD>
 __device__ __forceinline__ void write_particle(const IntArgs& a, int64_t pid, const OT* v) {
   static_cast<OT*>(a.gamma)[pid] = v[0];
   if (a.grad) {
@@ -159,10 +215,10 @@ __device__ __forceinline__ void write_particle(const IntArgs& a, int64_t pid, co
   }
   if (a.nm == 1) {
     static_cast<OT*>(a.mom)[pid] = v[0];
-  } else if (MOM) {
+  } else if (MD >= 1) {
     OT* m = static_cast<OT*>(a.mom) + pid * a.nm;
 #pragma unroll
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < nmom_of(MD); ++i)
       if (i < a.nm) m[i] = v[3 + i];
   }
 }
@@ -181,9 +237,9 @@ template <typename OT> constexpr int int_minb() {
   return sizeof(OT) == sizeof(float) ? SPH2D_INT_MINB : SPH2D_INT_MINB64;
 }
 
-template <typename OT, int KID, bool MOM>
+template <typename OT, int KID, int MD>
 __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs a) {
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -197,7 +253,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
     int fix = 0;
     if (q < a.P) {
       pid = __ldg(a.pair_pid + q);
-      fix = eval_pair<OT, KID, MOM>(a, pid, __ldg(a.pair_tri + q), v);
+      fix = eval_pair<OT, KID, MD>(a, pid, __ldg(a.pair_tri + q), v);
     }
     fixes += __popc(__ballot_sync(0xffffffffu, fix));
     // segmented suffix sum: lane l accumulates the lanes l.. of its own particle
@@ -218,7 +274,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
     if (head) {
       const int64_t cs = ch * 32;
       const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
-      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, MOM>(a, pid, v);
+      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, MD>(a, pid, v);
       OT* slots = static_cast<OT*>(a.slots);
       if (lane == 0) {
 #pragma unroll
@@ -266,22 +322,25 @@ __device__ __forceinline__ bool near_half(const R* l) {
 }
 
 // one piece of the cubic spline for a local triangle of orientation s != 0 -> v (scaled)
-template <typename R, bool MOM>
+template <typename R, int MD>
 __device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double C, double invH, R* v) {
   const R sc = piece ? R(2) : R(1);
   PairOut<R> h;
   clear(h);
-  tri_poly<R, PolyCube, MOM, true>(sc * l[0], sc * l[1], sc * l[2], sc * l[3], sc * l[4], sc * l[5], h);
+  tri_poly<R, PolyCube, MD, true>(sc * l[0], sc * l[1], sc * l[2], sc * l[3], sc * l[4], sc * l[5], h);
   const R k = R(C) * R(s);
   const R wg = piece ? R(-0.25) : R(2), wd = piece ? R(-0.5) : R(2);
   v[0] = (k * wg) * h.g;
   v[1] = (-k * R(invH) * wd) * h.gx;
   v[2] = (-k * R(invH) * wd) * h.gy;
-  if (MOM) {
-    const R w1 = piece ? R(-0.125) : R(2), w2 = piece ? R(-0.0625) : R(2), w3 = piece ? R(-0.03125) : R(2);
+  if (MD >= 1) {
+    const R w1 = piece ? R(-0.125) : R(2);
     v[3] = (k * wg) * h.m[0];
 #pragma unroll
     for (int i = 1; i < 3; ++i) v[3 + i] = (k * w1) * h.m[i];
+  }
+  if (MD >= 3) {
+    const R w2 = piece ? R(-0.0625) : R(2), w3 = piece ? R(-0.03125) : R(2);
 #pragma unroll
     for (int i = 3; i < 6; ++i) v[3 + i] = (k * w2) * h.m[i];
 #pragma unroll
@@ -289,11 +348,11 @@ __device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double
   }
 }
 
-template <typename OT, bool MOM>
+template <typename OT, int MD>
 __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArgs a, OT* __restrict__ vals,
                                                           int64_t* __restrict__ list,
                                                           unsigned long long* __restrict__ count) {
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   unsigned long long fixes = 0;
@@ -324,7 +383,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArg
 #pragma unroll
             for (int i = 0; i < NV; ++i) w[i] = 0.0f;
           } else {
-            cubic_piece<float, MOM>(lf, 0, s, a.C, a.invH, w);
+            cubic_piece<float, MD>(lf, 0, s, a.C, a.invH, w);
             need = near_half<float>(lf);
           }
 #pragma unroll
@@ -350,12 +409,12 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArg
             for (int i = 0; i < NV; ++i) w[i] = 0.0;
             need = false;
           } else {
-            cubic_piece<double, MOM>(ld, 0, s, a.C, a.invH, w);
+            cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
             need = near_half<double>(ld);
           }
         } else {
           // FP64 fix-up of an FP32 pair: both pieces here, nothing left for the list
-          eval_local<double, KID_CUBIC, MOM>(ld, a.C, a.invH, w);
+          eval_local<double, KID_CUBIC, MD>(ld, a.C, a.invH, w);
           need = false;
           fix = 1;
         }
@@ -379,11 +438,11 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArg
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
 
-template <typename OT, bool MOM>
+template <typename OT, int MD>
 __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntArgs a, OT* __restrict__ vals,
                                                            const int64_t* __restrict__ list,
                                                            const unsigned long long* __restrict__ count) {
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int64_t n = int64_t(*count);
   unsigned long long fixes = 0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -401,7 +460,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntAr
         lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
       }
       const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
-      cubic_piece<float, MOM>(lf, 1, s, a.C, a.invH, w);
+      cubic_piece<float, MD>(lf, 1, s, a.C, a.invH, w);
       bool ok = true;
 #pragma unroll
       for (int k = 0; k < NV; ++k) ok = ok && isfinite(w[k]);
@@ -419,7 +478,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntAr
         ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
       }
       const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-      cubic_piece<double, MOM>(ld, 1, s, a.C, a.invH, w);
+      cubic_piece<double, MD>(ld, 1, s, a.C, a.invH, w);
 #pragma unroll
       for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
       if (sizeof(OT) == sizeof(float)) ++fixes;
@@ -432,9 +491,9 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntAr
 }
 
 // per-particle sums of per-pair values [P][NV] in pair order
-template <typename OT, bool MOM>
+template <typename OT, int MD>
 __global__ void __launch_bounds__(128) reduce_pairs_kernel(IntArgs a, const OT* __restrict__ vals) {
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -466,7 +525,7 @@ __global__ void __launch_bounds__(128) reduce_pairs_kernel(IntArgs a, const OT* 
     if (head) {
       const int64_t cs = ch * 32;
       const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
-      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, MOM>(a, pid, v);
+      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, MD>(a, pid, v);
       OT* slots = static_cast<OT*>(a.slots);
       if (lane == 0) {
 #pragma unroll
@@ -481,9 +540,9 @@ __global__ void __launch_bounds__(128) reduce_pairs_kernel(IntArgs a, const OT* 
 }
 
 // particles without pairs get zeros; particles whose pairs span chunks add their partials
-template <typename OT, bool MOM>
+template <typename OT, int MD>
 __global__ void finalize_kernel(IntArgs a) {
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   const int64_t s0 = a.pair_off[i], s1 = a.pair_off[i + 1];
@@ -503,11 +562,11 @@ __global__ void finalize_kernel(IntArgs a) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] += slots[(c1 * 2) * NV + k];
   }
-  write_particle<OT, MOM>(a, i, v);
+  write_particle<OT, MD>(a, i, v);
 }
 
 // independent pairs: [P][8] doubles -> [P][3+nm]
-template <typename OT, int KID, bool MOM>
+template <typename OT, int KID, int MD>
 __global__ void __launch_bounds__(256) pair_entry_kernel(const double* __restrict__ pairs, int64_t P,
                                                          double invH, double C, int nm,
                                                          OT* __restrict__ out,
@@ -523,16 +582,16 @@ __global__ void __launch_bounds__(256) pair_entry_kernel(const double* __restric
       ld[2 * j] = (q[2 + 2 * j] - px) * invH;
       ld[2 * j + 1] = (q[3 + 2 * j] - py) * invH;
     }
-    OT v[MOM ? 13 : 3];
-    fix = eval_mode<OT, KID, MOM>(ld, C, invH, v);
+    OT v[nv_of(MD)];
+    fix = eval_mode<OT, KID, MD>(ld, C, invH, v);
     OT* o = out + i * (3 + nm);
     o[0] = v[0];
     o[1] = v[1];
     o[2] = v[2];
     if (nm == 1) o[3] = v[0];
-    else if (MOM) {
+    else if (MD >= 1) {
 #pragma unroll
-      for (int m = 0; m < 10; ++m)
+      for (int m = 0; m < nmom_of(MD); ++m)
         if (m < nm) o[3 + m] = v[3 + m];
     }
   }
@@ -552,9 +611,9 @@ static unsigned resident_blocks(Ctx* c, K kern, int64_t wanted) {
   return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
 }
 
-template <typename OT, bool MOM>
+template <typename OT, int MD>
 static sph2d_status run_cubic(Ctx* c, IntArgs a) {
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int64_t nchunks = (a.P + 31) >> 5;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
   if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(a.P > 0 ? a.P : 1) * NV * sizeof(OT));
@@ -568,32 +627,32 @@ static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   if (a.P > 0) {
     const int64_t blocks = (a.P + 127) / 128;
-    SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MOM>), resident_blocks(c, cubic_first_kernel<OT, MOM>, blocks), 128,
+    SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MD>), resident_blocks(c, cubic_first_kernel<OT, MD>, blocks), 128,
                  a, vals, list, count);
-    SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MOM>), resident_blocks(c, cubic_second_kernel<OT, MOM>, blocks), 128,
+    SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MD>), resident_blocks(c, cubic_second_kernel<OT, MD>, blocks), 128,
                  a, vals, list, count);
-    SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MOM>), resident_blocks(c, reduce_pairs_kernel<OT, MOM>, (nchunks + 3) / 4),
+    SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MD>), resident_blocks(c, reduce_pairs_kernel<OT, MD>, (nchunks + 3) / 4),
                  128, a, vals);
   }
-  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MOM>), unsigned((a.N + 255) / 256), 256, a);
+  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
   return SPH2D_OK;
 }
 
-template <typename OT, int KID, bool MOM>
+template <typename OT, int KID, int MD>
 static sph2d_status run_integrals(Ctx* c, IntArgs a) {
   if constexpr (KID == KID_CUBIC) {
-    return run_cubic<OT, MOM>(c, a);
+    return run_cubic<OT, MD>(c, a);
   } else {
   static int grid_blocks = 0;
   if (grid_blocks == 0) {
     int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrals_kernel<OT, KID, MOM>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrals_kernel<OT, KID, MD>, 128, 0);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     grid_blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
-  constexpr int NV = MOM ? 13 : 3;
+  constexpr int NV = nv_of(MD);
   const int64_t nchunks = (a.P + 31) >> 5;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
   if (s != SPH2D_OK) return s;
@@ -601,22 +660,31 @@ static sph2d_status run_integrals(Ctx* c, IntArgs a) {
   if (a.P > 0) {
     int64_t want = (nchunks + 3) / 4;                    // 4 warps per block
     const unsigned blocks = unsigned(want < grid_blocks ? (want > 0 ? want : 1) : grid_blocks);
-    SPH2D_LAUNCH(c, (integrals_kernel<OT, KID, MOM>), blocks, 128, a);
+    SPH2D_LAUNCH(c, (integrals_kernel<OT, KID, MD>), blocks, 128, a);
   }
-  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MOM>), unsigned((a.N + 255) / 256), 256, a);
+  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
   return SPH2D_OK;
   }
 }
 
+// moment degree computed for a requested moment_degree: -1/0 -> 0, 1 -> 1, 2/3 -> 3
+inline int md_for(int moment_degree) { return moment_degree >= 2 ? 3 : (moment_degree == 1 ? 1 : 0); }
+
+template <typename OT, int KID>
+static sph2d_status run_md(Ctx* c, int md, IntArgs a) {
+  return md == 3 ? run_integrals<OT, KID, 3>(c, a)
+                 : (md == 1 ? run_integrals<OT, KID, 1>(c, a) : run_integrals<OT, KID, 0>(c, a));
+}
+
 template <typename OT>
-static sph2d_status dispatch_integrals(Ctx* c, int kernel, bool mom, IntArgs a) {
+static sph2d_status dispatch_integrals(Ctx* c, int kernel, int md, IntArgs a) {
   switch (kernel) {
-    case KID_WC2: return mom ? run_integrals<OT, KID_WC2, true>(c, a) : run_integrals<OT, KID_WC2, false>(c, a);
-    case KID_WC4: return mom ? run_integrals<OT, KID_WC4, true>(c, a) : run_integrals<OT, KID_WC4, false>(c, a);
-    case KID_WC6: return mom ? run_integrals<OT, KID_WC6, true>(c, a) : run_integrals<OT, KID_WC6, false>(c, a);
-    default: return mom ? run_integrals<OT, KID_CUBIC, true>(c, a) : run_integrals<OT, KID_CUBIC, false>(c, a);
+    case KID_WC2: return run_md<OT, KID_WC2>(c, md, a);
+    case KID_WC4: return run_md<OT, KID_WC4>(c, md, a);
+    case KID_WC6: return run_md<OT, KID_WC6>(c, md, a);
+    default: return run_md<OT, KID_CUBIC>(c, md, a);
   }
 }
 
@@ -624,18 +692,21 @@ template <typename OT>
 static sph2d_status dispatch_pairs(Ctx* c, const double* pairs, int64_t P, int kernel, double H,
                                    int deg, unsigned long long* nfix, void* out) {
   const int nm = num_moments(deg);
-  const bool mom = deg >= 1;
+  const int md = md_for(deg);
   const double invH = 1.0 / H, C = kernel_C(kernel);
   const unsigned blocks = unsigned((P + 255) / 256);
   if (P == 0) return SPH2D_OK;
   OT* o = static_cast<OT*>(out);
 #define SPH2D_PE(K, MM) SPH2D_LAUNCH(c, (pair_entry_kernel<OT, K, MM>), blocks, 256, pairs, P, invH, C, nm, o, nfix)
+#define SPH2D_PEK(K) \
+  do { if (md == 3) SPH2D_PE(K, 3); else if (md == 1) SPH2D_PE(K, 1); else SPH2D_PE(K, 0); } while (0)
   switch (kernel) {
-    case KID_WC2: if (mom) SPH2D_PE(KID_WC2, true); else SPH2D_PE(KID_WC2, false); break;
-    case KID_WC4: if (mom) SPH2D_PE(KID_WC4, true); else SPH2D_PE(KID_WC4, false); break;
-    case KID_WC6: if (mom) SPH2D_PE(KID_WC6, true); else SPH2D_PE(KID_WC6, false); break;
-    default: if (mom) SPH2D_PE(KID_CUBIC, true); else SPH2D_PE(KID_CUBIC, false); break;
+    case KID_WC2: SPH2D_PEK(KID_WC2); break;
+    case KID_WC4: SPH2D_PEK(KID_WC4); break;
+    case KID_WC6: SPH2D_PEK(KID_WC6); break;
+    default: SPH2D_PEK(KID_CUBIC); break;
   }
+#undef SPH2D_PEK
 #undef SPH2D_PE
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "pair integrals launch");

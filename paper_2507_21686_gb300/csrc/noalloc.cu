@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) integrals_noalloc_kernel(IntArgs a) {
         else hi = mid - 1;
       }
       pid = int(lo);
-      fix = eval_pair<OT, KID, false>(a, pid, __ldg(a.pair_tri + q), v);
+      fix = eval_pair<OT, KID, 0>(a, pid, __ldg(a.pair_tri + q), v);
     }
     fixes += __popc(__ballot_sync(0xffffffffu, fix));
 #pragma unroll
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) integrals_noalloc_kernel(IntArgs a) {
     if (head) {
       const int64_t cs = ch * 32;
       const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
-      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, false>(a, pid, v);
+      if (s0 >= cs && s1 <= cs + 32) write_particle<OT, 0>(a, pid, v);
       OT* slots = static_cast<OT*>(a.slots);
       if (lane == 0) {
 #pragma unroll
@@ -120,7 +120,7 @@ static cudaError_t launch_noalloc(const IntArgs& a, cudaStream_t st) {
     const unsigned blocks = unsigned(want < grid_blocks ? (want > 0 ? want : 1) : grid_blocks);
     integrals_noalloc_kernel<OT, KID><<<blocks, 128, 0, st>>>(a);
   }
-  if (a.N > 0) finalize_kernel<OT, false><<<unsigned((a.N + 255) / 256), 256, 0, st>>>(a);
+  if (a.N > 0) finalize_kernel<OT, 0><<<unsigned((a.N + 255) / 256), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

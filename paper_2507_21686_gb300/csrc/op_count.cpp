@@ -131,7 +131,7 @@ static bool within_half(const double* l) {
   return near || (pos != neg);
 }
 
-template <typename R, int KID, bool MOM>
+template <typename R, int KID, int MD>
 static void count_one(const double* l) {
   R v[6];
   for (int j = 0; j < 6; ++j) v[j] = R(l[j]);
@@ -140,49 +140,56 @@ static void count_one(const double* l) {
   if (KID == KID_CUBIC) {
     // first piece always, second piece only where it is non-zero, as the kernels evaluate it
     clear(o);
-    tri_poly<R, PolyCube, MOM, true>(v[0], v[1], v[2], v[3], v[4], v[5], o);
+    tri_poly<R, PolyCube, MD, true>(v[0], v[1], v[2], v[3], v[4], v[5], o);
     if (within_half(l)) {
       PairOut<R> h;
       clear(h);
       const R sc(2.0);
-      tri_poly<R, PolyCube, MOM, true>(sc * v[0], sc * v[1], sc * v[2], sc * v[3], sc * v[4], sc * v[5], h);
+      tri_poly<R, PolyCube, MD, true>(sc * v[0], sc * v[1], sc * v[2], sc * v[3], sc * v[4], sc * v[5], h);
       o.g = o.g + h.g;
       o.gx = o.gx + h.gx;
       o.gy = o.gy + h.gy;
-      if (MOM)
-        for (int m = 0; m < 10; ++m) o.m[m] = o.m[m] + h.m[m];
+      for (int m = 0; m < (MD >= 3 ? 10 : (MD >= 1 ? 3 : 0)); ++m) o.m[m] = o.m[m] + h.m[m];
     }
   } else {
-    tri_raw<R, KID, MOM>(v[0], v[1], v[2], v[3], v[4], v[5], o);
+    tri_raw<R, KID, MD>(v[0], v[1], v[2], v[3], v[4], v[5], o);
   }
   // constants and orientation applied per output, as in the kernels
   const R k(1.0);
   R s = k * o.g;
   s = k * o.gx;
   s = k * o.gy;
-  if (MOM)
-    for (int m = 0; m < 10; ++m) s = k * o.m[m];
+  for (int m = 0; m < (MD >= 3 ? 10 : (MD >= 1 ? 3 : 0)); ++m) s = k * o.m[m];
   (void)s;
 }
 
+template <typename R, int KID>
+static void count_md(int md, const double* l) {
+  if (md == 3) count_one<R, KID, 3>(l);
+  else if (md == 1) count_one<R, KID, 1>(l);
+  else count_one<R, KID, 0>(l);
+}
+
 template <typename R>
-static void count_kernel(int kid, bool mom, const double* l) {
+static void count_kernel(int kid, int md, const double* l) {
   switch (kid) {
-    case 0: mom ? count_one<R, 0, true>(l) : count_one<R, 0, false>(l); break;
-    case 1: mom ? count_one<R, 1, true>(l) : count_one<R, 1, false>(l); break;
-    case 2: mom ? count_one<R, 2, true>(l) : count_one<R, 2, false>(l); break;
-    default: mom ? count_one<R, 3, true>(l) : count_one<R, 3, false>(l); break;
+    case 0: count_md<R, 0>(md, l); break;
+    case 1: count_md<R, 1>(md, l); break;
+    case 2: count_md<R, 2>(md, l); break;
+    default: count_md<R, 3>(md, l); break;
   }
 }
 }  // namespace sph2d
 
 extern "C" {
-// Count the operations of one pair (local-frame triangle l[6], H = 1).  out[7] = add, mul,
-// fma, div, sqrt, transcendental, other.  Returns flops (fma = 2).
-int64_t sph2d_count_pair_ops(int kernel, int moments, int fp32, const double* l, int64_t* out) {
+// Count the operations of one pair (local-frame triangle l[6], H = 1) with moments up to
+// `moment_degree` (-1..3; 2 and 3 compute all ten, 1 the first three, as the kernels do).
+// out[7] = add, mul, fma, div, sqrt, transcendental, other.  Returns flops (fma = 2).
+int64_t sph2d_count_pair_ops(int kernel, int moment_degree, int fp32, const double* l, int64_t* out) {
   sph2d::g_tally = sph2d::OpTally{};
-  if (fp32) sph2d::count_kernel<sph2d::Counted<float>>(kernel, moments != 0, l);
-  else sph2d::count_kernel<sph2d::Counted<double>>(kernel, moments != 0, l);
+  const int md = moment_degree >= 2 ? 3 : (moment_degree == 1 ? 1 : 0);
+  if (fp32) sph2d::count_kernel<sph2d::Counted<float>>(kernel, md, l);
+  else sph2d::count_kernel<sph2d::Counted<double>>(kernel, md, l);
   const sph2d::OpTally& t = sph2d::g_tally;
   if (out) {
     out[0] = t.add; out[1] = t.mul; out[2] = t.fma; out[3] = t.div;

@@ -577,7 +577,8 @@ template <> struct AccSel<double, PolyWC6> { using type = AccDD<double>; };
 // one edge (fan (0, A, B)) of a triangle for the polynomial kernel P; accumulates the
 // signed fan integrals into o (global frame, raw)
 // ---------------------------------------------------------------------------------------
-template <typename R, class P, bool MOM>
+// MD: moment degree computed, 0 (none), 1 (M00, M10, M01) or 3 (all ten)
+template <typename R, class P, int MD>
 SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   const R ex = bx - ax, ey = by - ay;
   const R l2 = ex * ex + ey * ey;
@@ -616,16 +617,19 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   R en = R(kg) * I_c;                                    // gradient along n
   R et = R(kg) * I_s;                                    // gradient along e2
   R E[10];                                               // edge-frame moments s^j t^l
-  if (MOM) {
-    constexpr double k3 = kappa<P>(3), k4 = kappa<P>(4), k5 = kappa<P>(5);
+  if (MD >= 1) {
+    constexpr double k3 = kappa<P>(3);
+    E[0] = eg;
+    E[1] = R(k3) * I_c;                                  // s
+    E[2] = R(k3) * I_s;                                  // t
+  }
+  if (MD >= 3) {
+    constexpr double k4 = kappa<P>(4), k5 = kappa<P>(5);
     const R scA = sA * cA, sc1 = s1 * c1, sc2 = s2 * c2, scB = sB * cB;
     const R I_sc = SPH2D_BR(sc1, scA, sc2, scB);         // [s c]
     const R I_ss = SPH2D_BR(s1 * s1, sA * sA, s2 * s2, sB * sB);
     const R I_s3 = SPH2D_BR(s1 * s1 * s1, sA * sA * sA, s2 * s2 * s2, sB * sB * sB);
     const R I_c3 = SPH2D_BR(c1 * c1 * c1, cA * cA * cA, c2 * c2 * c2, cB * cB * cB);
-    E[0] = eg;
-    E[1] = R(k3) * I_c;                                  // s
-    E[2] = R(k3) * I_s;                                  // t
     E[3] = R(k4) * R(0.5) * (dus + I_sc);                // s^2 : int cos^2
     E[4] = R(k4) * R(0.5) * I_ss;                        // s t : int sin cos = [sin^2/2]
     E[5] = R(k4) * R(0.5) * (dus - I_sc);                // t^2 : int sin^2
@@ -655,14 +659,16 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
       Sg = AC::template madd<P>(Sg, dJ, row, SL_G);
       Sn = AC::template madd<P>(Sn, dJ, row, SL_N);
       St = AC::template madd<P>(St, dP, row, SL_T);
-      if (MOM) {
-        const A e1 = dJ * d2a, e2 = dP * d2a;
+      if (MD >= 1) {
         S10 = AC::template madd<P>(S10, dJ, row, SL_10);
+        S01 = AC::template madd<P>(S01, dP, row, SL_01);
+      }
+      if (MD >= 3) {
+        const A e1 = dJ * d2a, e2 = dP * d2a;
         S20 = AC::template madd<P>(S20, dJ, row, SL_20);
         S30 = AC::template madd<P>(S30, dJ, row, SL_30);
         S02 = AC::template madd<P>(AC::template madd<P>(S02, dJ, row, SL_02A), e1, row, SL_02B);
         S12 = AC::template madd<P>(AC::template madd<P>(S12, dJ, row, SL_12A), e1, row, SL_12B);
-        S01 = AC::template madd<P>(S01, dP, row, SL_01);
         S11 = AC::template madd<P>(S11, dP, row, SL_11);
         S21 = AC::template madd<P>(S21, dP, row, SL_21);
         S03 = AC::template madd<P>(AC::template madd<P>(S03, dP, row, SL_03A), e2, row, SL_03B);
@@ -674,7 +680,8 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     step(1, dJp, zeroA);                                    // q = 0
     A p1 = AC::c(1), p2 = AC::c(1);                         // rho^q at the two ends
     A dJq2 = dJm, dJq1 = dJp;                               // Delta J_{q-2}, Delta J_{q-1}
-    constexpr int QMAX = MOM ? P::K + 4 : P::K;
+    // highest row any requested sum uses: gamma/gradient K, first moments K + 2, all K + 4
+    constexpr int QMAX = MD >= 3 ? P::K + 4 : (MD >= 1 ? P::K + 2 : P::K);
 #if SPH2D_Q_UNROLL
 #pragma unroll
 #else
@@ -694,10 +701,12 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     eg += d * AC::result(Sg);
     en += d2 * AC::result(Sn);
     et += d * AC::result(St);
-    if (MOM) {
-      const R d3 = d2 * d, d4 = d2 * d2;
+    if (MD >= 1) {
       E[1] += d2 * AC::result(S10);
       E[2] += d * AC::result(S01);
+    }
+    if (MD >= 3) {
+      const R d3 = d2 * d, d4 = d2 * d2;
       E[3] += d3 * AC::result(S20);
       E[4] += d2 * AC::result(S11);
       E[5] += d * AC::result(S02);
@@ -711,12 +720,14 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   o.g += eg;
   o.gx += en * nx - et * ny;
   o.gy += en * ny + et * nx;
-  if (MOM) {
+  if (MD >= 1) {
     // p_x = s nx - t ny, p_y = s ny + t nx: expand p_x^a p_y^b into s^j t^l
-    const R X = nx, Y = ny;
     o.m[0] += eg;
-    o.m[1] += X * E[1] - Y * E[2];
-    o.m[2] += Y * E[1] + X * E[2];
+    o.m[1] += nx * E[1] - ny * E[2];
+    o.m[2] += ny * E[1] + nx * E[2];
+  }
+  if (MD >= 3) {
+    const R X = nx, Y = ny;
     const R XX = X * X, YY = Y * Y, XY = X * Y;
     o.m[3] += XX * E[3] - R(2) * XY * E[4] + YY * E[5];
     o.m[4] += XY * E[3] + (XX - YY) * E[4] - XY * E[5];
@@ -732,13 +743,13 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
 }
 
 // signed sum over the three fans of one local-frame triangle, single polynomial piece
-template <typename R, class P, bool MOM, bool UNROLL_FANS>
+template <typename R, class P, int MD, bool UNROLL_FANS>
 SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   R x0 = ax, y0 = ay, x1 = bx, y1 = by, x2 = cx, y2 = cy;
   if (UNROLL_FANS) {
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      add_fan<R, P, MOM>(x0, y0, x1, y1, o);
+      add_fan<R, P, MD>(x0, y0, x1, y1, o);
       const R tx = x0, ty = y0;
       x0 = x1;
       y0 = y1;
@@ -751,7 +762,7 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   }
 #pragma unroll 1
   for (int e = 0; e < 3; ++e) {
-    add_fan<R, P, MOM>(x0, y0, x1, y1, o);
+    add_fan<R, P, MD>(x0, y0, x1, y1, o);
     const R tx = x0, ty = y0;
     x0 = x1;
     y0 = y1;
@@ -764,12 +775,12 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
 
 // raw integrals of kernel KID over the local-frame triangle, in input orientation
 // (multiply by the orientation sign for the unsigned integral)
-template <typename R, int KID, bool MOM>
+template <typename R, int KID, int MD>
 SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   clear(o);
-  if (KID == KID_WC2) tri_poly<R, PolyWC2, MOM, true>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MOM, true>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MOM, true>(ax, ay, bx, by, cx, cy, o);
+  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, true>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, true>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, true>(ax, ay, bx, by, cx, cy, o);
   else {
     // k(q) = 2 k1(q) - k1(2q), k1 = (1-q)^3_+.  With p' = 2p:
     //   int f(p) k1(2|p|) dA = 1/4 int f(p'/2) k1(|p'|) dA',  f = p^m -> 2^-m
@@ -780,18 +791,20 @@ SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
       const R sc = piece ? R(2) : R(1);
       PairOut<R> h;
       clear(h);
-      tri_poly<R, PolyCube, MOM, false>(sc * ax, sc * ay, sc * bx, sc * by, sc * cx, sc * cy, h);
+      tri_poly<R, PolyCube, MD, false>(sc * ax, sc * ay, sc * bx, sc * by, sc * cx, sc * cy, h);
       const R wg = piece ? R(-0.25) : R(2);     // 2^-(m+2), m = 0
       const R wd = piece ? R(-0.5) : R(2);      // gradient
       o.g += wg * h.g;
       o.gx += wd * h.gx;
       o.gy += wd * h.gy;
-      if (MOM) {
-        const R w1 = piece ? R(-0.125) : R(2), w2 = piece ? R(-0.0625) : R(2),
-                w3 = piece ? R(-0.03125) : R(2);
+      if (MD >= 1) {
+        const R w1 = piece ? R(-0.125) : R(2);
         o.m[0] += wg * h.m[0];
 #pragma unroll
         for (int i = 1; i < 3; ++i) o.m[i] += w1 * h.m[i];
+      }
+      if (MD >= 3) {
+        const R w2 = piece ? R(-0.0625) : R(2), w3 = piece ? R(-0.03125) : R(2);
 #pragma unroll
         for (int i = 3; i < 6; ++i) o.m[i] += w2 * h.m[i];
 #pragma unroll

@@ -76,6 +76,10 @@ sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, v
 sph2d_status launch_pair_integrals(Ctx* c, const double* pairs, int64_t P, int kernel, double H,
                                    int moment_degree, int mode, void* out);
 
+// piecewise-linear boundary fields over the context's pair list (fields.cu)
+sph2d_status launch_fields(Ctx* c, int kernel, int mode, const float* values, int nf, void* value,
+                           void* grad);
+
 // adjoint (backward.cu)
 sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma,
                              void* d_particles, void* d_tris);

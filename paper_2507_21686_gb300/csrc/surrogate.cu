@@ -523,12 +523,12 @@ __global__ void __launch_bounds__(128) surrogate_fallback_kernel(IntArgs a, cons
     const int64_t q = sa.fb_list[i];
     float v[3];
     if (LIST) {
-      eval_pair<float, KID, false>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
+      eval_pair<float, KID, 0>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
     } else {
       double ld[6];
       float lf[6];
       pair_local(pairs + 8 * q, a.invH, ld, lf);
-      eval_mode<float, KID, false>(ld, a.C, a.invH, v);
+      eval_mode<float, KID, 0>(ld, a.C, a.invH, v);
     }
     sa.vals[3 * q] = v[0];
     sa.vals[3 * q + 1] = v[1];
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(128) reduce_vals_kernel(IntArgs a, const float
     if (head) {
       const int64_t cs = ch * 32;
       const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
-      if (s0 >= cs && s1 <= cs + 32) write_particle<float, false>(a, pid, v);
+      if (s0 >= cs && s1 <= cs + 32) write_particle<float, 0>(a, pid, v);
       float* slots = static_cast<float*>(a.slots);
       if (lane == 0) {
 #pragma unroll
@@ -908,7 +908,7 @@ sph2d_status surrogate_integrals(Ctx* c, void* gamma, void* grad) {
     const unsigned g = persistent_grid(c, reduce_vals_kernel, ((a.P + 31) / 32 + 3) / 4);
     SPH2D_LAUNCH(c, (reduce_vals_kernel), g, 128, a, sa.vals);
   }
-  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<float, false>), nblk(a.N), 256, a);
+  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<float, 0>), nblk(a.N), 256, a);
   return serving_finish(c, sa, cl.P);
 }
 

@@ -46,13 +46,20 @@ def _load():
     return _lib
 
 
-def pair_ops(kernel, moments: bool, fp32: bool, local_tri) -> tuple[int, np.ndarray]:
+def _degree(moments) -> int:
+    """moments: True (all ten, degree 3), False (none) or a moment degree -1..3."""
+    if isinstance(moments, bool):
+        return 3 if moments else -1
+    return int(moments)
+
+
+def pair_ops(kernel, moments, fp32: bool, local_tri) -> tuple[int, np.ndarray]:
     """(flops, [add, mul, fma, div, sqrt, transcendental, other]) for one local-frame pair."""
     lib = _load()
     l = np.ascontiguousarray(local_tri, dtype=np.float64).reshape(6)
     out = np.zeros(7, dtype=np.int64)
     k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    f = lib.sph2d_count_pair_ops(k, int(bool(moments)), int(bool(fp32)), l.ctypes.data, out.ctypes.data)
+    f = lib.sph2d_count_pair_ops(k, _degree(moments), int(bool(fp32)), l.ctypes.data, out.ctypes.data)
     return int(f), out
 
 
