@@ -93,8 +93,9 @@ def test_constant_field_matches_boundary_integrals(ctx):
     val, gr = ctx.field_integrals(_t(vv), "wendland_c2", "fp64")
     g, gg = g.cpu().numpy(), gg.cpu().numpy()
     val, gr = val.cpu().numpy()[:, 0], gr.cpu().numpy()[:, 0]
-    # the value uses the same gamma sums (bit for bit); the gradient comes by parts
-    assert np.array_equal(val, np.float64(1.75) * g)
+    # the value uses the same gamma sums (to a few ulps: the two instantiations may contract
+    # different multiply-adds); the gradient comes by parts, a different route
+    assert np.max(np.abs(val - 1.75 * g)) <= 1e-14 * 1.75
     s = scales("wendland_c2", H, 0)[1]
     assert np.max(np.abs(gr - 1.75 * gg)) <= TOL_FP64 * 1.75 * s
 
