@@ -398,6 +398,9 @@ def run_ours(args):
     gamma_grad_only = {"per_kernel_ms": gg, "value": P * len(KERNELS) / (sum(gg.values()) / 1e3),
                        "unit": UNIT, "note": "integral launches only (culling excluded), no moments"}
 
+    # ---- piecewise-linear boundary fields (two fields, Wendland C4) over the same pair list
+    fields = run_fields(ctx, parts, tris, w, stream, flush, P)
+
     # ---- adjoint workload: 262,144 particles x 51,712 triangles, Wendland C4
     adjoint = run_adjoint(ctx, dev, stream, flush)
 
@@ -458,6 +461,7 @@ def run_ours(args):
         "case_histogram": case_hist,
         "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
         "gamma_grad_only": gamma_grad_only,
+        "fields": fields,
         "adjoint": adjoint,
         "surrogate": surrogate,
         "e2e": e2e,
@@ -465,6 +469,40 @@ def run_ours(args):
         "measured_peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):
+    """<A> and <grad A> of two per-vertex fields (rho = 1 + x y / 4 and rho u, u = sin 3x +
+    cos 2y) on the benchmark pair list, FP32 + fix-up and FP64."""
+    import torch
+    ctx.build_cells(parts, tris, w.H)
+    v = w.triangles.reshape(-1, 3, 2).astype(np.float64)
+    rho = 1.0 + 0.25 * v[..., 0] * v[..., 1]
+    u = np.sin(3 * v[..., 0]) + np.cos(2 * v[..., 1])
+    vv = torch.from_numpy(np.stack([rho, rho * u], axis=-1).astype(np.float32)).to(parts.device)
+    k = "wendland_c4"
+    out, res = {}, {"kernel": k, "fields": 2, "pairs": P}
+    for mode in ("fp32_fixup", "fp64"):
+        out[mode] = ctx.field_integrals(vv, k, mode)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a_, b_ in ev:
+            flush.zero_()
+            a_.record(stream)
+            ctx.field_integrals(vv, k, mode)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+        res[mode] = {"ms": ms, "pairs_per_s": P / (ms / 1e3)}
+    a32, g32 = out["fp32_fixup"]
+    a64, g64 = out["fp64"]
+    sa = float(np.max(np.abs(vv.cpu().numpy())))
+    from tests.helpers import scales
+    sg = scales(k, w.H, 0)[1]
+    res["max_err_fp32_vs_fp64"] = {
+        "value": float(((a32.double() - a64).abs() / torch.clamp(a64.abs(), min=sa)).max()),
+        "grad": float(((g32.double() - g64).abs() / torch.clamp(g64.abs(), min=sa * sg)).max())}
+    res["speedup_fp32_vs_fp64"] = res["fp64"]["ms"] / res["fp32_fixup"]["ms"]
+    return res
 
 
 def run_adjoint(ctx, dev, stream, flush, steps=3):
