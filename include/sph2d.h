@@ -191,17 +191,24 @@ sph2d_status sph2d_pair_integrals(sph2d_ctx* ctx, const double* pairs, int64_t P
                                   double H, int moment_degree, int mode, void* out);
 
 /*
- * Adjoint of sph2d_boundary_integrals for a loss L(gamma): given dL/dgamma, returns
- *   d_particles [N][2] = dL/dx_i      = dL/dgamma_i * grad_gamma_i   (Sec. 3, Eq. basicdiff)
- *   d_tris      [M][6] = dL/dnu_j     = sum_i dL/dgamma_i * d gamma_i / d nu_j
- * where d gamma_i/d nu_j is the transport-theorem edge integral of W weighted by the
- * vertex's hat function (no counterpart printed in the paper; it is the derivative of its
- * area integral with respect to the boundary).  The pair list is rebuilt from the inputs;
- * per-pair geometry is recomputed, nothing is stored from the forward call.  Vertex
- * gradients are reduced triangle-major in a fixed order (deterministic).
+ * Adjoint of sph2d_boundary_integrals for a loss L(gamma, grad gamma): given dL/dgamma and
+ * optionally dL/dgrad gamma, returns
+ *   d_particles [N][2] = dL/dx_i  = dL/dgamma_i grad gamma_i           (Sec. 3, Eq. basicdiff)
+ *                                  + (d grad gamma_i / d x_i)^T dL/dgrad gamma_i
+ *   d_tris      [M][6] = dL/dnu_j = sum_i dL/dgamma_i d gamma_i / d nu_j
+ *                                  + (d grad gamma_i / d nu_j)^T dL/dgrad gamma_i
+ * where d gamma_i/d nu_j is the transport-theorem edge integral of W weighted by the vertex's
+ * hat function, and d grad gamma / d nu_j the derivative of the divergence-theorem boundary
+ * form grad gamma = -oint W n ds edge by edge (closed-form square-root integrals of k'(r)/r and
+ * k'(r) r, and k at the clipped edge ends); d grad gamma_i / d x_i = -sum_j d grad gamma_i /
+ * d nu_j.  None of these is printed in the paper: they are derivatives of its integrals.
+ * The pair list is rebuilt from the inputs; per-pair geometry is recomputed, nothing is stored
+ * from the forward call.  Vertex gradients are reduced triangle-major and the second-order
+ * particle terms particle-major, both in fixed orders (deterministic).
  *   d_gamma       device real [N]
- *   d_grad_gamma  must be NULL (second-order terms are not provided: UNSUPPORTED)
- * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, UNSUPPORTED, CUDA.
+ *   d_grad_gamma  device real [N][2], or NULL for a loss of gamma alone
+ * Errors: INVALID_ARG, NONFINITE_INPUT, OUT_OF_MEMORY, UNSUPPORTED (surrogate mode; more than
+ * 2^31 - 1 pairs), CUDA.
  */
 sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* ctx, const float* particles,
                                                int64_t N, const float* tris, int64_t M,

@@ -66,6 +66,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.orc_pairs.argtypes = [Ci, D, P, I64, P]
     lib.orc_pairs_vertex_grad.argtypes = [Ci, D, P, I64, P]
     lib.orc_pair_field.argtypes = [Ci, D, P, P, P, P]
+    lib.orc_grad_jacobian.argtypes = [Ci, D, P, P, P]
+    lib.orc_pairs_grad_jacobian.argtypes = [Ci, D, P, I64, P]
     lib.orc_pairs_field.argtypes = [Ci, D, P, P, I64, P]
     lib.orc_kernel_C.argtypes = [Ci]
     lib.orc_kernel_C.restype = D
@@ -76,7 +78,7 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.orc_gauss_legendre.argtypes = [Ci, P, P]
     for f in ("orc_pair", "orc_vertex_grad", "orc_cull", "orc_particle_sums", "orc_pairs",
               "orc_pairs_vertex_grad", "orc_num_threads", "orc_version", "orc_pair_field",
-              "orc_pairs_field"):
+              "orc_pairs_field", "orc_grad_jacobian", "orc_pairs_grad_jacobian"):
         getattr(lib, f).restype = ctypes.c_int if f != "orc_kernel_C" else D
     _libs[mutant] = lib
     return lib
@@ -198,6 +200,23 @@ def particle_field_sums(kernel, H: float, particles: np.ndarray, triangles: np.n
         np.add.at(grad[:, f, 0], pid, r[:, 1])
         np.add.at(grad[:, f, 1], pid, r[:, 2])
     return val, grad
+
+
+def grad_jacobian(kernel, H: float, xp, tri) -> np.ndarray:
+    """d grad gamma / d nu_j, [3, 2, 2] with [j, b, a] = d (grad gamma)_b / d (nu_j)_a, from the
+    divergence-theorem boundary form differentiated edge by edge (1-D quadratures)."""
+    xp = np.ascontiguousarray(xp, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.float64).reshape(6)
+    out = np.zeros(12)
+    _lib().orc_grad_jacobian(_kid(kernel), float(H), _ptr(xp), _ptr(tri), _ptr(out))
+    return out.reshape(3, 2, 2)
+
+
+def pairs_grad_jacobian(kernel, H: float, pairs_arr: np.ndarray) -> np.ndarray:
+    p = np.ascontiguousarray(pairs_arr, dtype=np.float64).reshape(-1, 8)
+    out = np.zeros((len(p), 12))
+    _lib().orc_pairs_grad_jacobian(_kid(kernel), float(H), _ptr(p), len(p), _ptr(out))
+    return out.reshape(-1, 3, 2, 2)
 
 
 def cull(particles: np.ndarray, triangles: np.ndarray, H: float):

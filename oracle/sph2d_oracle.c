@@ -579,6 +579,99 @@ int orc_pair_field(int kid, double H, const double* xp, const double* tri, const
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* second order: d grad gamma / d nu_j.  grad gamma = -(C/H) oint k(|p|) n_out ds in the    */
+/* local frame (divergence theorem).  Edge e = (A, B): F_e = n_out L int_0^1 k(|A + s(B-A)|) */
+/* ds; its derivative by B is sg R I + n_out L (x) U_s and by A is -sg R I + n_out L (x)     */
+/* (U_1 - U_s), R (x, y) = (y, -x), I = int k ds, U_1 = int k'(rho) p/rho ds, U_s = int       */
+/* k'(rho) p/rho s ds (s from A to B).  Here I, U_1, U_s are plain 1-D quadratures.         */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { int kid; double ax, ay, ex, ey; } edge2_ctx;
+
+static void edge2_fn(const void* ctx, double s, double* f) {
+  const edge2_ctx* ec = (const edge2_ctx*)ctx;
+  double px = ec->ax + s * ec->ex, py = ec->ay + s * ec->ey;
+  double r = hypot(px, py);
+  double k = orc_kernel_k(ec->kid, r);
+  double dk = r > 0.0 ? orc_kernel_dk(ec->kid, r) / r : 0.0;     /* k'(r)/r, p/r direction */
+  f[0] = k;
+  f[1] = dk * px;
+  f[2] = dk * py;
+  f[3] = dk * px * s;
+  f[4] = dk * py * s;
+}
+
+static void edge2_integrals(int kid, const double* A, const double* B, double* out5, quad_stats* st) {
+  edge2_ctx ec = {kid, A[0], A[1], B[0] - A[0], B[1] - A[1]};
+  for (int i = 0; i < 5; ++i) out5[i] = 0.0;
+  double L2 = ec.ex * ec.ex + ec.ey * ec.ey;
+  if (L2 == 0.0) return;
+  double bp[16];
+  int nb = 0;
+  bp[nb++] = 0.0;
+  bp[nb++] = 1.0;
+  double sf = -(A[0] * ec.ex + A[1] * ec.ey) / L2;
+  if (sf > 0.0 && sf < 1.0) bp[nb++] = sf;
+  double radii[2];
+  int nr = kernel_piece_radii(kid, radii);
+  double dd = A[0] * A[0] + A[1] * A[1] - (A[0] * ec.ex + A[1] * ec.ey) * (A[0] * ec.ex + A[1] * ec.ey) / L2;
+  if (dd < 0) dd = 0;
+  for (int k = 0; k < nr; ++k) {
+    double R2 = radii[k] * radii[k];
+    if (dd < R2) {
+      double hw = sqrt((R2 - dd) / L2);
+      if (sf - hw > 0.0 && sf - hw < 1.0) bp[nb++] = sf - hw;
+      if (sf + hw > 0.0 && sf + hw < 1.0) bp[nb++] = sf + hw;
+    }
+  }
+  qsort(bp, nb, sizeof(double), cmp_dbl);
+  for (int i = 0; i + 1 < nb; ++i) integrate(edge2_fn, &ec, 5, bp[i], bp[i + 1], 1e-17, out5, st);
+}
+
+/* out[12]: out[4 j + 2 b + a] = d (grad gamma)_b / d (nu_j)_a, caller's vertex order */
+int orc_grad_jacobian(int kid, double H, const double* xp, const double* tri, double* out) {
+  if (!kernel_ok(kid) || !(H > 0.0)) return -1;
+  gl_init();
+  for (int i = 0; i < 12; ++i) out[i] = 0.0;
+  double p[6];
+  for (int j = 0; j < 3; ++j) {
+    p[2 * j] = (tri[2 * j] - xp[0]) / H;
+    p[2 * j + 1] = (tri[2 * j + 1] - xp[1]) / H;
+  }
+  double area2 = (p[2] - p[0]) * (p[5] - p[1]) - (p[3] - p[1]) * (p[4] - p[0]);
+  if (area2 == 0.0) return 0;
+  double sg = area2 > 0 ? 1.0 : -1.0;
+  quad_stats st = {0, 0};
+  double scale = -orc_kernel_C(kid) / (H * H);
+  for (int e = 0; e < 3; ++e) {
+    int ia = e, ib = (e + 1) % 3;
+    const double* A = p + 2 * ia;
+    const double* B = p + 2 * ib;
+    double ex = B[0] - A[0], ey = B[1] - A[1], L = hypot(ex, ey);
+    if (L == 0.0) continue;
+    double nLx = sg * ey, nLy = -sg * ex;        /* n_out L = sg R (B - A) */
+    double q[5];
+    edge2_integrals(kid, A, B, q, &st);
+    double I = q[0], U1[2] = {q[1], q[2]}, Us[2] = {q[3], q[4]};
+    double RI[2][2] = {{0.0, sg * I}, {-sg * I, 0.0}};
+    double nL[2] = {nLx, nLy};
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        out[4 * ib + 2 * b + a] += scale * (RI[b][a] + nL[b] * Us[a]);
+        out[4 * ia + 2 * b + a] += scale * (-RI[b][a] + nL[b] * (U1[a] - Us[a]));
+      }
+  }
+  return st.max_depth_hit ? 1 : 0;
+}
+
+int orc_pairs_grad_jacobian(int kid, double H, const double* pairs, int64_t P, double* out /*[P][12]*/) {
+  if (!kernel_ok(kid) || !(H > 0.0)) return -1;
+  gl_init();
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t q = 0; q < P; ++q) orc_grad_jacobian(kid, H, pairs + 8 * q, pairs + 8 * q + 2, out + 12 * q);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* culling predicate: the operation order is part of the interface (include/sph2d.h)    */
 /* ------------------------------------------------------------------------------------ */
 static int cull_keep(double px, double py, const float* tf, double H2) {

@@ -187,18 +187,20 @@ class Context:
         return val, gr
 
     # -- adjoint -----------------------------------------------------------------------
-    def backward(self, particles, tris, kernel, H: float, d_gamma, mode="fp64"):
-        """dL/dx [N, 2] and dL/dvertices [M, 6] from dL/dgamma [N]."""
+    def backward(self, particles, tris, kernel, H: float, d_gamma, mode="fp64", d_grad=None):
+        """dL/dx [N, 2] and dL/dvertices [M, 6] from dL/dgamma [N] and optionally
+        dL/dgrad gamma [N, 2]."""
         p = as_particles(particles, self._dev())
         t = as_triangles(tris, self._dev())
         dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
         dg = d_gamma.to(device=self._dev(), dtype=dt).contiguous()
+        dgr = d_grad.to(device=self._dev(), dtype=dt).contiguous() if d_grad is not None else None
         dp = torch.empty((p.shape[0], 2), dtype=dt, device=self._dev())
         dtr = torch.empty((t.shape[0], 6), dtype=dt, device=self._dev())
         self._bind_stream()
         check(self.lib, self.h, self.lib.sph2d_boundary_integrals_backward(
             self.h, _ptr(p), p.shape[0], _ptr(t), t.shape[0], _kernel_id(kernel), float(H),
-            _mode_id(mode), _ptr(dg), None, _ptr(dp), _ptr(dtr)))
+            _mode_id(mode), _ptr(dg), _ptr(dgr) if dgr is not None else None, _ptr(dp), _ptr(dtr)))
         return dp, dtr
 
     # -- learned surrogate -------------------------------------------------------------
@@ -290,23 +292,24 @@ def pair_integrals(pairs, kernel, H: float, moment_degree: int = -1, mode="fp64"
 
 
 class BoundaryGamma(torch.autograd.Function):
-    """gamma(particles, triangles) with the library's adjoint kernel as backward.
+    """(gamma, grad gamma)(particles, triangles) with the library's adjoint kernels as backward.
 
-    Gradients flow to particle positions (x, y) and triangle vertices.  Only gamma is
-    differentiable here (grad_gamma is returned detached)."""
+    Gradients flow to particle positions (x, y) and triangle vertices through both outputs
+    (the grad gamma path uses the second-order kernels)."""
 
     @staticmethod
     def forward(ctx, particles, tris, kernel, H, mode):
         g, gr, _ = context().boundary_integrals(particles, tris, kernel, H, -1, mode, True)
         ctx.save_for_backward(particles, tris)
         ctx.kernel, ctx.H, ctx.mode = kernel, H, mode
-        ctx.mark_non_differentiable(gr)
         return g, gr
 
     @staticmethod
     def backward(ctx, d_gamma, d_grad):
         particles, tris = ctx.saved_tensors
-        dp, dt = context().backward(particles, tris, ctx.kernel, ctx.H, d_gamma, ctx.mode)
+        if d_gamma is None:
+            d_gamma = torch.zeros(particles.shape[0], dtype=particles.dtype, device=particles.device)
+        dp, dt = context().backward(particles, tris, ctx.kernel, ctx.H, d_gamma, ctx.mode, d_grad)
         gp = torch.zeros_like(particles)
         gp[:, :2] = dp.to(particles.dtype)
         return gp, dt.to(tris.dtype).reshape(tris.shape), None, None, None

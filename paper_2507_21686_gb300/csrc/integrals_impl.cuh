@@ -206,6 +206,56 @@ __device__ __forceinline__ int vertex_grad_pair(const float4 p, const float* t, 
   return sizeof(OT) == sizeof(float) ? 1 : 0;
 }
 
+// d grad gamma / d nu_j of one culled pair in world units, J[12] with J[4 j + 2 b + a] =
+// d (grad gamma)_b / d (nu_j)_a, in the mode's precision; FP32 geometry is trusted under the
+// same rule as vertex_grad_pair; returns 1 if the FP64 path was used
+template <typename OT, int KID>
+__device__ __forceinline__ int grad_jacobian_pair(const float4 p, const float* t, double invH, double C, OT* J) {
+  if (sizeof(OT) == sizeof(float)) {
+    const float ih = float(invH);
+    float v[6];
+    float pmax = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      v[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+      v[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+      pmax = fmaxf(pmax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+    }
+    const float a2 = fabsf(diff_of_products(v[2] - v[0], v[5] - v[1], v[3] - v[1], v[4] - v[0]));
+    float lmax = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int b = e == 2 ? 0 : e + 1;
+      const float ex = v[2 * b] - v[2 * e], ey = v[2 * b + 1] - v[2 * e + 1];
+      lmax = fmaxf(lmax, sqrtf(ex * ex + ey * ey));
+    }
+    if (pmax <= kFixupCoordLimit && (a2 == 0.0f || 64.0f * a2 >= lmax * pmax)) {
+      float w[12];
+      tri_grad_jacobian<float, KID>(v, w);
+      bool ok = true;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) ok = ok && isfinite(w[i]);
+      if (ok) {
+        const float k = float(-C * invH * invH);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) J[i] = OT(k * w[i]);
+        return 0;
+      }
+    }
+  }
+  double v[6], w[12];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    v[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * invH;
+    v[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * invH;
+  }
+  tri_grad_jacobian<double, KID>(v, w);
+  const double k = -C * invH * invH;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) J[i] = OT(k * w[i]);
+  return sizeof(OT) == sizeof(float) ? 1 : 0;
+}
+
 template <typename OT, int MD>
 __device__ __forceinline__ void write_particle(const IntArgs& a, int64_t pid, const OT* v) {
   static_cast<OT*>(a.gamma)[pid] = v[0];

@@ -85,6 +85,14 @@ struct PolyWC6 {
          : k == 8 ? -1155.0 : k == 9 ? 704.0 : k == 10 ? -231.0 : k == 11 ? 32.0 : 0.0;
   }
 };
+struct PolyCubeIn {  // cubic spline for q < 1/2: 1 - 6 q^2 + 6 q^3
+  static constexpr int K = 3;
+  SPH2D_HD static constexpr double b(int k) { return k == 0 ? 1.0 : k == 2 ? -6.0 : k == 3 ? 6.0 : 0.0; }
+};
+struct PolyCubeOut {  // cubic spline for 1/2 <= q < 1: 2 (1-q)^3
+  static constexpr int K = 3;
+  SPH2D_HD static constexpr double b(int k) { return k == 0 ? 2.0 : k == 1 ? -6.0 : k == 2 ? 6.0 : k == 3 ? -2.0 : 0.0; }
+};
 struct PolyCube {  // (1-q)^3
   static constexpr int K = 3;
   SPH2D_HD static constexpr double b(int k) {
@@ -895,6 +903,142 @@ SPH2D_HD void tri_vertex_grad_poly(const R* v, R* g) {
     g[2 * ia + 1] += wa * ny;
     g[2 * ib] += wb * nx;
     g[2 * ib + 1] += wb * ny;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// second order: Jacobians of grad gamma.  grad gamma = -(C/H) oint k(|p|) n_out ds (divergence
+// theorem, local frame).  Per edge e = (A, B) with outward normal n and unit tangent u, on the
+// line p = f n + t u (f = A . n, rho^2 = f^2 + t^2, t from the foot of the perpendicular):
+//   F_e = n L I,  I = int_0^1 k ds = Jo / L,  Jo = int k dt
+//   dF_e/dB = sg R I + (n L) (x) U_s,   dF_e/dA = -sg R I + (n L) (x) (U_1 - U_s)
+//   U_1 = int_0^1 k'(rho) p/rho ds     = (n f S0 + u Dk) / L
+//   U_s = int_0^1 k'(rho) p/rho s ds   = (n f (Dk - tA S0) + u (S2 - f^2 S0 - tA Dk)) / L^2
+// with S0 = int k'(rho)/rho dt, S2 = int k'(rho) rho dt (square-root integrals: sums of
+// Delta J_q with the coefficients of k'(q)/q and k'(q) q), Dk = int k'(rho) t/rho dt
+// = k(rho_2) - k(rho_1) = sum_m b_m Delta rho^m (from the recurrence's compensated powers: a
+// direct difference of two kernel values cancels near the support edge), R the rotation
+// (x, y) -> (y, -x), sg the orientation.  Then
+// d grad gamma / d nu_j = -(C/H^2) sum_{e ni j} dF_e/dv_j and d grad gamma / d x_i = -sum_j
+// of those (translation invariance); the last equals (C/H^2) oint k'(rho) n (x) p/rho ds.
+// ---------------------------------------------------------------------------------------
+template <typename R, class P>
+SPH2D_HD void edge_grad_integrals(R d, R t1, R t2, R& Jo, R& S0, R& S2, R& Dk) {
+  using AC = typename AccSel<R, P>::type;
+  using A = typename AC::T;
+  using SM = typename AC::Sum;
+  SM sJ = AC::zero(), s0 = AC::zero(), s2 = AC::zero(), sk = AC::zero();
+  if (!(t2 > t1)) {
+    Jo = S0 = S2 = Dk = R(0);
+    return;
+  }
+  const A d2a = AC::sq(d);
+  const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
+  const R r1 = sqrt(d * d + t1 * t1), r2 = sqrt(d * d + t2 * t2);
+  // Delta J_{-1} = asinh(t2/d) - asinh(t1/d): needed as such only when k'(q)/q has a 1/q term
+  // (then the interval never reaches the particle), otherwise only as d^2 J_{-1}
+  const bool need_m1 = bk<P>(1) != 0.0;
+  const A dJm = (d > Tiny<R>::v() || (need_m1 && t1 * t2 > R(0))) ? AC::jm1(t1, t2, r1, r2, d, r1a, r2a) : AC::c(0);
+  const A dJp = AC::from(t2) - AC::from(t1);
+  // row q = -1 and q = 0
+  if (need_m1) s0 = AC::maddc(s0, dJm, bk<P>(1), 1.0);
+  sJ = AC::maddc(sJ, dJp, bk<P>(0), 1.0);
+  s0 = AC::maddc(s0, dJp, 2.0 * bk<P>(2), 1.0);
+  A p1 = AC::c(1), p2 = AC::c(1);
+  A dJq2 = dJm, dJq1 = dJp;
+#pragma unroll
+  for (int q = 1; q <= P::K; ++q) {
+    p1 = p1 * r1a;
+    p2 = p2 * r2a;
+    const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);
+    const R qf = R(q), iq = R(1) / R(q + 1);
+    const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);
+    sJ = AC::maddc(sJ, dJ, bk<P>(q), 1.0);
+    s0 = AC::maddc(s0, dJ, double(q + 2) * bk<P>(q + 2), 1.0);
+    s2 = AC::maddc(s2, dJ, double(q) * bk<P>(q), 1.0);
+    sk = AC::maddc(sk, p2 - p1, bk<P>(q), 1.0);
+    dJq2 = dJq1;
+    dJq1 = dJ;
+  }
+  Jo = AC::result(sJ);
+  S0 = AC::result(s0);
+  S2 = AC::result(s2);
+  Dk = AC::result(sk);
+}
+
+// edge integrals Jo, S0, S2 of kernel KID over t in [t1, t2] (already clipped to the support)
+template <typename R, int KID>
+SPH2D_HD void edge_grad_integrals_k(R d, R t1, R t2, R& Jo, R& S0, R& S2, R& Dk) {
+  if (KID == KID_WC2) edge_grad_integrals<R, PolyWC2>(d, t1, t2, Jo, S0, S2, Dk);
+  else if (KID == KID_WC4) edge_grad_integrals<R, PolyWC4>(d, t1, t2, Jo, S0, S2, Dk);
+  else if (KID == KID_WC6) edge_grad_integrals<R, PolyWC6>(d, t1, t2, Jo, S0, S2, Dk);
+  else {
+    // inner polynomial on |t| < th (rho < 1/2), outer polynomial on the rest
+    const R th = d < R(0.5) ? sqrt((R(0.5) - d) * (R(0.5) + d)) : R(0);
+    R j, s0, s2, dk;
+    // inner [max(t1, -th), min(t2, th)], outer [t1, min(t2, -th)] and [max(t1, th), t2]
+    // (empty intervals contribute 0; k is continuous at 1/2, so the Dk pieces telescope)
+    edge_grad_integrals<R, PolyCubeIn>(d, fmax(t1, -th), fmin(t2, th), Jo, S0, S2, Dk);
+    edge_grad_integrals<R, PolyCubeOut>(d, t1, fmin(t2, -th), j, s0, s2, dk);
+    Jo += j;
+    S0 += s0;
+    S2 += s2;
+    Dk += dk;
+    edge_grad_integrals<R, PolyCubeOut>(d, fmax(t1, th), t2, j, s0, s2, dk);
+    Jo += j;
+    S0 += s0;
+    S2 += s2;
+    Dk += dk;
+  }
+}
+
+// raw Jacobians (without -C/H^2): J[12], J[4 j + 2 b + a] = d F_b / d v_{j,a} summed over the
+// two edges of vertex j (grad gamma = -(C/H) sum_e F_e, so d grad gamma / d nu = -(C/H^2) J)
+template <typename R, int KID>
+SPH2D_HD void tri_grad_jacobian(const R* v, R* J) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) J[i] = R(0);
+  const R area2 = diff_of_products(v[2] - v[0], v[5] - v[1], v[3] - v[1], v[4] - v[0]);
+  if (area2 == R(0)) return;
+  const R sg = area2 > R(0) ? R(1) : R(-1);
+#pragma unroll 1
+  for (int e = 0; e < 3; ++e) {
+    const int ia = e, ib = e == 2 ? 0 : e + 1;
+    const R ax = v[2 * ia], ay = v[2 * ia + 1], bx = v[2 * ib], by = v[2 * ib + 1];
+    const R ex = bx - ax, ey = by - ay;
+    const R l2 = ex * ex + ey * ey;
+    if (l2 == R(0)) continue;
+    const R L = sqrt(l2), il = R(1) / L;
+    const R ux = ex * il, uy = ey * il;                  // unit tangent
+    const R nx = sg * uy, ny = -sg * ux;                 // outward unit normal
+    const R f = ax * nx + ay * ny;                       // signed line distance along n
+    const R d = fabs(f);
+    const R tA = ax * ux + ay * uy, tB = bx * ux + by * uy;
+    if (!(d < R(1))) continue;                           // edge line outside the support
+    const R ts = sqrt((R(1) - d) * (R(1) + d));
+    const R t1 = fmin(fmax(tA, -ts), ts), t2 = fmin(fmax(tB, -ts), ts);
+    if (!(t2 > t1)) continue;
+    R Jo, S0, S2, Dk;
+    edge_grad_integrals_k<R, KID>(d, t1, t2, Jo, S0, S2, Dk);
+    const R I = Jo * il;
+    // U_1 and U_s in (n, u) components, then to x, y
+    const R u1n = f * S0 * il, u1t = Dk * il;
+    const R usn = f * (Dk - tA * S0) * il * il, ust = (S2 - f * f * S0 - tA * Dk) * il * il;
+    const R U1x = u1n * nx + u1t * ux, U1y = u1n * ny + u1t * uy;
+    const R Usx = usn * nx + ust * ux, Usy = usn * ny + ust * uy;
+    const R nLx = nx * L, nLy = ny * L;
+    // sg R I: R = [[0, 1], [-1, 0]]
+    const R rI01 = sg * I, rI10 = -sg * I;
+    // vertex B: sg R I + nL (x) U_s
+    J[4 * ib + 0] += nLx * Usx;
+    J[4 * ib + 1] += rI01 + nLx * Usy;
+    J[4 * ib + 2] += rI10 + nLy * Usx;
+    J[4 * ib + 3] += nLy * Usy;
+    // vertex A: -sg R I + nL (x) (U_1 - U_s)
+    J[4 * ia + 0] += nLx * (U1x - Usx);
+    J[4 * ia + 1] += -rI01 + nLx * (U1y - Usy);
+    J[4 * ia + 2] += -rI10 + nLy * (U1x - Usx);
+    J[4 * ia + 3] += nLy * (U1y - Usy);
   }
 }
 

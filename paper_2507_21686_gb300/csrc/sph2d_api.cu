@@ -373,14 +373,12 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* h, const float* partic
   if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
     return set_err(c, mode == SPH2D_SURROGATE ? SPH2D_ERR_UNSUPPORTED : SPH2D_ERR_INVALID_ARG,
                    "backward supports SPH2D_FP64 and SPH2D_FP32_FIXUP");
-  if (d_grad_gamma)
-    return set_err(c, SPH2D_ERR_UNSUPPORTED, "gradients through grad_gamma are not provided");
   if ((N > 0 && (!d_gamma || !d_particles)) || (M > 0 && !d_tris))
     return set_err(c, SPH2D_ERR_INVALID_ARG, "null gradient pointer");
   cudaSetDevice(c->device);
   s = build_cells(c, particles, N, tris, M, H);
   if (s != SPH2D_OK) return s;
-  return launch_backward(c, kernel, mode, d_gamma, d_particles, d_tris);
+  return launch_backward(c, kernel, mode, d_gamma, d_grad_gamma, d_particles, d_tris);
 }
 
 sph2d_status sph2d_field_integrals(sph2d_ctx* h, int kernel, int mode, const float* vertex_values, int nf,

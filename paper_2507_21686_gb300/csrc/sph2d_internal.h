@@ -82,7 +82,7 @@ sph2d_status launch_fields(Ctx* c, int kernel, int mode, const float* values, in
 
 // adjoint (backward.cu)
 sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma,
-                             void* d_particles, void* d_tris);
+                             const void* d_grad, void* d_particles, void* d_tris);
 
 // learned surrogate (surrogate.cu); callers validate arguments and sur_ready
 sph2d_status surrogate_init(Ctx* c, int kernel, uint64_t seed);

@@ -117,7 +117,7 @@ def test_autograd_function(ctx):
     assert torch.allclose(gt, dtr, rtol=1e-6, atol=1e-6 * dtr.abs().max().item())
 
 
-def test_backward_rejects_second_order_and_bad_args(ctx):
+def test_backward_rejects_bad_args(ctx):
     import torch
     from paper_2507_21686_gb300._lib import Sph2dError
     from paper_2507_21686_gb300.api import _ptr
@@ -127,7 +127,75 @@ def test_backward_rejects_second_order_and_bad_args(ctx):
     dp = torch.zeros((len(w.particles), 2), dtype=torch.float64, device="cuda")
     dt = torch.zeros((len(w.triangles), 6), dtype=torch.float64, device="cuda")
     st = ctx.lib.sph2d_boundary_integrals_backward(ctx.h, _ptr(p), p.shape[0], _ptr(t), t.shape[0], 0,
-                                                   w.H, 0, _ptr(dg), _ptr(dp), _ptr(dp), _ptr(dt))
-    assert st == 6                                       # d_grad_gamma given: UNSUPPORTED
+                                                   w.H, 2, _ptr(dg), None, _ptr(dp), _ptr(dt))
+    assert st == 6                                       # surrogate mode: UNSUPPORTED
     with pytest.raises(Sph2dError):
         ctx.backward(p, t, "wendland_c2", -1.0, dg, "fp64")
+
+
+# ---------------------------------------------------------------------------------------
+# second order: dL/d grad gamma
+# ---------------------------------------------------------------------------------------
+def oracle_backward2(kernel, H, parts, tris, dg, dgr):
+    """first-order part plus (d grad gamma / d x_i)^T G_i and (d grad gamma / d nu_j)^T G_i"""
+    ref_p, ref_t, _ = oracle_backward(kernel, H, parts, tris, dg)
+    off, pt = oracle.cull(parts, tris, H)
+    pid = np.repeat(np.arange(len(parts)), np.diff(off))
+    pairs = np.zeros((len(pt), 8))
+    pairs[:, :2] = parts[pid, :2]
+    pairs[:, 2:] = tris[pt]
+    J = oracle.pairs_grad_jacobian(kernel, H, pairs)            # [P, 3, b, a]
+    G = dgr[pid]                                                 # [P, 2]
+    vt = np.einsum("pjba,pb->pja", J, G)                         # J_j^T G
+    dtri = ref_t.copy()
+    np.add.at(dtri, pt, vt.reshape(-1, 6))
+    dp = ref_p.copy()
+    np.add.at(dp, pid, -vt.sum(axis=1))
+    return dp, dtri
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32_fixup"])
+@pytest.mark.parametrize("kernel", ["wendland_c2", "wendland_c4", "wendland_c6", "cubic_spline"])
+def test_second_order_backward_matches_oracle(ctx, kernel, mode):
+    rng = np.random.default_rng(32)
+    for w in (W.wall_strip(), W.box_obstacle(n=64)):
+        n = len(w.particles)
+        dg = rng.normal(size=n)
+        dgr = rng.normal(size=(n, 2))
+        ref_p, ref_t = oracle_backward2(kernel, w.H, w.particles, w.triangles, dg, dgr)
+        dt = np.float64 if mode == "fp64" else np.float32
+        dp, dtr = ctx.backward(_t(w.particles), _t(w.triangles), kernel, w.H, _t(dg.astype(dt)), mode,
+                               d_grad=_t(dgr.astype(dt)))
+        sg = scales(kernel, w.H, 0)[1]
+        s = sg * (np.abs(dg).max() + np.abs(dgr).max() / w.H)     # grad-of-grad scales as 1/H^2
+        tol = TOL_FP64 if mode == "fp64" else TOL_FP32
+        assert rel_err(dp.cpu().numpy(), ref_p, s).max() <= tol
+        assert rel_err(dtr.cpu().numpy(), ref_t, s).max() <= tol
+
+
+def test_second_order_finite_differences(ctx):
+    """L = sum_i G_i . grad gamma_i: the GPU's dL/dx and dL/dnu against central differences of
+    the oracle's grad gamma (FP64)"""
+    w = W.wall_strip()
+    parts, tris, H = w.particles.astype(np.float64), w.triangles.astype(np.float64), w.H
+    rng = np.random.default_rng(33)
+    G = rng.normal(size=(len(parts), 2))
+    dp, dtr = ctx.backward(_t(w.particles), _t(w.triangles), "cubic_spline", H,
+                           _t(np.zeros(len(parts))), "fp64", d_grad=_t(G))
+    dp, dtr = dp.cpu().numpy(), dtr.cpu().numpy()
+    off, pt = oracle.cull(w.particles, w.triangles, H)
+
+    def loss_particle(i, x):
+        tot = 0.0
+        for t in pt[off[i]:off[i + 1]]:
+            tot += G[i] @ oracle.pair("cubic_spline", H, x, tris[t])[1:3]
+        return tot
+
+    eps = 1e-6 * H
+    for i in np.flatnonzero(np.diff(off))[:6]:
+        for a in range(2):
+            xp_, xm_ = parts[i, :2].copy(), parts[i, :2].copy()
+            xp_[a] += eps
+            xm_[a] -= eps
+            fd = (loss_particle(i, xp_) - loss_particle(i, xm_)) / (2 * eps)
+            assert abs(dp[i, a] - fd) <= 1e-6 * max(1.0, abs(fd)) / H
