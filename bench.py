@@ -532,8 +532,23 @@ def run_adjoint(ctx, dev, stream, flush, steps=3):
             torch.cuda.synchronize()
             fw.append(e[0].elapsed_time(e[1]))
             bw.append(e[1].elapsed_time(e[2]))
+        # second order: L = sum (gamma - gamma*)^2 + sum |grad gamma|^2 H^2 (dL/dgrad gamma given)
+        _, gr, _ = ctx.boundary_integrals(parts, tris, "wendland_c4", w.H, -1, mode)
+        dgr = 2.0 * gr * (w.H * w.H)
+        ctx.backward(parts, tris, "wendland_c4", w.H, 2.0 * (g - gs), mode, d_grad=dgr)
+        bw2 = []
+        for _ in range(steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            ctx.backward(parts, tris, "wendland_c4", w.H, 2.0 * (g - gs), mode, d_grad=dgr)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            bw2.append(e[0].elapsed_time(e[1]))
         out[mode] = {"pairs": P, "forward_ms": float(np.mean(fw)), "backward_ms": float(np.mean(bw)),
-                     "backward_pairs_per_s": P / (np.mean(bw) / 1e3)}
+                     "backward_pairs_per_s": P / (np.mean(bw) / 1e3),
+                     "backward_second_order_ms": float(np.mean(bw2)),
+                     "backward_second_order_pairs_per_s": P / (np.mean(bw2) / 1e3)}
     return out
 
 
