@@ -398,6 +398,9 @@ def run_ours(args):
     gamma_grad_only = {"per_kernel_ms": gg, "value": P * len(KERNELS) / (sum(gg.values()) / 1e3),
                        "unit": UNIT, "note": "integral launches only (culling excluded), no moments"}
 
+    # ---- hybrid FP32 mode (quadrature for triangles well inside the support), same step
+    hybrid = run_hybrid(ctx, parts, tris, w, stream, flush, P, step, timed)
+
     # ---- piecewise-linear boundary fields (two fields, Wendland C4) over the same pair list
     fields = run_fields(ctx, parts, tris, w, stream, flush, P)
 
@@ -461,6 +464,7 @@ def run_ours(args):
         "case_histogram": case_hist,
         "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
         "gamma_grad_only": gamma_grad_only,
+        "hybrid": hybrid,
         "fields": fields,
         "adjoint": adjoint,
         "surrogate": surrogate,
@@ -469,6 +473,41 @@ def run_ours(args):
         "measured_peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_hybrid(ctx, parts, tris, w, stream, flush, P, step, timed, reps=3):
+    """The benchmark step in SPH2D_FP32_HYBRID mode: per-kernel times, pairs/s, the share of
+    pairs left to the closed form and the error against the FP64 GPU path."""
+    import torch
+    from tests.helpers import rel_err, scales
+    ms, kms, _, _ = timed("fp32_hybrid", reps, 1, per_kernel=True)
+    kmeans = [float(np.mean(x)) for x in kms[1:]]
+    fb = ctx.stats()["n_fallback"]
+    oh = step("fp32_hybrid")
+    o64 = step("fp64")
+    err = {}
+    for k, a, b in zip(KERNELS, oh, o64):
+        got = torch.cat([a[0][:, None], a[1], a[2]], 1).double().cpu().numpy()
+        ref = torch.cat([b[0][:, None], b[1], b[2]], 1).cpu().numpy()
+        err[k] = float(rel_err(got, ref, scales(k, w.H, 10)).max())
+    del oh, o64
+    gg = {}
+    for k in KERNELS:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        ctx.integrals_from_pairs(k, -1, "fp32_hybrid")
+        for a_, b_ in ev:
+            flush.zero_()
+            a_.record(stream)
+            ctx.integrals_from_pairs(k, -1, "fp32_hybrid")
+            b_.record(stream)
+        torch.cuda.synchronize()
+        gg[k] = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+    return {"value": P * len(KERNELS) / (float(np.mean(ms)) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+            "per_kernel_ms": dict(zip(KERNELS, kmeans)), "closed_form_share": fb / max(P, 1),
+            "max_rel_err_vs_fp64_path": err,
+            "gamma_grad_only": {"per_kernel_ms": gg, "value": P * len(KERNELS) / (sum(gg.values()) / 1e3)},
+            "note": "same step as the headline (cull + 3 kernels, moments to degree 3); quadrature for "
+                    "triangles inside the support and >= half their longest edge from the particle"}
 
 
 def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):

@@ -22,7 +22,7 @@ STATUS = {
     7: "SPH2D_ERR_OUT_OF_MEMORY",
 }
 KERNELS = {"wendland_c2": 0, "wendland_c4": 1, "wendland_c6": 2, "cubic_spline": 3}
-MODES = {"fp64": 0, "fp32_fixup": 1, "surrogate": 2}
+MODES = {"fp64": 0, "fp32_fixup": 1, "surrogate": 2, "fp32_hybrid": 3}
 
 # every symbol the header declares, with (restype, argtypes)
 _P = ctypes.c_void_p

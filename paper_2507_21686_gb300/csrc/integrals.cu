@@ -7,6 +7,7 @@ namespace sph2d {
 
 sph2d_status integrals_fp64(Ctx* c, int kernel, int md, const IntArgs& a);
 sph2d_status integrals_fp32(Ctx* c, int kernel, int md, const IntArgs& a);
+sph2d_status integrals_hybrid(Ctx* c, int kernel, int md, const IntArgs& a);
 sph2d_status pairs_fp64(Ctx* c, const double* pairs, int64_t P, int kernel, double H, int deg,
                         unsigned long long* nfix, void* out);
 sph2d_status pairs_fp32(Ctx* c, const double* pairs, int64_t P, int kernel, double H, int deg,
@@ -37,7 +38,9 @@ sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, v
   cudaError_t e = cudaMemsetAsync(a.nfix, 0, sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   const int md = md_for(moment_degree);
-  s = mode == SPH2D_FP64 ? integrals_fp64(c, kernel, md, a) : integrals_fp32(c, kernel, md, a);
+  s = mode == SPH2D_FP64 ? integrals_fp64(c, kernel, md, a)
+                         : (mode == SPH2D_FP32_HYBRID ? integrals_hybrid(c, kernel, md, a)
+                                                      : integrals_fp32(c, kernel, md, a));
   if (s != SPH2D_OK) return s;
   e = cudaMemcpyAsync(c->pinned + 8, a.nfix, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                       c->stream);
@@ -45,7 +48,7 @@ sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, v
   c->stats.n_pairs = cl.P;
   c->stats.n_fallback = 0;
   c->fixup_pending = true;
-  c->fallback_pending = false;
+  c->fallback_pending = mode == SPH2D_FP32_HYBRID;   // pinned[10]: pairs left to the closed form
   return SPH2D_OK;
 }
 

@@ -258,7 +258,7 @@ static sph2d_status check_outputs(Ctx* c, int kernel, int moment_degree, int mod
     if (!c->sur_ready) return set_err(c, SPH2D_ERR_NOT_BUILT, "surrogate not initialised");
     if (kernel != c->sur_kernel)
       return set_err(c, SPH2D_ERR_INVALID_ARG, "the surrogate was initialised for another kernel");
-  } else if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP) {
+  } else if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP && mode != SPH2D_FP32_HYBRID) {
     return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown mode");
   }
   if (N > 0 && !gamma) return set_err(c, SPH2D_ERR_INVALID_ARG, "gamma must not be NULL");
@@ -351,6 +351,8 @@ sph2d_status sph2d_pair_integrals(sph2d_ctx* h, const double* pairs, int64_t P, 
     return set_err(c, SPH2D_ERR_INVALID_ARG, "moment_degree must be -1..3");
   if (mode == SPH2D_SURROGATE)
     return set_err(c, SPH2D_ERR_UNSUPPORTED, "independent pairs go through sph2d_surrogate_pairs");
+  if (mode == SPH2D_FP32_HYBRID)
+    return set_err(c, SPH2D_ERR_UNSUPPORTED, "the hybrid mode runs over a culled pair list only");
   if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
     return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown mode");
   if (reinterpret_cast<uintptr_t>(pairs) & 7u)
@@ -371,7 +373,8 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* h, const float* partic
   if (s != SPH2D_OK) return s;
   if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
   if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
-    return set_err(c, mode == SPH2D_SURROGATE ? SPH2D_ERR_UNSUPPORTED : SPH2D_ERR_INVALID_ARG,
+    return set_err(c, (mode == SPH2D_SURROGATE || mode == SPH2D_FP32_HYBRID) ? SPH2D_ERR_UNSUPPORTED
+                                                                            : SPH2D_ERR_INVALID_ARG,
                    "backward supports SPH2D_FP64 and SPH2D_FP32_FIXUP");
   if ((N > 0 && (!d_gamma || !d_particles)) || (M > 0 && !d_tris))
     return set_err(c, SPH2D_ERR_INVALID_ARG, "null gradient pointer");
@@ -389,7 +392,8 @@ sph2d_status sph2d_field_integrals(sph2d_ctx* h, int kernel, int mode, const flo
   if (!c->cells.built) return set_err(c, SPH2D_ERR_NOT_BUILT, "no pair list built");
   if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
   if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
-    return set_err(c, mode == SPH2D_SURROGATE ? SPH2D_ERR_UNSUPPORTED : SPH2D_ERR_INVALID_ARG,
+    return set_err(c, (mode == SPH2D_SURROGATE || mode == SPH2D_FP32_HYBRID) ? SPH2D_ERR_UNSUPPORTED
+                                                                            : SPH2D_ERR_INVALID_ARG,
                    "field integrals support SPH2D_FP64 and SPH2D_FP32_FIXUP");
   if (nf < 1 || nf > SPH2D_MAX_FIELDS) return set_err(c, SPH2D_ERR_INVALID_ARG, "nf must be 1..SPH2D_MAX_FIELDS");
   if ((c->cells.M > 0 && !vertex_values) || (c->cells.N > 0 && !value))

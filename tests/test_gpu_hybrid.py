@@ -1,0 +1,80 @@
+"""Hybrid FP32 mode (quadrature for triangles well inside the support, closed form otherwise)
+through the C-ABI against the FP64 oracle, within the FP32 tolerance for every output."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_21686_gb300 import workloads as W
+from tests.helpers import TOL_FP32, rel_err, scales
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["wendland_c2", "wendland_c4", "wendland_c6", "cubic_spline"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2507_21686_gb300 import build
+    build.build()
+    from paper_2507_21686_gb300.api import Context
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def check(ctx, w, kernel, deg, sample, seed=5):
+    g, gr, mo = ctx.boundary_integrals(_t(w.particles), _t(w.triangles), kernel, w.H, deg, "fp32_hybrid")
+    st = ctx.stats()
+    g, gr = g.double().cpu().numpy(), gr.double().cpu().numpy()
+    mo = mo.double().cpu().numpy() if mo is not None else np.zeros((len(g), 0))
+    idx = np.random.default_rng(seed).choice(len(w.particles), sample, replace=False)
+    sub = w.particles[idx]
+    off, pt = oracle.cull(sub, w.triangles, w.H)
+    og, ogr, omo, fl = oracle.particle_sums(kernel, w.H, sub, w.triangles, off, pt, deg)
+    assert fl.sum() == 0
+    got = np.concatenate([g[idx, None], gr[idx], mo[idx]], axis=1)
+    ref = np.concatenate([og[:, None], ogr, omo], axis=1)
+    err = rel_err(got, ref, scales(kernel, w.H, mo.shape[1]))
+    return err.max(), st
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("deg", [-1, 1, 3])
+def test_hybrid_box_vs_oracle(ctx, kernel, deg):
+    w = W.box_obstacle(2, 128, 32)
+    err, st = check(ctx, w, kernel, deg, 300)
+    assert err <= TOL_FP32, err
+    # a real share of the pairs took the quadrature (the rest the closed form)
+    assert 0 < st["n_fallback"] < 0.9 * st["n_pairs"]
+
+
+def test_hybrid_full_size_sampled(ctx):
+    w = W.box_obstacle()
+    err, st = check(ctx, w, "wendland_c4", 3, 150)
+    assert err <= TOL_FP32, err
+    print(f"\nhybrid C4 full size: closed form for {st['n_fallback'] / st['n_pairs']:.3f} of {st['n_pairs']} pairs")
+
+
+def test_hybrid_deterministic_and_unsupported_paths(ctx):
+    import torch
+    from paper_2507_21686_gb300._lib import Sph2dError
+    w = W.wall_strip()
+    a = ctx.boundary_integrals(_t(w.particles), _t(w.triangles), "wendland_c2", w.H, 3, "fp32_hybrid")
+    b = ctx.boundary_integrals(_t(w.particles), _t(w.triangles), "wendland_c2", w.H, 3, "fp32_hybrid")
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
+    pairs = np.zeros((4, 8))
+    pairs[:, 2:] = [0.1, 0.1, 0.3, 0.1, 0.2, 0.3]
+    with pytest.raises(Sph2dError, match="UNSUPPORTED"):
+        ctx.pair_integrals(_t(pairs), "wendland_c2", 1.0, -1, "fp32_hybrid")
+    with pytest.raises(Sph2dError, match="UNSUPPORTED"):
+        ctx.backward(_t(w.particles), _t(w.triangles), "wendland_c2", w.H,
+                     torch.zeros(len(w.particles), device="cuda"), "fp32_hybrid")
