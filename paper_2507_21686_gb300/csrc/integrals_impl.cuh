@@ -398,92 +398,115 @@ __device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double
   }
 }
 
+// first piece of pair q into vals[q]; need: the pair lies within H/2 (second piece pending);
+// returns 1 when an FP32 pair took the FP64 fix-up (both pieces done there)
 template <typename OT, int MD>
-__global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArgs a, OT* __restrict__ vals,
-                                                          int64_t* __restrict__ list,
-                                                          unsigned long long* __restrict__ count) {
+__device__ __forceinline__ int cubic_first_pair(const IntArgs& a, int64_t q, OT* __restrict__ vals, bool& need) {
   constexpr int NV = nv_of(MD);
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  unsigned long long fixes = 0;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < a.P; base += stride) {
-    const int64_t q = base + lane;
-    bool need = false;
-    int fix = 0;
-    if (q < a.P) {
-      const int pid = __ldg(a.pair_pid + q);
-      const float4 p = a.parts[pid];
-      const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-      OT v[NV];
-      bool done = false;
-      if (sizeof(OT) == sizeof(float)) {
-        const float ih = float(a.invH);
-        float lf[6];
-        bool ok = true;
+  const int pid = __ldg(a.pair_pid + q);
+  const float4 p = a.parts[pid];
+  const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
+  OT v[NV];
+  int fix = 0;
+  bool done = false;
+  need = false;
+  if (sizeof(OT) == sizeof(float)) {
+    const float ih = float(a.invH);
+    float lf[6];
+    bool ok = true;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
-          lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
-          ok = ok && fabsf(lf[2 * j]) <= kFixupCoordLimit && fabsf(lf[2 * j + 1]) <= kFixupCoordLimit;
-        }
-        if (ok) {
-          const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
-          float w[13];
-          if (s == 0) {
+    for (int j = 0; j < 3; ++j) {
+      lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+      lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+      ok = ok && fabsf(lf[2 * j]) <= kFixupCoordLimit && fabsf(lf[2 * j + 1]) <= kFixupCoordLimit;
+    }
+    if (ok) {
+      const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
+      float w[13];
+      if (s == 0) {
 #pragma unroll
-            for (int i = 0; i < NV; ++i) w[i] = 0.0f;
-          } else {
-            cubic_piece<float, MD>(lf, 0, s, a.C, a.invH, w);
-            need = near_half<float>(lf);
-          }
-#pragma unroll
-          for (int i = 0; i < NV; ++i) ok = ok && isfinite(w[i]);
-          if (ok) {
-#pragma unroll
-            for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
-            done = true;
-          }
-        }
+        for (int i = 0; i < NV; ++i) w[i] = 0.0f;
+      } else {
+        cubic_piece<float, MD>(lf, 0, s, a.C, a.invH, w);
+        need = near_half<float>(lf);
       }
-      if (!done) {
-        double ld[6], w[13];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-          ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-        }
-        if (sizeof(OT) == sizeof(double)) {
-          const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-          if (s == 0) {
-#pragma unroll
-            for (int i = 0; i < NV; ++i) w[i] = 0.0;
-            need = false;
-          } else {
-            cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
-            need = near_half<double>(ld);
-          }
-        } else {
-          // FP64 fix-up of an FP32 pair: both pieces here, nothing left for the list
-          eval_local<double, KID_CUBIC, MD>(ld, a.C, a.invH, w);
-          need = false;
-          fix = 1;
-        }
+      for (int i = 0; i < NV; ++i) ok = ok && isfinite(w[i]);
+      if (ok) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
+        done = true;
       }
-      OT* out = vals + q * NV;
+    }
+  }
+  if (!done) {
+    double ld[6], w[13];
 #pragma unroll
-      for (int i = 0; i < NV; ++i) out[i] = v[i];
+    for (int j = 0; j < 3; ++j) {
+      ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+      ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+    }
+    if (sizeof(OT) == sizeof(double)) {
+      const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+      if (s == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) w[i] = 0.0;
+        need = false;
+      } else {
+        cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
+        need = near_half<double>(ld);
+      }
+    } else {
+      // FP64 fix-up of an FP32 pair: both pieces here, nothing left for the list
+      eval_local<double, KID_CUBIC, MD>(ld, a.C, a.invH, w);
+      need = false;
+      fix = 1;
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
+  }
+  OT* out = vals + q * NV;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = v[i];
+  return fix;
+}
+
+// warp-aggregated append of the lanes with flag set to list (count: its length)
+__device__ __forceinline__ void warp_append(bool flag, int64_t q, int64_t* __restrict__ list,
+                                            unsigned long long* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (m) {
+    unsigned long long b = 0;
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) b = atomicAdd(count, (unsigned long long)__popc(m));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = q;
+  }
+}
+
+// first piece of every pair (src == nullptr) or of the pairs src lists (src_count entries)
+template <typename OT, int MD>
+__global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArgs a, OT* __restrict__ vals,
+                                                          const int64_t* __restrict__ src,
+                                                          const unsigned long long* __restrict__ src_count,
+                                                          int64_t* __restrict__ list,
+                                                          unsigned long long* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t n = src ? int64_t(*src_count) : a.P;
+  unsigned long long fixes = 0;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
+    const int64_t i = base + lane;
+    bool need = false;
+    int fix = 0;
+    int64_t q = 0;
+    if (i < n) {
+      q = src ? src[i] : i;
+      fix = cubic_first_pair<OT, MD>(a, q, vals, need);
     }
     fixes += __popc(__ballot_sync(0xffffffffu, fix));
-    const unsigned m = __ballot_sync(0xffffffffu, need);
-    if (m) {
-      unsigned long long b = 0;
-      const int leader = __ffs(m) - 1;
-      if (lane == leader) b = atomicAdd(count, (unsigned long long)__popc(m));
-      b = __shfl_sync(0xffffffffu, b, leader);
-      if (need) list[b + __popc(m & ((1u << lane) - 1u))] = q;
-    }
+    warp_append(need, q, list, count);
   }
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
@@ -678,7 +701,7 @@ static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   if (a.P > 0) {
     const int64_t blocks = (a.P + 127) / 128;
     SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MD>), resident_blocks(c, cubic_first_kernel<OT, MD>, blocks), 128,
-                 a, vals, list, count);
+                 a, vals, nullptr, nullptr, list, count);
     SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MD>), resident_blocks(c, cubic_second_kernel<OT, MD>, blocks), 128,
                  a, vals, list, count);
     SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MD>), resident_blocks(c, reduce_pairs_kernel<OT, MD>, (nchunks + 3) / 4),

@@ -1,5 +1,6 @@
-"""Hybrid FP32 mode (quadrature for triangles well inside the support, closed form otherwise)
-through the C-ABI against the FP64 oracle, within the FP32 tolerance for every output."""
+"""Hybrid FP32 mode (quadrature for triangles away from the particle, inside the support or
+small and across its edge; closed form otherwise) through the C-ABI against the FP64 oracle,
+within the FP32 tolerance for every output."""
 from __future__ import annotations
 
 import numpy as np
@@ -55,6 +56,30 @@ def test_hybrid_box_vs_oracle(ctx, kernel, deg):
     assert err <= TOL_FP32, err
     # a real share of the pairs took the quadrature (the rest the closed form)
     assert 0 < st["n_fallback"] < 0.9 * st["n_pairs"]
+
+
+def triangle_soup(seed, n=24, count=2500, lo=0.05, hi=1.2):
+    """jittered n x n particles in [0,1]^2 (H = 2.5/n) under overlapping generic triangles of
+    longest edge ~ logU[lo, hi] H with centroids over [-H, 1+H]^2: every size class across
+    the support edge, on both sides of each kernel's size limit for quadrature there"""
+    rng = np.random.default_rng(seed)
+    H = 2.5 / n
+    parts = W.jittered_lattice(n, 1.0 / n, 0.25, rng)
+    c = rng.uniform(-H, 1.0 + H, size=(count, 2))
+    s = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)) * H * 0.5
+    ang = rng.uniform(0, 2 * np.pi, size=(count, 1)) + np.array([0.0, 2.1, 4.2]) + rng.uniform(-0.5, 0.5, (count, 3))
+    rad = s[:, None] * rng.uniform(0.6, 1.0, size=(count, 3))
+    v = np.stack([c[:, None, 0] + rad * np.cos(ang), c[:, None, 1] + rad * np.sin(ang)], axis=-1)
+    tris = v.reshape(count, 6).astype(np.float32)
+    return W.Workload(f"triangle_soup_{n * n}_x_{count}", H, KERNELS, 3, parts, tris)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_hybrid_mixed_sizes_vs_oracle(ctx, kernel):
+    w = triangle_soup(11)
+    err, st = check(ctx, w, kernel, 3, 200)
+    assert err <= TOL_FP32, err
+    assert 0.05 * st["n_pairs"] < st["n_fallback"] < 0.95 * st["n_pairs"]
 
 
 def test_hybrid_full_size_sampled(ctx):
