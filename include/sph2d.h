@@ -83,18 +83,21 @@ typedef enum {
   SPH2D_FP32_FIXUP = 1,  /* FP32 arithmetic; pairs whose error bound exceeds the budget are
                             recomputed in FP64 (count reported by sph2d_last_stats) */
   SPH2D_SURROGATE = 2,   /* learned surrogate with guarded analytic fallback (gamma, grad only) */
-  SPH2D_FP32_HYBRID = 3  /* FP32 with quadrature for triangles well inside the support (below) */
+  SPH2D_FP32_HYBRID = 3  /* FP32 with quadrature for triangles away from the particle (below) */
 } sph2d_mode;
 
 typedef struct sph2d_ctx sph2d_ctx;
 
-/* SPH2D_FP32_HYBRID (the extension Sec. 6.1 suggests): a pair whose triangle lies inside the
- * support (every vertex within H of the particle) and at least half its longest edge away from
- * it -- for the cubic spline also entirely inside or entirely beyond H/2 -- is integrated by a
- * 36-point conical-product Gauss-Legendre rule in FP32 (measured error <= 5e-6 of the output
- * scales for every output, moments included, against 1e-5 for SPH2D_FP32_FIXUP); every other
- * pair takes the SPH2D_FP32_FIXUP closed form.  Float outputs; n_fallback counts the pairs left
- * to the closed form.  Per-particle paths only (not sph2d_pair_integrals, the adjoint or the
+/* SPH2D_FP32_HYBRID (the extension Sec. 6.1 suggests): a pair whose triangle lies at least
+ * half its longest edge away from the particle, and either inside the support (every vertex
+ * within H) or across its edge with one vertex inside and a longest edge below a per-kernel
+ * size (Wendland C2 0.6 H, C4 0.75 H, C6 0.7 H, cubic spline 0.45 H), is integrated in FP32
+ * by a 36-point conical-product Gauss-Legendre rule whose rays stop at the support circle
+ * (measured error <= 1.5e-6 of the output scales per pair for every output, moments
+ * included, against 1e-5 for SPH2D_FP32_FIXUP); the cubic spline's second piece (support
+ * H/2) joins the quadrature inside H/2 and otherwise takes its closed form.  Every other pair
+ * takes the SPH2D_FP32_FIXUP closed form.  Float outputs; n_fallback counts the pairs left to
+ * the closed form.  Per-particle paths only (not sph2d_pair_integrals, the adjoint or the
  * field integrals: UNSUPPORTED). */
 
 /* Statistics of the most recent integral call on a context. */
