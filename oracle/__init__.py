@@ -8,7 +8,9 @@ quadrature, in ``sph2d_oracle.c``; this module only builds and marshals.
 
 ``pair_field`` / ``pairs_field`` / ``particle_field_sums``: piecewise-linear boundary fields
 (Sec. 3, Eq. singleSpherical and basicdiff) by polar quadrature of the barycentric field times
-W and grad W.
+W and grad W.  ``pair_field_p`` / ``pairs_field_p`` / ``particle_field_sums_p``: Lagrange
+fields of order 1-3 from node values (``field_nodes`` gives the node positions), by the same
+quadrature with the field evaluated from its nodal basis.
 
 Outputs of ``pairs`` (per pair, 16 doubles):
   0 gamma | 1,2 grad gamma (divergence theorem) | 3,4 grad gamma (polar route, k')
@@ -69,6 +71,9 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.orc_grad_jacobian.argtypes = [Ci, D, P, P, P]
     lib.orc_pairs_grad_jacobian.argtypes = [Ci, D, P, I64, P]
     lib.orc_pairs_field.argtypes = [Ci, D, P, P, I64, P]
+    lib.orc_pair_field_p.argtypes = [Ci, D, P, P, Ci, P, P]
+    lib.orc_pairs_field_p.argtypes = [Ci, D, P, Ci, P, I64, P]
+    lib.orc_field_nodes.argtypes = [P, Ci, P]
     lib.orc_kernel_C.argtypes = [Ci]
     lib.orc_kernel_C.restype = D
     lib.orc_kernel_k.argtypes = [Ci, D]
@@ -78,7 +83,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
     lib.orc_gauss_legendre.argtypes = [Ci, P, P]
     for f in ("orc_pair", "orc_vertex_grad", "orc_cull", "orc_particle_sums", "orc_pairs",
               "orc_pairs_vertex_grad", "orc_num_threads", "orc_version", "orc_pair_field",
-              "orc_pairs_field", "orc_grad_jacobian", "orc_pairs_grad_jacobian"):
+              "orc_pairs_field", "orc_grad_jacobian", "orc_pairs_grad_jacobian", "orc_pair_field_p",
+              "orc_pairs_field_p", "orc_field_nodes"):
         getattr(lib, f).restype = ctypes.c_int if f != "orc_kernel_C" else D
     _libs[mutant] = lib
     return lib
@@ -174,6 +180,75 @@ def pairs_field(kernel, H: float, pairs_arr: np.ndarray, values: np.ndarray, mut
     if rc != 0:
         raise ValueError("oracle: bad arguments")
     return out
+
+
+def nodes_per_triangle(order: int) -> int:
+    return (order + 1) * (order + 2) // 2
+
+
+def field_nodes(triangles: np.ndarray, order: int) -> np.ndarray:
+    """World positions of the order-k Lagrange nodes of each triangle: [M, nn, 2]."""
+    tris = np.ascontiguousarray(triangles, dtype=np.float64).reshape(-1, 6)
+    nn = nodes_per_triangle(order)
+    out = np.zeros((len(tris), nn, 2))
+    lib = _lib()
+    for m in range(len(tris)):
+        row = np.ascontiguousarray(tris[m])
+        buf = np.zeros(2 * nn)
+        if lib.orc_field_nodes(_ptr(row), int(order), _ptr(buf)) != 0:
+            raise ValueError("oracle: bad order")
+        out[m] = buf.reshape(nn, 2)
+    return out
+
+
+def pair_field_p(kernel, H: float, xp, tri, order: int, values, mutant: int = 0) -> np.ndarray:
+    """Lagrange field of order 1-3 on one triangle (node values [nn]) -> [<A>, <grad A>]."""
+    xp = np.ascontiguousarray(xp, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.float64).reshape(6)
+    a = np.ascontiguousarray(values, dtype=np.float64).reshape(nodes_per_triangle(order))
+    out = np.zeros(3)
+    rc = _lib(mutant).orc_pair_field_p(_kid(kernel), float(H), _ptr(xp), _ptr(tri), int(order), _ptr(a), _ptr(out))
+    if rc < 0:
+        raise ValueError("oracle: bad arguments")
+    return out
+
+
+def pairs_field_p(kernel, H: float, pairs_arr: np.ndarray, order: int, values: np.ndarray,
+                  mutant: int = 0) -> np.ndarray:
+    """Many pairs [P, 8] with node values [P, nn] -> [P, 3] (<A>, <grad A>)."""
+    p = np.ascontiguousarray(pairs_arr, dtype=np.float64).reshape(-1, 8)
+    a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1, nodes_per_triangle(order))
+    out = np.zeros((len(p), 3))
+    rc = _lib(mutant).orc_pairs_field_p(_kid(kernel), float(H), _ptr(p), int(order), _ptr(a), len(p), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle: bad arguments")
+    return out
+
+
+def particle_field_sums_p(kernel, H: float, particles: np.ndarray, triangles: np.ndarray, off, pair_tri,
+                          order: int, node_values: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Per-particle sums of Lagrange fields of order 1-3: node_values [M, nn, nf] ->
+    value [N, nf], grad [N, nf, 2]."""
+    parts = np.asarray(particles, dtype=np.float32)
+    tris = np.asarray(triangles, dtype=np.float32).reshape(-1, 6)
+    nv = np.asarray(node_values, dtype=np.float32)
+    if nv.ndim == 2:
+        nv = nv[:, :, None]
+    nf = nv.shape[2]
+    off = np.asarray(off, dtype=np.int64)
+    pt = np.asarray(pair_tri, dtype=np.int64)
+    pid = np.repeat(np.arange(len(parts)), np.diff(off))
+    pr = np.zeros((len(pt), 8))
+    pr[:, :2] = parts[pid, :2]
+    pr[:, 2:] = tris[pt]
+    val = np.zeros((len(parts), nf))
+    grad = np.zeros((len(parts), nf, 2))
+    for f in range(nf):
+        r = pairs_field_p(kernel, H, pr, order, nv[pt, :, f].astype(np.float64))
+        np.add.at(val[:, f], pid, r[:, 0])
+        np.add.at(grad[:, f, 0], pid, r[:, 1])
+        np.add.at(grad[:, f, 1], pid, r[:, 2])
+    return val, grad
 
 
 def particle_field_sums(kernel, H: float, particles: np.ndarray, triangles: np.ndarray, off, pair_tri,

@@ -416,6 +416,87 @@ static void field_fn(const void* ctx, double th, double* f) {
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Lagrange (P1, P2, P3) boundary fields over the triangle (Sec. 3 interpolates a field     */
+/* linearly; the paper's introduction names higher-order element fields as the extension).  */
+/* Nodes: the principal lattice {(i, j, l)/k : i + j + l = k} in barycentric coordinates,   */
+/* ordered vertices 0, 1, 2; then each edge (0,1), (1,2), (2,0) from its first vertex to    */
+/* its second; then the interior node (P3: the centroid).  The basis function of the node   */
+/* with indices (i, j, l) is Silvester's product R_i(k lambda_0) R_j(k lambda_1)            */
+/* R_l(k lambda_2), R_n(z) = prod_{s<n} (z - s)/(s + 1): 1 at its node, 0 at the others.    */
+/* ------------------------------------------------------------------------------------ */
+static const int NODES_P1[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+static const int NODES_P2[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {0, 1, 1}, {1, 0, 1}};
+#if ORC_MUTANT == 6
+/* the two nodes of edge (0,1) swapped */
+static const int NODES_P3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {1, 2, 0}, {2, 1, 0},
+                                    {0, 2, 1}, {0, 1, 2}, {1, 0, 2}, {2, 0, 1}, {1, 1, 1}};
+#else
+static const int NODES_P3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {1, 2, 0},
+                                    {0, 2, 1}, {0, 1, 2}, {1, 0, 2}, {2, 0, 1}, {1, 1, 1}};
+#endif
+
+static double silvester_r(int n, double z) {
+  double v = 1.0;
+  for (int s = 0; s < n; ++s) v *= (z - s) / (s + 1);
+  return v;
+}
+
+typedef struct {
+  int kid, order, nn;
+  const tri_t* t;
+  const int (*nodes)[3];
+  double A[10];
+  double l0x, l0y, l0c, l1x, l1y, l1c;   /* lambda_0, lambda_1 as affine functions of p */
+} nfield_ctx;
+
+/* the field at local point (x, y) */
+static double nfield_eval(const nfield_ctx* fc, double x, double y) {
+  double lam[3];
+  lam[0] = fc->l0c + fc->l0x * x + fc->l0y * y;
+  lam[1] = fc->l1c + fc->l1x * x + fc->l1y * y;
+  lam[2] = 1.0 - lam[0] - lam[1];
+  double v = 0.0;
+  for (int n = 0; n < fc->nn; ++n) {
+    double phi = 1.0;
+    for (int m = 0; m < 3; ++m) phi *= silvester_r(fc->nodes[n][m], fc->order * lam[m]);
+    v += fc->A[n] * phi;
+  }
+  return v;
+}
+
+/* along the ray of direction u, clipped to the triangle and the support:
+ *   f[0] = int A(r u) k(r) r dr,  f[1..2] = u int A(r u) k'(r) r dr
+ * by Gauss-Legendre on each kernel piece (exact: a polynomial in r there) */
+static void nfield_radial_piece(const nfield_ctx* fc, double ux, double uy, double r0, double r1, double* f) {
+  double h = 0.5 * (r1 - r0), c = 0.5 * (r1 + r0);
+  for (int i = 0; i < GL_RAD; ++i) {
+    double r = c + h * glr_x[i], w = h * glr_w[i];
+    double a = nfield_eval(fc, r * ux, r * uy);
+    f[0] += w * a * orc_kernel_k(fc->kid, r) * r;
+    f[1] += w * a * orc_kernel_dk(fc->kid, r) * r;
+  }
+}
+
+static void nfield_fn(const void* ctx, double th, double* f) {
+  const nfield_ctx* fc = (const nfield_ctx*)ctx;
+  f[0] = f[1] = f[2] = 0.0;
+  double ux = cos(th), uy = sin(th), r0, r1;
+  if (!ray_clip(fc->t, ux, uy, &r0, &r1)) return;
+  if (r1 > 1.0) r1 = 1.0;
+  if (!(r1 > r0)) return;
+  double g[2] = {0.0, 0.0};
+  if (fc->kid == K_CUBIC && r0 < 0.5 && r1 > 0.5) {
+    nfield_radial_piece(fc, ux, uy, r0, 0.5, g);
+    nfield_radial_piece(fc, ux, uy, 0.5, r1, g);
+  } else {
+    nfield_radial_piece(fc, ux, uy, r0, r1, g);
+  }
+  f[0] = g[0];
+  f[1] = g[1] * ux;
+  f[2] = g[1] * uy;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* edge line integrals: int_0^1 k(|A + s(B-A)|) {1, s} L ds                              */
 /* ------------------------------------------------------------------------------------ */
 typedef struct { int kid; double ax, ay, ex, ey, L; } edge_ctx;
@@ -778,6 +859,73 @@ int orc_pairs_vertex_grad(int kid, double H, const double* pairs, int64_t P, dou
   gl_init();
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t q = 0; q < P; ++q) orc_vertex_grad(kid, H, pairs + 8 * q, pairs + 8 * q + 2, out + 6 * q);
+  return 0;
+}
+
+/* Lagrange field of order k (1..3) on one triangle: node values A[(k+1)(k+2)/2] in the
+ * node order above, the caller's vertex order.
+ *   out[0] = int_T A(x') W(x - x') dx',  out[1..2] = int_T A(x') grad_x W(x - x') dx'
+ * by polar quadrature of the field (evaluated from its nodal basis) times the kernel. */
+int orc_pair_field_p(int kid, double H, const double* xp, const double* tri, int order, const double* A,
+                     double* out) {
+  if (!kernel_ok(kid) || !(H > 0.0) || order < 1 || order > 3) return -1;
+  gl_init();
+  out[0] = out[1] = out[2] = 0.0;
+  double p[6];
+  for (int j = 0; j < 3; ++j) {
+    p[2 * j] = (tri[2 * j] - xp[0]) / H;
+    p[2 * j + 1] = (tri[2 * j + 1] - xp[1]) / H;
+  }
+  tri_t t;
+  if (tri_setup(p, &t) == 0) return 0;
+  /* barycentric coordinates of the caller's vertices (Sec. 3), as in orc_pair_field */
+  double x0 = p[0], y0 = p[1], x1 = p[2], y1 = p[3], x2 = p[4], y2 = p[5];
+  double D = (y1 - y2) * (x0 - x2) + (x2 - x1) * (y0 - y2);
+  nfield_ctx fc;
+  fc.kid = kid;
+  fc.order = order;
+  fc.nn = (order + 1) * (order + 2) / 2;
+  fc.t = &t;
+  fc.nodes = order == 1 ? NODES_P1 : (order == 2 ? NODES_P2 : NODES_P3);
+  for (int n = 0; n < fc.nn; ++n) fc.A[n] = A[n];
+  fc.l0x = (y1 - y2) / D;
+  fc.l0y = (x2 - x1) / D;
+  fc.l0c = -(fc.l0x * x2 + fc.l0y * y2);
+  fc.l1x = (y2 - y0) / D;
+  fc.l1y = (x0 - x2) / D;
+  fc.l1c = -(fc.l1x * x2 + fc.l1y * y2);
+  quad_stats st = {0, 0};
+  double q[3];
+  polar_integrate(kid, &t, nfield_fn, &fc, 3, q, &st);
+  double C = orc_kernel_C(kid);
+  out[0] = C * q[0];
+  out[1] = -(C / H) * q[1];
+  out[2] = -(C / H) * q[2];
+  return st.max_depth_hit ? 1 : 0;
+}
+
+/* world positions of the order-k nodes of one triangle -> xy[2 nn] */
+int orc_field_nodes(const double* tri, int order, double* xy) {
+  if (order < 1 || order > 3) return -1;
+  const int (*nodes)[3] = order == 1 ? NODES_P1 : (order == 2 ? NODES_P2 : NODES_P3);
+  int nn = (order + 1) * (order + 2) / 2;
+  for (int n = 0; n < nn; ++n) {
+    xy[2 * n] = xy[2 * n + 1] = 0.0;
+    for (int m = 0; m < 3; ++m) {
+      xy[2 * n] += tri[2 * m] * nodes[n][m] / (double)order;
+      xy[2 * n + 1] += tri[2 * m + 1] * nodes[n][m] / (double)order;
+    }
+  }
+  return 0;
+}
+
+int orc_pairs_field_p(int kid, double H, const double* pairs, int order, const double* A, int64_t P,
+                      double* out) {
+  if (!kernel_ok(kid) || !(H > 0.0) || order < 1 || order > 3) return -1;
+  gl_init();
+  const int nn = (order + 1) * (order + 2) / 2;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < P; ++q) orc_pair_field_p(kid, H, pairs + 8 * q, pairs + 8 * q + 2, order, A + nn * q, out + 3 * q);
   return 0;
 }
 
