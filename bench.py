@@ -403,6 +403,7 @@ def run_ours(args):
 
     # ---- piecewise-linear boundary fields (two fields, Wendland C4) over the same pair list
     fields = run_fields(ctx, parts, tris, w, stream, flush, P)
+    fields["lagrange"] = run_fields_p(ctx, parts, tris, w, stream, flush, P)
 
     # ---- adjoint workload: 262,144 particles x 51,712 triangles, Wendland C4
     adjoint = run_adjoint(ctx, dev, stream, flush)
@@ -542,6 +543,47 @@ def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):
         "value": float(((a32.double() - a64).abs() / torch.clamp(a64.abs(), min=sa)).max()),
         "grad": float(((g32.double() - g64).abs() / torch.clamp(g64.abs(), min=sa * sg)).max())}
     res["speedup_fp32_vs_fp64"] = res["fp64"]["ms"] / res["fp32_fixup"]["ms"]
+    return res
+
+
+def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3):
+    """<A> and <grad A> of two Lagrange fields of order 2 and 3 (the fields of run_fields
+    sampled at the element nodes) on the benchmark pair list, hybrid FP32 and FP64."""
+    import torch
+    from paper_2507_21686_gb300.workloads import field_node_positions
+    from tests.helpers import scales
+    ctx.build_cells(parts, tris, w.H)
+    k = "wendland_c4"
+    res = {"kernel": k, "fields": 2, "pairs": P}
+    for order in (2, 3):
+        v = field_node_positions(w.triangles, order)
+        rho = 1.0 + 0.25 * v[..., 0] * v[..., 1]
+        u = np.sin(3 * v[..., 0]) + np.cos(2 * v[..., 1])
+        vv = torch.from_numpy(np.stack([rho, rho * u], axis=-1).astype(np.float32)).to(parts.device)
+        out, r = {}, {}
+        for mode in ("fp32_hybrid", "fp64"):
+            out[mode] = ctx.field_integrals(vv, k, mode, order=order)
+            if mode == "fp32_hybrid":
+                r["closed_form_share"] = ctx.stats()["n_fallback"] / max(P, 1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a_, b_ in ev:
+                flush.zero_()
+                a_.record(stream)
+                ctx.field_integrals(vv, k, mode, order=order)
+                b_.record(stream)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+            r[mode] = {"ms": ms, "pairs_per_s": P / (ms / 1e3)}
+        a32, g32 = out["fp32_hybrid"]
+        a64, g64 = out["fp64"]
+        sa = float(np.max(np.abs(vv.cpu().numpy())))
+        sg = scales(k, w.H, 0)[1]
+        r["max_err_hybrid_vs_fp64"] = {
+            "value": float(((a32.double() - a64).abs() / torch.clamp(a64.abs(), min=sa)).max()),
+            "grad": float(((g32.double() - g64).abs() / torch.clamp(g64.abs(), min=sa * sg)).max())}
+        r["speedup_hybrid_vs_fp64"] = r["fp64"]["ms"] / r["fp32_hybrid"]["ms"]
+        res[f"order{order}"] = r
+        del out, a32, g32, a64, g64
     return res
 
 

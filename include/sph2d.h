@@ -283,6 +283,32 @@ sph2d_status sph2d_field_integrals(sph2d_ctx* ctx, int kernel, int mode, const f
                                    int nf, void* value, void* grad);
 
 /*
+ * Lagrange boundary fields of order 2 or 3 (the higher-order element fields the paper's
+ * introduction names as the extension of Sec. 3's linear interpolation).  Each triangle carries
+ * nodes_of(order) = (order+1)(order+2)/2 node values per field on the principal lattice
+ * {(i, j, l)/order : i + j + l = order} in barycentric coordinates, in this order: the three
+ * vertices (input order); then the nodes inside edge (0,1), edge (1,2), edge (2,0), each edge
+ * from its first vertex to its second (order 2: the midpoints; order 3: the points at 1/3 and
+ * 2/3); then, for order 3, the centroid.  The field is the unique polynomial of that degree
+ * through the nodes; value and grad as for sph2d_field_integrals.
+ *   node_values  device float [M][nodes_of(order)][nf]
+ *   order        2 or 3 (order 1 is sph2d_field_integrals)
+ *   mode         SPH2D_FP64: closed form (moments to degree 3 and the boundary term's edge
+ *                integrals of k(rho) t^m, m <= 3) for every pair, double outputs.  Its rounding
+ *                error grows like (distance / element size)^order: ~1e-11 of the field scale
+ *                for elements of H/3.
+ *                SPH2D_FP32_HYBRID: the hybrid mode's quadrature in FP32 (the field evaluated
+ *                from its nodes at every quadrature point) for pairs that qualify, the FP64
+ *                closed form for the rest; float outputs; n_fallback in sph2d_last_stats
+ *                counts the closed-form pairs.
+ *                SPH2D_FP32_FIXUP: UNSUPPORTED (the closed form in FP32 loses up to
+ *                (distance / size)^order digits of the field scale).
+ * Does not synchronise.  Errors: NOT_BUILT, INVALID_ARG, UNSUPPORTED, OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_field_integrals_p(sph2d_ctx* ctx, int kernel, int mode, int order, const float* node_values,
+                                     int nf, void* value, void* grad);
+
+/*
  * ---- Learned surrogate -------------------------------------------------------------------
  * The paper has no counterpart: a small network that replaces the closed form for pairs
  * inside a trained domain, evaluated on tensor cores (FP16 operands, FP32 accumulation; the

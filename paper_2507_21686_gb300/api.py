@@ -169,21 +169,29 @@ class Context:
             _mode_id(mode), _ptr(out)))
         return out
 
-    def field_integrals(self, vertex_values, kernel, mode="fp64", want_grad: bool = True):
-        """Piecewise-linear fields over the pair list of the last build: vertex_values
-        [M, 3, nf] (or [M, 3]) -> value [N, nf], grad [N, nf, 2] (or None)."""
+    def field_integrals(self, vertex_values, kernel, mode="fp64", want_grad: bool = True, order: int = 1):
+        """Lagrange fields over the pair list of the last build: node values [M, nodes, nf]
+        (or [M, nodes]; nodes = 3, 6 or 10 for order 1, 2 or 3) -> value [N, nf], grad
+        [N, nf, 2] (or None).  Order 1 is the piecewise-linear field."""
         vv = torch.as_tensor(vertex_values)
         if vv.dim() == 2:
             vv = vv[:, :, None]
         nf = vv.shape[2]
+        if vv.shape[1] != (order + 1) * (order + 2) // 2:
+            raise ValueError(f"order {order} needs {(order + 1) * (order + 2) // 2} node values per triangle")
         vv = vv.to(device=self._dev(), dtype=torch.float32).contiguous()
         n = self._keep[0].shape[0] if hasattr(self, "_keep") else 0
         dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
         val = torch.empty((n, nf), dtype=dt, device=self._dev())
         gr = torch.empty((n, nf, 2), dtype=dt, device=self._dev()) if want_grad else None
         self._bind_stream()
-        check(self.lib, self.h, self.lib.sph2d_field_integrals(
-            self.h, _kernel_id(kernel), _mode_id(mode), _ptr(vv), int(nf), _ptr(val), _ptr(gr)))
+        if order == 1:
+            rc = self.lib.sph2d_field_integrals(
+                self.h, _kernel_id(kernel), _mode_id(mode), _ptr(vv), int(nf), _ptr(val), _ptr(gr))
+        else:
+            rc = self.lib.sph2d_field_integrals_p(
+                self.h, _kernel_id(kernel), _mode_id(mode), int(order), _ptr(vv), int(nf), _ptr(val), _ptr(gr))
+        check(self.lib, self.h, rc)
         return val, gr
 
     # -- adjoint -----------------------------------------------------------------------

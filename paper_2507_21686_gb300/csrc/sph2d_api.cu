@@ -404,6 +404,27 @@ sph2d_status sph2d_field_integrals(sph2d_ctx* h, int kernel, int mode, const flo
   return launch_fields(c, kernel, mode, vertex_values, nf, value, grad);
 }
 
+sph2d_status sph2d_field_integrals_p(sph2d_ctx* h, int kernel, int mode, int order, const float* node_values,
+                                     int nf, void* value, void* grad) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  c->err.clear();
+  if (!c->cells.built) return set_err(c, SPH2D_ERR_NOT_BUILT, "no pair list built");
+  if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
+  if (order != 2 && order != 3) return set_err(c, SPH2D_ERR_INVALID_ARG, "order must be 2 or 3");
+  if (mode != SPH2D_FP64 && mode != SPH2D_FP32_HYBRID)
+    return set_err(c, (mode == SPH2D_SURROGATE || mode == SPH2D_FP32_FIXUP) ? SPH2D_ERR_UNSUPPORTED
+                                                                           : SPH2D_ERR_INVALID_ARG,
+                   "order 2 and 3 fields support SPH2D_FP64 and SPH2D_FP32_HYBRID");
+  if (nf < 1 || nf > SPH2D_MAX_FIELDS) return set_err(c, SPH2D_ERR_INVALID_ARG, "nf must be 1..SPH2D_MAX_FIELDS");
+  if ((c->cells.M > 0 && !node_values) || (c->cells.N > 0 && !value))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "null pointer");
+  if (reinterpret_cast<uintptr_t>(node_values) & 3u)
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "node values must be 4-byte aligned");
+  cudaSetDevice(c->device);
+  return launch_fields_p(c, kernel, mode, order, node_values, nf, value, grad);
+}
+
 // ---- learned surrogate -----------------------------------------------------------------
 static sph2d_status sur_ctx(sph2d_ctx* h, Ctx** out, bool need_ready) {
   if (!h) return SPH2D_ERR_INVALID_ARG;

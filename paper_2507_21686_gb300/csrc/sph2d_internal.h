@@ -79,6 +79,8 @@ sph2d_status launch_pair_integrals(Ctx* c, const double* pairs, int64_t P, int k
 // piecewise-linear boundary fields over the context's pair list (fields.cu)
 sph2d_status launch_fields(Ctx* c, int kernel, int mode, const float* values, int nf, void* value,
                            void* grad);
+sph2d_status launch_fields_p(Ctx* c, int kernel, int mode, int order, const float* values, int nf, void* value,
+                             void* grad);
 
 // adjoint (backward.cu)
 sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma,

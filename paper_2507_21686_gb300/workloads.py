@@ -338,6 +338,25 @@ def surrogate_box(seed: int = 5, n: int = 2048, obstacle_cells: int = 660) -> Wo
     return w
 
 
+# node lattice of the order-k Lagrange triangle (barycentric indices / k), in the node order of
+# sph2d_field_integrals_p: vertices, the nodes inside edges (0,1), (1,2), (2,0) from the
+# first vertex to the second, then the interior node
+_NODE_LATTICE = {
+    1: [(1, 0, 0), (0, 1, 0), (0, 0, 1)],
+    2: [(2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (0, 1, 1), (1, 0, 1)],
+    3: [(3, 0, 0), (0, 3, 0), (0, 0, 3), (2, 1, 0), (1, 2, 0), (0, 2, 1), (0, 1, 2), (1, 0, 2), (2, 0, 1),
+        (1, 1, 1)],
+}
+
+
+def field_node_positions(triangles: np.ndarray, order: int) -> np.ndarray:
+    """World positions [M, nodes, 2] of the order-k field nodes of each triangle (float64), for
+    sampling a field function into node values."""
+    t = np.asarray(triangles, dtype=np.float64).reshape(-1, 3, 2)
+    w = np.asarray(_NODE_LATTICE[order], dtype=np.float64) / order
+    return np.einsum("nj,mjc->mnc", w, t)
+
+
 def full_cover_square(n_side: int = 2) -> np.ndarray:
     """Triangulation of [-1,1]^2 into 2*n_side^2 triangles (n_side=2: the paper's 8-triangle
     mesh of Sec. 6.2; n_side=... finer meshes for additivity checks).  float64 [M, 6]."""

@@ -162,3 +162,13 @@ def test_mutant_is_caught():
     rv, _ = ref(xp[0], xp[1], H * H * kernel_second_moment("wendland_c2"))
     v, _ = mesh_field_p("wendland_c2", H, xp, tris, 3, f, mutant=6)
     assert abs(v - rv) > 1e-6
+
+
+def test_input_node_positions_match_the_oracle():
+    """the input generator's node lattice (used to sample fields for the GPU path) is the
+    oracle's"""
+    from paper_2507_21686_gb300.workloads import field_node_positions
+    rng = np.random.default_rng(45)
+    tris = rng.normal(size=(20, 6))
+    for order in (1, 2, 3):
+        assert np.allclose(field_node_positions(tris, order), oracle.field_nodes(tris, order), atol=1e-15)
