@@ -309,6 +309,37 @@ sph2d_status sph2d_field_integrals_p(sph2d_ctx* ctx, int kernel, int mode, int o
                                      int nf, void* value, void* grad);
 
 /*
+ * ---- Boundary pressure coupling (Appendix A) ---------------------------------------------
+ * Uses the particles and triangles of the context's build (sph2d_build_cells); the particles
+ * double as the fluid whose pressures are extrapolated.  Per-particle inputs are device float
+ * [N]: density rho_i, pressure p_i, volume V_i = m_i / rho_i.
+ *
+ * sph2d_mls_pressure: moving-least-squares pressure at Q points (device float [Q][2]) -> out
+ * (device real [Q]: double for SPH2D_FP64, float for SPH2D_FP32_FIXUP).  At a point b the
+ * linear fit a + g . (x_j - b)/H to the pressures of the particles within H, weighted by
+ * V_j k(|x_j - b|/H), gives p(b) = a; where the fit's 3 x 3 normal matrix has determinant
+ * <= 1e-6 (sum w)^3 (fewer than three neighbours, or collinear) the weighted average
+ * sum w p / sum w; 0 where no particle lies within H.  (The appendix cites Band et al.'s MLS
+ * pressure extrapolation without a formula; this is the reading used.)
+ *
+ * sph2d_boundary_pressure: the boundary's pressure acceleration (device real [N][2])
+ *   a_i = - int_Omega rho_0b (p(x')/rho_0b^2 + p_i/rho_i^2) grad_x W(x_i - x') dx'
+ * with the boundary density at rho_0b > 0 and p(x') by
+ *   model 1: MLS at each triangle vertex (stored as float), interpolated barycentrically:
+ *            a_i = -(1/rho_0b) <grad p>_i - rho_0b p_i/rho_i^2 grad gamma_i
+ *   model 2: MLS at the point of each culled triangle's boundary closest to x_i, constant on
+ *            that triangle for that particle:
+ *            a_i = - sum_T rho_0b (p(x_iT)/rho_0b^2 + p_i/rho_i^2) grad gamma_iT
+ * Modes SPH2D_FP64 and SPH2D_FP32_FIXUP (the integrals as in sph2d_boundary_integrals; MLS in
+ * the mode's precision).  Does not synchronise.  Errors: NOT_BUILT, INVALID_ARG, UNSUPPORTED,
+ * OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_mls_pressure(sph2d_ctx* ctx, int kernel, int mode, const float* volume, const float* pressure,
+                                const float* points, int64_t Q, void* out);
+sph2d_status sph2d_boundary_pressure(sph2d_ctx* ctx, int kernel, int mode, int model, const float* density,
+                                     const float* pressure, const float* volume, double rho0_b, void* accel);
+
+/*
  * ---- Learned surrogate -------------------------------------------------------------------
  * The paper has no counterpart: a small network that replaces the closed form for pairs
  * inside a trained domain, evaluated on tensor cores (FP16 operands, FP32 accumulation; the

@@ -57,6 +57,8 @@ SIGNATURES = {
     "sph2d_pair_list_integrals_noalloc": (_ST, [_P, _I64, _P, _I64, _P, _P, _I64, _I, _D, _I, _P, _P, _P]),
     "sph2d_field_integrals": (_ST, [_P, _I, _I, _P, _I, _P, _P]),
     "sph2d_field_integrals_p": (_ST, [_P, _I, _I, _I, _P, _I, _P, _P]),
+    "sph2d_mls_pressure": (_ST, [_P, _I, _I, _P, _P, _P, _I64, _P]),
+    "sph2d_boundary_pressure": (_ST, [_P, _I, _I, _I, _P, _P, _P, _D, _P]),
     "sph2d_surrogate_init": (_ST, [_P, _I, ctypes.c_uint64]),
     "sph2d_surrogate_train": (_ST, [_P, _P, _I64, _D, _I, _I, _D, _D, ctypes.c_uint64,
                                     ctypes.POINTER(_D), ctypes.POINTER(_I64)]),

@@ -194,6 +194,35 @@ class Context:
         check(self.lib, self.h, rc)
         return val, gr
 
+    # -- boundary pressure coupling (Appendix A) -----------------------------------------
+    def mls_pressure(self, volume, pressure, points, kernel, mode="fp64"):
+        """MLS pressure of the build's particles at points [Q, 2] -> [Q]."""
+        vol = torch.as_tensor(volume).to(device=self._dev(), dtype=torch.float32).contiguous()
+        pr = torch.as_tensor(pressure).to(device=self._dev(), dtype=torch.float32).contiguous()
+        pts = torch.as_tensor(points).to(device=self._dev(), dtype=torch.float32).reshape(-1, 2).contiguous()
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        out = torch.empty(pts.shape[0], dtype=dt, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_mls_pressure(
+            self.h, _kernel_id(kernel), _mode_id(mode), _ptr(vol), _ptr(pr), _ptr(pts), pts.shape[0], _ptr(out)))
+        return out
+
+    def boundary_pressure(self, density, pressure, volume, rho0_b: float, kernel, mode="fp64", model: int = 2):
+        """Boundary pressure acceleration [N, 2] of the build's particles (model 1: vertex
+        pressures, model 2: contact-point pressures)."""
+        dev = self._dev()
+        rho = torch.as_tensor(density).to(device=dev, dtype=torch.float32).contiguous()
+        pr = torch.as_tensor(pressure).to(device=dev, dtype=torch.float32).contiguous()
+        vol = torch.as_tensor(volume).to(device=dev, dtype=torch.float32).contiguous()
+        n = self._keep[0].shape[0] if hasattr(self, "_keep") else 0
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        acc = torch.empty((n, 2), dtype=dt, device=dev)
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_boundary_pressure(
+            self.h, _kernel_id(kernel), _mode_id(mode), int(model), _ptr(rho), _ptr(pr), _ptr(vol),
+            float(rho0_b), _ptr(acc)))
+        return acc
+
     # -- adjoint -----------------------------------------------------------------------
     def backward(self, particles, tris, kernel, H: float, d_gamma, mode="fp64", d_grad=None):
         """dL/dx [N, 2] and dL/dvertices [M, 6] from dL/dgamma [N] and optionally

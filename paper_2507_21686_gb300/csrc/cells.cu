@@ -327,6 +327,7 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
                          double H) {
   Cells& cl = c->cells;
   cl.built = false;
+  cl.part_grid = false;
   cl.particles = particles;
   cl.tris = tris;
   cl.N = N;

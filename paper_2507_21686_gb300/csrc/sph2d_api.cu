@@ -197,7 +197,8 @@ sph2d_status sph2d_destroy(sph2d_ctx* h) {
                     &c.pair_off,  &c.pair_tri,    &c.pair_pid,  &c.counts,    &c.slots,
                     &c.host_flags_dev, &c.misc, &c.tri_off, &c.tri_pid, &c.tri_cursor,
                     &c.bwd_g, &c.bwd_grad, &c.pair_vals, &c.pair_list2, &c.sur_prm, &c.sur_split, &c.sur_act,
-                    &c.sur_data, &c.sur_idx, &c.sur_vals, &c.sur_fb};
+                    &c.sur_data, &c.sur_idx, &c.sur_vals, &c.sur_fb, &c.part_start, &c.part_cursor,
+                    &c.part_ids, &c.pres_vertex, &c.pres_tmp};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c.pinned) cudaFreeHost(c.pinned);
@@ -423,6 +424,46 @@ sph2d_status sph2d_field_integrals_p(sph2d_ctx* h, int kernel, int mode, int ord
     return set_err(c, SPH2D_ERR_INVALID_ARG, "node values must be 4-byte aligned");
   cudaSetDevice(c->device);
   return launch_fields_p(c, kernel, mode, order, node_values, nf, value, grad);
+}
+
+// ---- boundary pressure coupling (Appendix A) ----------------------------------------------
+static sph2d_status press_check(Ctx* c, int kernel, int mode) {
+  if (!c->cells.built) return set_err(c, SPH2D_ERR_NOT_BUILT, "no pair list built");
+  if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
+  if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
+    return set_err(c, (mode == SPH2D_SURROGATE || mode == SPH2D_FP32_HYBRID) ? SPH2D_ERR_UNSUPPORTED
+                                                                            : SPH2D_ERR_INVALID_ARG,
+                   "boundary pressure supports SPH2D_FP64 and SPH2D_FP32_FIXUP");
+  return SPH2D_OK;
+}
+
+sph2d_status sph2d_mls_pressure(sph2d_ctx* h, int kernel, int mode, const float* volume, const float* pressure,
+                                const float* points, int64_t Q, void* out) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  c->err.clear();
+  sph2d_status s = press_check(c, kernel, mode);
+  if (s != SPH2D_OK) return s;
+  if (Q < 0) return set_err(c, SPH2D_ERR_INVALID_ARG, "Q < 0");
+  if (Q > 0 && (!points || !out || (c->cells.N > 0 && (!volume || !pressure))))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "null pointer");
+  cudaSetDevice(c->device);
+  return launch_mls_points(c, kernel, mode, volume, pressure, points, Q, out);
+}
+
+sph2d_status sph2d_boundary_pressure(sph2d_ctx* h, int kernel, int mode, int model, const float* density,
+                                     const float* pressure, const float* volume, double rho0_b, void* accel) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  c->err.clear();
+  sph2d_status s = press_check(c, kernel, mode);
+  if (s != SPH2D_OK) return s;
+  if (model != 1 && model != 2) return set_err(c, SPH2D_ERR_INVALID_ARG, "model must be 1 or 2");
+  if (!(rho0_b > 0.0) || !std::isfinite(rho0_b)) return set_err(c, SPH2D_ERR_INVALID_ARG, "rho0_b must be > 0");
+  if (c->cells.N > 0 && (!density || !pressure || !volume || !accel))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "null pointer");
+  cudaSetDevice(c->device);
+  return launch_boundary_pressure(c, kernel, mode, model, density, pressure, volume, rho0_b, accel);
 }
 
 // ---- learned surrogate -----------------------------------------------------------------

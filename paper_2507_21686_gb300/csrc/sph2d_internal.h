@@ -19,6 +19,7 @@ struct DevBuf {
 // culling grid + pair list of the last build
 struct Cells {
   bool built = false;
+  bool part_grid = false;     // particle grid of this build made (boundary pressure / MLS)
   const float* particles = nullptr;
   const float* tris = nullptr;
   int64_t N = 0, M = 0;
@@ -43,6 +44,8 @@ struct Ctx {
       pair_vals, pair_list2;   // per-pair values and second-piece list of the cubic spline
   // learned surrogate: parameters (+ Adam state), training data and scratch, serving scratch
   DevBuf sur_prm, sur_split, sur_act, sur_data, sur_idx, sur_vals, sur_fb;
+  // boundary pressure coupling: particle grid (cell starts, cursors, ids) and scratch
+  DevBuf part_start, part_cursor, part_ids, pres_vertex, pres_tmp;
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
   bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
   bool fallback_pending = false;  // pinned[10] holds the fallback count of the last surrogate call
@@ -81,6 +84,12 @@ sph2d_status launch_fields(Ctx* c, int kernel, int mode, const float* values, in
                            void* grad);
 sph2d_status launch_fields_p(Ctx* c, int kernel, int mode, int order, const float* values, int nf, void* value,
                              void* grad);
+
+// boundary pressure coupling (pressure.cu)
+sph2d_status launch_mls_points(Ctx* c, int kernel, int mode, const float* vol, const float* pres, const float* pts,
+                               int64_t Q, void* out);
+sph2d_status launch_boundary_pressure(Ctx* c, int kernel, int mode, int model, const float* rho, const float* pres,
+                                      const float* vol, double rho0b, void* accel);
 
 // adjoint (backward.cu)
 sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma,
