@@ -405,6 +405,9 @@ def run_ours(args):
     fields = run_fields(ctx, parts, tris, w, stream, flush, P)
     fields["lagrange"] = run_fields_p(ctx, parts, tris, w, stream, flush, P)
 
+    # ---- boundary pressure coupling (Appendix A) on the same workload
+    pressure = run_pressure(ctx, parts, tris, w, stream, flush, P)
+
     # ---- adjoint workload: 262,144 particles x 51,712 triangles, Wendland C4
     adjoint = run_adjoint(ctx, dev, stream, flush)
 
@@ -467,6 +470,7 @@ def run_ours(args):
         "gamma_grad_only": gamma_grad_only,
         "hybrid": hybrid,
         "fields": fields,
+        "pressure": pressure,
         "adjoint": adjoint,
         "surrogate": surrogate,
         "e2e": e2e,
@@ -584,6 +588,43 @@ def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3):
         r["speedup_hybrid_vs_fp64"] = r["fp64"]["ms"] / r["fp32_hybrid"]["ms"]
         res[f"order{order}"] = r
         del out, a32, g32, a64, g64
+    return res
+
+
+def run_pressure(ctx, parts, tris, w, stream, flush, P, reps=3):
+    """Boundary pressure acceleration (Appendix A) of every particle of the benchmark workload
+    under a hydrostatic fluid state: both models, FP32 + fix-up and FP64, Wendland C4."""
+    import torch
+    from paper_2507_21686_gb300.workloads import hydrostatic_state
+    from tests.helpers import scales
+    n = int(round(np.sqrt(len(w.particles))))
+    st = hydrostatic_state(w.particles, 1.0 / n, 2)
+    dev = parts.device
+    rho, pr, vol = (torch.from_numpy(st[k]).to(dev) for k in ("density", "pressure", "volume"))
+    ctx.build_cells(parts, tris, w.H)
+    k = "wendland_c4"
+    res = {"kernel": k, "pairs": P, "state": "hydrostatic, rho 1000 +-1%, p = 1000 g (1 - y) +-2%, rho_0b 1000"}
+    pmax = float(st["pressure"].max())
+    sc = (2.0 * pmax / 1000.0) * scales(k, w.H, 0)[1]
+    for model in (1, 2):
+        out, r = {}, {}
+        for mode in ("fp32_fixup", "fp64"):
+            out[mode] = ctx.boundary_pressure(rho, pr, vol, st["rho0_b"], k, mode, model)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a_, b_ in ev:
+                flush.zero_()
+                a_.record(stream)
+                ctx.boundary_pressure(rho, pr, vol, st["rho0_b"], k, mode, model)
+                b_.record(stream)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+            r[mode] = {"ms": ms, "particles_per_s": len(w.particles) / (ms / 1e3), "pairs_per_s": P / (ms / 1e3)}
+        r["max_err_fp32_vs_fp64"] = float((out["fp32_fixup"].double() - out["fp64"]).abs().max() / sc)
+        res[f"model{model}"] = r
+        del out
+    res["note"] = ("times include the MLS pressures (model 1: 3 per triangle; model 2: one per pair) and, for "
+                   "model 1, the linear-field and boundary-integral passes; the particle grid is built once per "
+                   "cell build (first call, untimed)")
     return res
 
 

@@ -306,20 +306,25 @@ def box_obstacle(seed: int = 2, n: int = 1024, obstacle_cells: int | None = None
                     ["wendland_c2", "wendland_c4", "cubic_spline"], 3, parts, tris)
 
 
-def hydrostatic_box(seed: int = 6, n: int = 1024, obstacle_cells: int | None = None) -> Workload:
-    """The box-with-obstacle geometry of box_obstacle(seed, n) with fluid state for the boundary
-    pressure coupling: rest density 1000 with +-1% noise, hydrostatic pressure 1000 g (1 - y)
-    (g = 9.81) with +-2% noise, volumes dx^2; boundary rest density rho_0b = 1000.  extra holds
-    float32 arrays density, pressure, volume and rho0_b."""
-    w = box_obstacle(seed, n, obstacle_cells)
+def hydrostatic_state(particles: np.ndarray, dx: float, seed: int) -> dict:
+    """Fluid state for the boundary pressure coupling: rest density 1000 with +-1% noise,
+    hydrostatic pressure 1000 g (1 - y) (g = 9.81) with +-2% noise, volumes dx^2; boundary rest
+    density rho_0b = 1000.  float32 arrays density, pressure, volume and rho0_b."""
     rng = np.random.default_rng(seed + 100)
-    N = len(w.particles)
-    y = w.particles[:, 1].astype(np.float64)
+    N = len(particles)
+    y = np.asarray(particles)[:, 1].astype(np.float64)
     dens = 1000.0 * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, size=N))
     pres = 1000.0 * 9.81 * (1.0 - y) * (1.0 + 0.02 * rng.uniform(-1.0, 1.0, size=N))
-    w.extra = {"density": dens.astype(np.float32), "pressure": pres.astype(np.float32),
-               "volume": np.full(N, (1.0 / n) ** 2, dtype=np.float32), "rho0_b": 1000.0}
-    w.name = f"hydrostatic_box_{N}_x_{len(w.triangles)}"
+    return {"density": dens.astype(np.float32), "pressure": pres.astype(np.float32),
+            "volume": np.full(N, dx * dx, dtype=np.float32), "rho0_b": 1000.0}
+
+
+def hydrostatic_box(seed: int = 6, n: int = 1024, obstacle_cells: int | None = None) -> Workload:
+    """The box-with-obstacle geometry of box_obstacle(seed, n) with the fluid state of
+    hydrostatic_state in extra."""
+    w = box_obstacle(seed, n, obstacle_cells)
+    w.extra = hydrostatic_state(w.particles, 1.0 / n, seed)
+    w.name = f"hydrostatic_box_{len(w.particles)}_x_{len(w.triangles)}"
     return w
 
 
