@@ -168,7 +168,7 @@ static unsigned blocks_for(Ctx* c, K kern, int64_t wanted) {
 template <int KID, int MD>
 static sph2d_status run_hybrid(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
-  constexpr int nlists = KID == KID_CUBIC ? 2 : 1;
+  constexpr int nlists = KID == KID_CUBIC ? 3 : 1;
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t cap = a.P > 0 ? a.P : 1;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(float));
@@ -178,19 +178,22 @@ static sph2d_status run_hybrid(Ctx* c, IntArgs a) {
   a.slots = c->slots.ptr;
   float* vals = static_cast<float*>(c->pair_vals.ptr);
   int64_t* list = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
-  int64_t* near = list + cap;                        // cubic: pairs within H/2 among the list
-  auto* count = static_cast<unsigned long long*>(c->pair_list2.ptr);
-  cudaError_t e = cudaMemsetAsync(count, 0, 2 * sizeof(unsigned long long), c->stream);
+  int64_t* near = list + cap;                        // cubic: pairs within H/2 whose second piece is pending
+  int64_t* fix_list = list + 2 * cap;                // cubic: FP32 pairs for the FP64 fix-up
+  auto* count = static_cast<unsigned long long*>(c->pair_list2.ptr);   // [0] list, [1] near, [2] fix-up
+  cudaError_t e = cudaMemsetAsync(count, 0, 64, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   if (a.P > 0) {
     const int64_t blocks = (a.P + 127) / 128;
     SPH2D_LAUNCH(c, (hybrid_first_kernel<KID, MD>), blocks_for(c, hybrid_first_kernel<KID, MD>, blocks), 128, a,
                  quad_rule(), vals, list, count, near, count + 1);
     if constexpr (KID == KID_CUBIC) {
-      // the cubic spline's two pieces over the list, as its closed-form path (the second
-      // piece also for the quadrature pairs already in near)
+      // the cubic spline's pieces over the list, as its closed-form path (the second piece also
+      // for the quadrature pairs already in near)
       SPH2D_LAUNCH(c, (cubic_first_kernel<float, MD>), blocks_for(c, cubic_first_kernel<float, MD>, blocks), 128,
-                   a, vals, list, count, near, count + 1);
+                   a, vals, list, count, near, count + 1, fix_list, count + 2);
+      SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), blocks_for(c, cubic_fixup_kernel<MD>, blocks), 128, a, vals,
+                   fix_list, count + 2);
       SPH2D_LAUNCH(c, (cubic_second_kernel<float, MD>), blocks_for(c, cubic_second_kernel<float, MD>, blocks), 128,
                    a, vals, near, count + 1);
     } else {

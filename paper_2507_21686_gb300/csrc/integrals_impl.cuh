@@ -398,17 +398,17 @@ __device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double
   }
 }
 
-// first piece of pair q into vals[q]; need: the pair lies within H/2 (second piece pending);
-// returns 1 when an FP32 pair took the FP64 fix-up (both pieces done there)
+// first piece of pair q into vals[q]; need: the pair lies within H/2 (second piece pending).
+// FP32: returns true, writing nothing, when the pair needs the FP64 fix-up (coordinates beyond
+// the FP32 range or a non-finite result); those pairs go to cubic_fixup_kernel, which keeps the
+// FP64 working set out of this kernel's registers
 template <typename OT, int MD>
-__device__ __forceinline__ int cubic_first_pair(const IntArgs& a, int64_t q, OT* __restrict__ vals, bool& need) {
+__device__ __forceinline__ bool cubic_first_pair(const IntArgs& a, int64_t q, OT* __restrict__ vals, bool& need) {
   constexpr int NV = nv_of(MD);
   const int pid = __ldg(a.pair_pid + q);
   const float4 p = a.parts[pid];
   const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-  OT v[NV];
-  int fix = 0;
-  bool done = false;
+  OT* out = vals + q * NV;
   need = false;
   if (sizeof(OT) == sizeof(float)) {
     const float ih = float(a.invH);
@@ -420,55 +420,68 @@ __device__ __forceinline__ int cubic_first_pair(const IntArgs& a, int64_t q, OT*
       lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
       ok = ok && fabsf(lf[2 * j]) <= kFixupCoordLimit && fabsf(lf[2 * j + 1]) <= kFixupCoordLimit;
     }
-    if (ok) {
-      const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
-      float w[13];
-      if (s == 0) {
+    if (!ok) return true;
+    const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
+    float w[13];
+    if (s == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) w[i] = 0.0f;
-      } else {
-        cubic_piece<float, MD>(lf, 0, s, a.C, a.invH, w);
-        need = near_half<float>(lf);
-      }
-#pragma unroll
-      for (int i = 0; i < NV; ++i) ok = ok && isfinite(w[i]);
-      if (ok) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
-        done = true;
-      }
+      for (int i = 0; i < NV; ++i) w[i] = 0.0f;
+    } else {
+      cubic_piece<float, MD>(lf, 0, s, a.C, a.invH, w);
+      need = near_half<float>(lf);
     }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) ok = ok && isfinite(w[i]);
+    if (!ok) {
+      need = false;
+      return true;
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
+    return false;
   }
-  if (!done) {
+  double ld[6], w[13];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+    ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+  }
+  const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+  if (s == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] = 0.0;
+  } else {
+    cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
+    need = near_half<double>(ld);
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
+  return false;
+}
+
+// the FP64 fix-up of the FP32 pairs cubic_first_kernel listed: both pieces of each pair
+template <int MD>
+__global__ void __launch_bounds__(128) cubic_fixup_kernel(IntArgs a, float* __restrict__ vals,
+                                                          const int64_t* __restrict__ list,
+                                                          const unsigned long long* __restrict__ count) {
+  constexpr int NV = nv_of(MD);
+  const int64_t n = int64_t(*count);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n > 0) atomicAdd(a.nfix, (unsigned long long)n);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t q = list[i];
+    const float4 p = a.parts[__ldg(a.pair_pid + q)];
+    const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
     double ld[6], w[13];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
       ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
     }
-    if (sizeof(OT) == sizeof(double)) {
-      const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-      if (s == 0) {
+    eval_local<double, KID_CUBIC, MD>(ld, a.C, a.invH, w);
+    float* o = vals + q * NV;
 #pragma unroll
-        for (int i = 0; i < NV; ++i) w[i] = 0.0;
-        need = false;
-      } else {
-        cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
-        need = near_half<double>(ld);
-      }
-    } else {
-      // FP64 fix-up of an FP32 pair: both pieces here, nothing left for the list
-      eval_local<double, KID_CUBIC, MD>(ld, a.C, a.invH, w);
-      need = false;
-      fix = 1;
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = OT(w[i]);
+    for (int k = 0; k < NV; ++k) o[k] = float(w[k]);
   }
-  OT* out = vals + q * NV;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) out[i] = v[i];
-  return fix;
 }
 
 // warp-aggregated append of the lanes with flag set to list (count: its length)
@@ -485,30 +498,30 @@ __device__ __forceinline__ void warp_append(bool flag, int64_t q, int64_t* __res
   }
 }
 
-// first piece of every pair (src == nullptr) or of the pairs src lists (src_count entries)
+// first piece of every pair (src == nullptr) or of the pairs src lists (src_count entries);
+// pairs within H/2 appended to list, FP32 pairs that need the FP64 fix-up to fix_list
 template <typename OT, int MD>
 __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArgs a, OT* __restrict__ vals,
                                                           const int64_t* __restrict__ src,
                                                           const unsigned long long* __restrict__ src_count,
                                                           int64_t* __restrict__ list,
-                                                          unsigned long long* __restrict__ count) {
+                                                          unsigned long long* __restrict__ count,
+                                                          int64_t* __restrict__ fix_list,
+                                                          unsigned long long* __restrict__ fix_count) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t n = src ? int64_t(*src_count) : a.P;
-  unsigned long long fixes = 0;
   for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
     const int64_t i = base + lane;
-    bool need = false;
-    int fix = 0;
+    bool need = false, defer = false;
     int64_t q = 0;
     if (i < n) {
       q = src ? src[i] : i;
-      fix = cubic_first_pair<OT, MD>(a, q, vals, need);
+      defer = cubic_first_pair<OT, MD>(a, q, vals, need);
     }
-    fixes += __popc(__ballot_sync(0xffffffffu, fix));
     warp_append(need, q, list, count);
+    if (sizeof(OT) == sizeof(float)) warp_append(defer, q, fix_list, fix_count);
   }
-  if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
 
 template <typename OT, int MD>
@@ -688,22 +701,28 @@ template <typename OT, int MD>
 static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
   const int64_t nchunks = (a.P + 31) >> 5;
+  const int64_t cap = a.P > 0 ? a.P : 1;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(a.P > 0 ? a.P : 1) * NV * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, size_t(a.P > 0 ? a.P : 1) * sizeof(int64_t) + 64);
+  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(cap) * NV * sizeof(OT));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, size_t(cap) * 2 * sizeof(int64_t) + 64);
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
   OT* vals = static_cast<OT*>(c->pair_vals.ptr);
+  // header: count of the near list [0] and of the fix-up list [2]; lists from byte 64
+  auto* hdr = static_cast<unsigned long long*>(c->pair_list2.ptr);
   int64_t* list = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
-  auto* count = static_cast<unsigned long long*>(c->pair_list2.ptr);
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), c->stream);
+  int64_t* fix_list = list + cap;
+  cudaError_t e = cudaMemsetAsync(hdr, 0, 64, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   if (a.P > 0) {
     const int64_t blocks = (a.P + 127) / 128;
     SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MD>), resident_blocks(c, cubic_first_kernel<OT, MD>, blocks), 128,
-                 a, vals, nullptr, nullptr, list, count);
+                 a, vals, nullptr, nullptr, list, hdr, fix_list, hdr + 2);
+    if (sizeof(OT) == sizeof(float))
+      SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), resident_blocks(c, cubic_fixup_kernel<MD>, blocks), 128, a,
+                   reinterpret_cast<float*>(vals), fix_list, hdr + 2);
     SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MD>), resident_blocks(c, cubic_second_kernel<OT, MD>, blocks), 128,
-                 a, vals, list, count);
+                 a, vals, list, hdr);
     SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MD>), resident_blocks(c, reduce_pairs_kernel<OT, MD>, (nchunks + 3) / 4),
                  128, a, vals);
   }

@@ -223,6 +223,28 @@ def test_huge_triangles_take_the_fixup_path(ctx):
     assert ctx.stats()["n_fixup"] > 0
 
 
+@pytest.mark.parametrize("kernel", ["wendland_c2", "cubic_spline"])
+@pytest.mark.parametrize("mode", ["fp32_fixup", "fp32_hybrid"])
+def test_huge_triangles_fixup_per_particle(ctx, kernel, mode):
+    """per-particle path with triangles reaching 60 H: their FP32 local coordinates leave the
+    trusted range, so those pairs take the FP64 fix-up (for the cubic spline, its own fix-up
+    pass over a list)"""
+    rng = np.random.default_rng(23)
+    parts = np.zeros((32, 4), dtype=np.float32)
+    parts[:, :2] = rng.uniform(-0.5, 0.5, size=(32, 2))
+    tris = rng.uniform(-60, 60, size=(24, 6))
+    tris[:, 0:2] = rng.uniform(-0.6, 0.6, size=(24, 2))       # one vertex among the particles
+    tris = np.concatenate([tris, W.wall_strip().triangles[:8] * 4 - 1.5]).astype(np.float32)
+    g, gr, mo = ctx.boundary_integrals(_t(parts), _t(tris), kernel, 1.0, 3, mode)
+    st = ctx.stats()
+    off, pt = oracle.cull(parts, tris, 1.0)
+    og, ogr, omo, fl = oracle.particle_sums(kernel, 1.0, parts, tris, off, pt, 3)
+    got = np.concatenate([g.double().cpu().numpy()[:, None], gr.double().cpu().numpy(), mo.double().cpu().numpy()], 1)
+    ref = np.concatenate([og[:, None], ogr, omo], 1)
+    assert rel_err(got, ref, scales(kernel, 1.0, 10)).max() <= TOL_FP32
+    assert st["n_fixup"] > 0
+
+
 # ---------------------------------------------------------------------------------------
 # behaviour
 # ---------------------------------------------------------------------------------------
