@@ -104,6 +104,22 @@ __device__ __forceinline__ int eval_mode(const double* ld, double C, double invH
   }
 }
 
+// FP64 fix-up of one FP32 pair, kept out of line: it runs for few pairs, and inlined its FP64
+// working set and code would sit in the FP32 kernel's register budget and instruction stream
+template <int KID, int MD>
+__device__ __noinline__ void eval_fixup64(const float4 p, const float* t, double invH, double C, float* v) {
+  double ld[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * invH;
+    ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * invH;
+  }
+  double w[13];
+  eval_local<double, KID, MD>(ld, C, invH, w);
+#pragma unroll
+  for (int i = 0; i < nv_of(MD); ++i) v[i] = float(w[i]);
+}
+
 template <typename OT, int KID, int MD>
 __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT* v) {
   const float4 p = a.parts[pid];
@@ -139,14 +155,8 @@ __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT*
         return 0;
       }
     }
-    double ld[6];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-      ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-    }
-    double w[13];
-    eval_local<double, KID, MD>(ld, a.C, a.invH, w);
+    float w[13];
+    eval_fixup64<KID, MD>(p, t, a.invH, a.C, w);
 #pragma unroll
     for (int i = 0; i < nv_of(MD); ++i) v[i] = OT(w[i]);
     return 1;
