@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--surrogate-n", type=int, default=2048,
                     help="particles per side of the surrogate serving box (obstacle scales with it)")
     ap.add_argument("--surrogate-train-pairs", type=int, default=8_000_000)
+    ap.add_argument("--box-n", type=int, default=1024,
+                    help="particles per side of the box workload (1024: the benchmark configuration; "
+                         "smaller values only for profiling captures)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: timed FP32 path only (no FP64 leg, e2e, CPU baseline, L2 flush)")
     return ap.parse_args()
@@ -243,7 +246,7 @@ def run_ours(args):
     from paper_2507_21686_gb300.api import Context
 
     dev = torch.device("cuda", local)
-    w = W.box_obstacle()
+    w = W.box_obstacle(2, args.box_n) if args.box_n != 1024 else W.box_obstacle()
     N, M = len(w.particles), len(w.triangles)
     parts_h = torch.from_numpy(w.particles).pin_memory()
     tris_h = torch.from_numpy(w.triangles).pin_memory()
