@@ -43,7 +43,8 @@ def _digest() -> str:
             if f.endswith((".cu", ".cuh", ".h", ".cpp")):
                 with open(os.path.join(d, f), "rb") as fh:
                     h.update(f.encode() + fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # flags with the checkout's own path left out, so that a copy elsewhere has the same digest
+    h.update(" ".join(f.replace(ROOT, "<root>") for f in ARCH + FLAGS).encode())
     return h.hexdigest()
 
 
