@@ -35,7 +35,8 @@ sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, v
   sph2d_status s = ensure(c, c->host_flags_dev, 64);
   if (s != SPH2D_OK) return s;
   a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr);
-  cudaError_t e = cudaMemsetAsync(a.nfix, 0, sizeof(unsigned long long), c->stream);
+  a.work = a.nfix + 1;                       // chunk counter of the pair kernels
+  cudaError_t e = cudaMemsetAsync(a.nfix, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   const int md = md_for(moment_degree);
   s = mode == SPH2D_FP64 ? integrals_fp64(c, kernel, md, a)

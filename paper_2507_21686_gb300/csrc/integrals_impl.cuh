@@ -45,7 +45,25 @@ struct IntArgs {
   int nm;
   void* slots;
   unsigned long long* nfix;
+  // zeroed counter for dynamic chunk scheduling of the pair kernels (null: static grid stride)
+  unsigned long long* work = nullptr;
 };
+
+// Chunk scheduling of the pair kernels.  Each warp starts at its own chunk; with a counter it
+// then takes the next free chunk (index nw + counter), fetched one chunk ahead so that the
+// atomic's latency hides behind the chunk's arithmetic.  Pair costs vary by a factor of several
+// across the mesh, and a static grid stride left the average SM idle for the last ~15% of the
+// kernel (ncu: sm__cycles_active.avg / sm__cycles_elapsed.avg = 0.85 for C2).  Results do not
+// depend on which warp takes a chunk.
+__device__ __forceinline__ unsigned long long chunk_prefetch(unsigned long long* work) {
+  unsigned long long nx = 0;
+  if (work && (threadIdx.x & 31) == 0) nx = atomicAdd(work, 1ull);
+  return nx;
+}
+__device__ __forceinline__ int64_t chunk_next(unsigned long long* work, int64_t ch, int64_t nw,
+                                              unsigned long long nx) {
+  return work ? nw + int64_t(__shfl_sync(0xffffffffu, nx, 0)) : ch + nw;
+}
 
 // raw integrals of one local-frame triangle -> v = (gamma, grad x, grad y, M00..M03)
 template <typename R, int KID, int MD>
@@ -304,7 +322,8 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   unsigned long long fixes = 0;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
     const int64_t q = ch * 32 + lane;
     int pid = -1;
     OT v[NV];
@@ -345,6 +364,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
         for (int i = 0; i < NV; ++i) slots[(ch * 2 + 1) * NV + i] = v[i];
       }
     }
+    ch = chunk_next(a.work, ch, nw, nx);
   }
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
@@ -521,8 +541,10 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArg
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t n = src ? int64_t(*src_count) : a.P;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
-    const int64_t i = base + lane;
+  const int64_t nchunks = (n + 31) >> 5, nw = stride >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t i = ch * 32 + lane;
     bool need = false, defer = false;
     int64_t q = 0;
     if (i < n) {
@@ -531,6 +553,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArg
     }
     warp_append(need, q, list, count);
     if (sizeof(OT) == sizeof(float)) warp_append(defer, q, fix_list, fix_count);
+    ch = chunk_next(a.work, ch, nw, nx);
   }
 }
 
@@ -540,8 +563,12 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntAr
                                                            const unsigned long long* __restrict__ count) {
   constexpr int NV = nv_of(MD);
   const int64_t n = int64_t(*count);
+  const int64_t nchunks = (n + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   unsigned long long fixes = 0;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t i = ch * 32 + (threadIdx.x & 31);
+    if (i < n) {
     const int64_t q = list[i];
     const float4 p = a.parts[__ldg(a.pair_pid + q)];
     const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
@@ -582,6 +609,8 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntAr
     OT* out = vals + q * NV;
 #pragma unroll
     for (int k = 0; k < NV; ++k) out[k] = out[k] + v[k];
+    }
+    ch = chunk_next(a.work, ch, nw, nx);
   }
   if (fixes) atomicAdd(a.nfix, fixes);
 }
@@ -726,13 +755,16 @@ static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   if (a.P > 0) {
     const int64_t blocks = (a.P + 127) / 128;
+    IntArgs a1 = a, a2 = a;
+    a1.work = hdr + 4;                                 // chunk counters (zeroed with the header)
+    a2.work = hdr + 5;
     SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MD>), resident_blocks(c, cubic_first_kernel<OT, MD>, blocks), 128,
-                 a, vals, nullptr, nullptr, list, hdr, fix_list, hdr + 2);
+                 a1, vals, nullptr, nullptr, list, hdr, fix_list, hdr + 2);
     if (sizeof(OT) == sizeof(float))
       SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), resident_blocks(c, cubic_fixup_kernel<MD>, blocks), 128, a,
                    reinterpret_cast<float*>(vals), fix_list, hdr + 2);
     SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MD>), resident_blocks(c, cubic_second_kernel<OT, MD>, blocks), 128,
-                 a, vals, list, hdr);
+                 a2, vals, list, hdr);
     SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MD>), resident_blocks(c, reduce_pairs_kernel<OT, MD>, (nchunks + 3) / 4),
                  128, a, vals);
   }
