@@ -742,17 +742,28 @@ def run_e2e(args, ctx, parts_h, tris_h, w, dev, stream, P, ws):
                torch.empty((N, 2), dtype=torch.float32).pin_memory(),
                torch.empty((N, nm), dtype=torch.float32).pin_memory()) for _ in KERNELS]
 
+    copy_stream = torch.cuda.Stream(dev)
+
     def e2e_step():
+        # each kernel's results go to the host on a side stream while the next kernel runs
+        cur = torch.cuda.current_stream(dev)
         p = parts_h.to(dev, non_blocking=True)
         t = tris_h.to(dev, non_blocking=True)
-        res = [ctx.boundary_integrals(p, t, KERNELS[0], w.H, MOMENT_DEGREE, "fp32_fixup")]
-        for k in KERNELS[1:]:
-            res.append(ctx.integrals_from_pairs(k, MOMENT_DEGREE, "fp32_fixup"))
-        for (g, gr, mo), (hg, hgr, hmo) in zip(res, outs_h):
-            hg.copy_(g, non_blocking=True)
-            hgr.copy_(gr, non_blocking=True)
-            hmo.copy_(mo, non_blocking=True)
-        torch.cuda.current_stream(dev).synchronize()
+        res = []
+        for i, k in enumerate(KERNELS):
+            if i == 0:
+                r = ctx.boundary_integrals(p, t, k, w.H, MOMENT_DEGREE, "fp32_fixup")
+            else:
+                r = ctx.integrals_from_pairs(k, MOMENT_DEGREE, "fp32_fixup")
+            res.append(r)
+            done = torch.cuda.Event()
+            done.record(cur)
+            copy_stream.wait_event(done)
+            with torch.cuda.stream(copy_stream):
+                for x, hx in zip(r, outs_h[i]):
+                    hx.copy_(x, non_blocking=True)
+        copy_stream.synchronize()
+        cur.synchronize()
 
     for _ in range(max(1, args.warmup)):
         e2e_step()

@@ -557,6 +557,22 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArg
   }
 }
 
+// the second piece of one pair in FP64 (an FP32 pair whose piece did not come out finite), out
+// of line as eval_fixup64
+template <int MD>
+__device__ __noinline__ void cubic_piece2_fp64(const float4 p, const float* t, double invH, double C, float* v) {
+  double ld[6], w[13];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * invH;
+    ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * invH;
+  }
+  const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+  cubic_piece<double, MD>(ld, 1, s, C, invH, w);
+#pragma unroll
+  for (int k = 0; k < nv_of(MD); ++k) v[k] = float(w[k]);
+}
+
 template <typename OT, int MD>
 __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntArgs a, OT* __restrict__ vals,
                                                            const int64_t* __restrict__ list,
@@ -594,17 +610,24 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntAr
       }
     }
     if (!done) {
-      double ld[6], w[13];
+      if (sizeof(OT) == sizeof(float)) {
+        float w[13];
+        cubic_piece2_fp64<MD>(p, t, a.invH, a.C, w);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-        ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+        for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
+        ++fixes;
+      } else {
+        double ld[6], w[13];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+          ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+        }
+        const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+        cubic_piece<double, MD>(ld, 1, s, a.C, a.invH, w);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
       }
-      const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-      cubic_piece<double, MD>(ld, 1, s, a.C, a.invH, w);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
-      if (sizeof(OT) == sizeof(float)) ++fixes;
     }
     OT* out = vals + q * NV;
 #pragma unroll
