@@ -189,8 +189,10 @@ __global__ void __launch_bounds__(128) field_p_quad_kernel(FieldArgs f, QuadRule
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const float ih = float(a.invH);
   const int nv = 3 * f.nf;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < a.P; base += stride) {
-    const int64_t q = base + lane;
+  const int64_t nchunks = (a.P + 31) >> 5, nw = stride >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t q = ch * 32 + lane;
     bool analytic = false;
     if (q < a.P) {
       const int tid = __ldg(a.pair_tri + q);
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(128) field_p_quad_kernel(FieldArgs f, QuadRule
       }
     }
     warp_append(analytic, q, list, count);
+    ch = chunk_next(a.work, ch, nw, nx);
   }
 }
 
@@ -229,14 +232,20 @@ __global__ void __launch_bounds__(128) field_p_list_kernel(FieldArgs f, float* _
   const IntArgs& a = f.a;
   const int64_t n = int64_t(*count);
   const int nv = 3 * f.nf;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t q = list[i];
-    double v[3 * kMaxFields];
-    field_p_pair64<KID, ORDER, GRAD>(f, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
-    float* o = vals + q * nv;
+  const int64_t nchunks = (n + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t i = ch * 32 + (threadIdx.x & 31);
+    if (i < n) {
+      const int64_t q = list[i];
+      double v[3 * kMaxFields];
+      field_p_pair64<KID, ORDER, GRAD>(f, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
+      float* o = vals + q * nv;
 #pragma unroll
-    for (int k = 0; k < 3 * kMaxFields; ++k)
-      if (k < nv) o[k] = float(v[k]);
+      for (int k = 0; k < 3 * kMaxFields; ++k)
+        if (k < nv) o[k] = float(v[k]);
+    }
+    ch = chunk_next(a.work, ch, nw, nx);
   }
 }
 
@@ -294,15 +303,18 @@ static sph2d_status run_fields_p(Ctx* c, int mode, FieldArgs f) {
     float* vals = static_cast<float*>(c->pair_vals.ptr);
     int64_t* list = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
     auto* count = static_cast<unsigned long long*>(c->pair_list2.ptr);
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), c->stream);
+    cudaError_t e = cudaMemsetAsync(count, 0, 64, c->stream);   // list length, chunk counters
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     if (f.a.P > 0) {
       const int64_t blocks = (f.a.P + 127) / 128;
+      FieldArgs fq = f, fl = f;
+      fq.a.work = count + 4;
+      fl.a.work = count + 5;
       SPH2D_LAUNCH(c, (field_p_quad_kernel<KID, ORDER, GRAD>),
-                   field_p_blocks(c, field_p_quad_kernel<KID, ORDER, GRAD>, blocks), 128, f, quad_rule(), vals, list,
+                   field_p_blocks(c, field_p_quad_kernel<KID, ORDER, GRAD>, blocks), 128, fq, quad_rule(), vals, list,
                    count);
       SPH2D_LAUNCH(c, (field_p_list_kernel<KID, ORDER, GRAD>),
-                   field_p_blocks(c, field_p_list_kernel<KID, ORDER, GRAD>, blocks), 128, f, vals, list, count);
+                   field_p_blocks(c, field_p_list_kernel<KID, ORDER, GRAD>, blocks), 128, fl, vals, list, count);
       SPH2D_LAUNCH(c, field_p_sum_kernel, field_p_blocks(c, field_p_sum_kernel, (nchunks + 3) / 4), 128, f, vals);
     }
     if (f.a.N > 0) SPH2D_LAUNCH(c, (field_finalize_kernel<float>), unsigned((f.a.N + 255) / 256), 256, f);

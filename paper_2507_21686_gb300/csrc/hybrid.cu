@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(128, int_minb<float>()) hybrid_first_kernel(In
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const float ih = float(a.invH);
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x - lane; base < a.P; base += stride) {
-    const int64_t q = base + lane;
+  const int64_t nchunks = (a.P + 31) >> 5, nw = stride >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t q = ch * 32 + lane;
     bool analytic = false, piece2 = false;
     if (q < a.P) {
       const float4 p = a.parts[__ldg(a.pair_pid + q)];
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(128, int_minb<float>()) hybrid_first_kernel(In
     }
     warp_append(analytic, q, list, count);
     if (KID == KID_CUBIC) warp_append(piece2, q, near, near_count);
+    ch = chunk_next(a.work, ch, nw, nx);
   }
 }
 
@@ -144,14 +147,20 @@ __global__ void __launch_bounds__(128, int_minb<float>()) hybrid_second_kernel(I
                                                                                const unsigned long long* __restrict__ count) {
   constexpr int NV = nv_of(MD);
   const int64_t n = int64_t(*count);
+  const int64_t nchunks = (n + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   unsigned long long fixes = 0;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t q = list[i];
-    float v[NV];
-    fixes += eval_pair<float, KID, MD>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
-    float* o = vals + q * NV;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t i = ch * 32 + (threadIdx.x & 31);
+    if (i < n) {
+      const int64_t q = list[i];
+      float v[NV];
+      fixes += eval_pair<float, KID, MD>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
+      float* o = vals + q * NV;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) o[k] = v[k];
+      for (int k = 0; k < NV; ++k) o[k] = v[k];
+    }
+    ch = chunk_next(a.work, ch, nw, nx);
   }
   if (fixes) atomicAdd(a.nfix, fixes);
 }
@@ -185,19 +194,23 @@ static sph2d_status run_hybrid(Ctx* c, IntArgs a) {
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   if (a.P > 0) {
     const int64_t blocks = (a.P + 127) / 128;
-    SPH2D_LAUNCH(c, (hybrid_first_kernel<KID, MD>), blocks_for(c, hybrid_first_kernel<KID, MD>, blocks), 128, a,
+    IntArgs aq = a, al = a, a2 = a;                  // chunk counters in the zeroed header
+    aq.work = count + 4;
+    al.work = count + 5;
+    a2.work = count + 6;
+    SPH2D_LAUNCH(c, (hybrid_first_kernel<KID, MD>), blocks_for(c, hybrid_first_kernel<KID, MD>, blocks), 128, aq,
                  quad_rule(), vals, list, count, near, count + 1);
     if constexpr (KID == KID_CUBIC) {
       // the cubic spline's pieces over the list, as its closed-form path (the second piece also
       // for the quadrature pairs already in near)
       SPH2D_LAUNCH(c, (cubic_first_kernel<float, MD>), blocks_for(c, cubic_first_kernel<float, MD>, blocks), 128,
-                   a, vals, list, count, near, count + 1, fix_list, count + 2);
+                   al, vals, list, count, near, count + 1, fix_list, count + 2);
       SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), blocks_for(c, cubic_fixup_kernel<MD>, blocks), 128, a, vals,
                    fix_list, count + 2);
       SPH2D_LAUNCH(c, (cubic_second_kernel<float, MD>), blocks_for(c, cubic_second_kernel<float, MD>, blocks), 128,
-                   a, vals, near, count + 1);
+                   a2, vals, near, count + 1);
     } else {
-      SPH2D_LAUNCH(c, (hybrid_second_kernel<KID, MD>), blocks_for(c, hybrid_second_kernel<KID, MD>, blocks), 128, a,
+      SPH2D_LAUNCH(c, (hybrid_second_kernel<KID, MD>), blocks_for(c, hybrid_second_kernel<KID, MD>, blocks), 128, al,
                    vals, list, count);
     }
     SPH2D_LAUNCH(c, (reduce_pairs_kernel<float, MD>), blocks_for(c, reduce_pairs_kernel<float, MD>, (nchunks + 3) / 4),
