@@ -4,8 +4,8 @@
 // with the boundary density at its rest value rho_0b and the boundary pressure p(x') from a
 // moving-least-squares fit to the particles' pressures, in the appendix's two models:
 //   1 (vertex pressure):  p by MLS at each triangle vertex, interpolated barycentrically;
-//     a_i = -(1/rho_0b) <grad p>_i - rho_0b p_i/rho_i^2 grad gamma_i  (the linear-field pass
-//     and the boundary integrals, combined per particle)
+//     a_i = -(1/rho_0b) <grad p>_i - rho_0b p_i/rho_i^2 grad gamma_i  (one fused pair pass:
+//     the linear-field gradient of the vertex pressures and grad gamma from one evaluation)
 //   2 (contact pressure): per pair one value p(x_iT) at the point of the triangle's boundary
 //     closest to x_i;  a_i = - sum_T rho_0b (p(x_iT)/rho_0b^2 + p_i/rho_i^2) grad gamma_iT
 //     (one fused pair pass: contact point, MLS, grad gamma_iT, weighted segmented sum).
@@ -191,19 +191,6 @@ __global__ void mls_vertices_kernel(PGrid g, const float4* __restrict__ parts, c
   out[i] = float(mls_eval<R, KID>(g, parts, vol, pres, R(tris[2 * i]), R(tris[2 * i + 1])));
 }
 
-template <typename OT>
-__global__ void pressure_combine_kernel(int64_t N, const OT* __restrict__ gradp, const OT* __restrict__ gradg,
-                                        const float* __restrict__ rho, const float* __restrict__ pres, double rho0b,
-                                        OT* __restrict__ acc) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const OT r = OT(__ldg(rho + i));
-  const OT k = OT(rho0b) * OT(__ldg(pres + i)) / (r * r);
-  const OT ib = OT(1.0 / rho0b);
-  acc[2 * i] = -ib * gradp[2 * i] - k * gradg[2 * i];
-  acc[2 * i + 1] = -ib * gradp[2 * i + 1] - k * gradg[2 * i + 1];
-}
-
 // point of the triangle's boundary closest to (x, y)
 template <typename R>
 __device__ __forceinline__ void closest_on_boundary(R x, R y, const float* t, R& cx, R& cy) {
@@ -244,7 +231,8 @@ __global__ void __launch_bounds__(128) contact_pressure_kernel(FieldArgs f, Pres
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   unsigned long long fixes = 0;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
     const int64_t q = ch * 32 + (threadIdx.x & 31);
     int pid = -1, fix = 0;
     OT v[NV];
@@ -268,6 +256,84 @@ __global__ void __launch_bounds__(128) contact_pressure_kernel(FieldArgs f, Pres
     }
     fixes += __popc(__ballot_sync(0xffffffffu, fix));
     field_warp_sum<OT>(f, ch, pid, v);
+    ch = chunk_next(a.work, ch, nw, nx);
+  }
+  if ((threadIdx.x & 31) == 0 && fixes) atomicAdd(a.nfix, fixes);
+}
+
+// model 1, one pair: the linear vertex-pressure field's gradient term and the pair's grad gamma
+// from one closed-form evaluation; v[1..2] = -(1/rho_0b) <grad p>_T - rho_0b p_i/rho_i^2 grad
+// gamma_T (the field gradient as in the linear-field pass: (a/H) gamma - sum_j p_j d gamma /
+// d nu_j); v[0] = <p>_T
+template <typename OT, int KID>
+__device__ __forceinline__ int vertex_pressure_pair(const IntArgs& a, const PressArgs& pa, const float* pv, int pid,
+                                                    int tid, OT* v) {
+  OT w[nv_of(1)];                           // gamma, grad gamma, M00, M10, M01
+  int fix = eval_pair<OT, KID, 1>(a, pid, tid, w);
+  OT g[6];
+  const float* t = a.tris + 6 * int64_t(tid);
+  const float4 p = a.parts[pid];
+  fix |= vertex_grad_pair<OT, KID>(p, t, a.invH, a.C, g);
+  OT l[6];
+  if (sizeof(OT) == sizeof(float)) {
+    const float ih = float(a.invH);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      l[2 * j] = OT((__ldg(t + 2 * j) - p.x) * ih);
+      l[2 * j + 1] = OT((__ldg(t + 2 * j + 1) - p.y) * ih);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      l[2 * j] = OT((double(__ldg(t + 2 * j)) - double(p.x)) * a.invH);
+      l[2 * j + 1] = OT((double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH);
+    }
+  }
+  const OT e1x = l[2] - l[0], e1y = l[3] - l[1], e2x = l[4] - l[0], e2y = l[5] - l[1];
+  const OT D = diff_of_products(e1x, e2y, e1y, e2x);
+  if (D == OT(0)) {
+    v[0] = v[1] = v[2] = OT(0);
+    return fix;
+  }
+  const OT r = OT(__ldg(pa.rho + pid));
+  const OT kg = OT(pa.rho0b) * OT(__ldg(pa.pres + pid)) / (r * r);
+  const OT ib = OT(1.0 / pa.rho0b);
+  const OT iD = OT(1) / D;
+  const float* P = pv + 3 * int64_t(tid);
+  const OT a0 = OT(__ldg(P)), a1 = OT(__ldg(P + 1)), a2 = OT(__ldg(P + 2));
+  const OT d1 = a1 - a0, d2 = a2 - a0;
+  const OT gx = (d1 * e2y - d2 * e1y) * iD, gy = (d2 * e1x - d1 * e2x) * iD;
+  const OT ih = OT(a.invH);
+  const OT fx = gx * ih * w[0] - (a0 * g[0] + a1 * g[2] + a2 * g[4]);
+  const OT fy = gy * ih * w[0] - (a0 * g[1] + a1 * g[3] + a2 * g[5]);
+  v[0] = a0 * w[0] + gx * (w[4] - l[0] * w[0]) + gy * (w[5] - l[1] * w[0]);
+  v[1] = -ib * fx - kg * w[1];
+  v[2] = -ib * fy - kg * w[2];
+  return fix;
+}
+
+// model 1: one fused pair pass, segmented sums as contact_pressure_kernel
+template <typename OT, int KID>
+__global__ void __launch_bounds__(128) vertex_pressure_kernel(FieldArgs f, PressArgs pa, const float* __restrict__ pv) {
+  constexpr int NV = 3 * kMaxFields;
+  const IntArgs& a = f.a;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long fixes = 0;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t q = ch * 32 + (threadIdx.x & 31);
+    int pid = -1, fix = 0;
+    OT v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = OT(0);
+    if (q < a.P) {
+      pid = __ldg(a.pair_pid + q);
+      fix = vertex_pressure_pair<OT, KID>(a, pa, pv, pid, __ldg(a.pair_tri + q), v);
+    }
+    fixes += __popc(__ballot_sync(0xffffffffu, fix));
+    field_warp_sum<OT>(f, ch, pid, v);
+    ch = chunk_next(a.work, ch, nw, nx);
   }
   if ((threadIdx.x & 31) == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
@@ -327,8 +393,21 @@ static sph2d_status mls_vertices_t(Ctx* c, int kernel, const float* vol, const f
   return SPH2D_OK;
 }
 
+template <typename OT, int KID>
+static sph2d_status launch_pass(Ctx* c, int model, const FieldArgs& f, const PressArgs& pa, const float* pv,
+                                int64_t want) {
+  if (model == 1)
+    SPH2D_LAUNCH(c, (vertex_pressure_kernel<OT, KID>), press_blocks(c, vertex_pressure_kernel<OT, KID>, want), 128,
+                 f, pa, pv);
+  else
+    SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID>), press_blocks(c, contact_pressure_kernel<OT, KID>, want), 128,
+                 f, pa);
+  return SPH2D_OK;
+}
+
+// one fused pair pass of model 1 (pv: vertex pressures) or model 2
 template <typename OT>
-static sph2d_status run_contact(Ctx* c, int kernel, FieldArgs f, PressArgs pa) {
+static sph2d_status run_pressure_pass(Ctx* c, int kernel, int model, FieldArgs f, PressArgs pa, const float* pv) {
   constexpr int NV = 3 * kMaxFields;
   const int64_t nchunks = (f.a.P + 31) >> 5;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
@@ -337,23 +416,12 @@ static sph2d_status run_contact(Ctx* c, int kernel, FieldArgs f, PressArgs pa) {
   if (f.a.P > 0) {
     const int64_t want = (nchunks + 3) / 4;
     switch (kernel) {
-      case KID_WC2:
-        SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID_WC2>),
-                     press_blocks(c, contact_pressure_kernel<OT, KID_WC2>, want), 128, f, pa);
-        break;
-      case KID_WC4:
-        SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID_WC4>),
-                     press_blocks(c, contact_pressure_kernel<OT, KID_WC4>, want), 128, f, pa);
-        break;
-      case KID_WC6:
-        SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID_WC6>),
-                     press_blocks(c, contact_pressure_kernel<OT, KID_WC6>, want), 128, f, pa);
-        break;
-      default:
-        SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID_CUBIC>),
-                     press_blocks(c, contact_pressure_kernel<OT, KID_CUBIC>, want), 128, f, pa);
-        break;
+      case KID_WC2: s = launch_pass<OT, KID_WC2>(c, model, f, pa, pv, want); break;
+      case KID_WC4: s = launch_pass<OT, KID_WC4>(c, model, f, pa, pv, want); break;
+      case KID_WC6: s = launch_pass<OT, KID_WC6>(c, model, f, pa, pv, want); break;
+      default: s = launch_pass<OT, KID_CUBIC>(c, model, f, pa, pv, want); break;
     }
+    if (s != SPH2D_OK) return s;
   }
   if (f.a.N > 0) SPH2D_LAUNCH(c, (field_finalize_kernel<OT>), unsigned((f.a.N + 255) / 256), 256, f);
   return SPH2D_OK;
@@ -366,70 +434,52 @@ sph2d_status launch_boundary_pressure(Ctx* c, int kernel, int mode, int model, c
   if (s != SPH2D_OK) return s;
   const size_t osz = mode == SPH2D_FP64 ? sizeof(double) : sizeof(float);
   const int64_t N = cl.N;
-  cudaError_t e;
+  s = ensure(c, c->pres_tmp, size_t(N > 0 ? N : 1) * osz);
+  if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
+  if (s != SPH2D_OK) return s;
+  const float* pv = nullptr;
   if (model == 1) {
-    // vertex pressures -> linear-field gradient <grad p>, plus grad gamma, combined per particle
+    // vertex pressures (float, as the field tables), three per triangle
     s = ensure(c, c->pres_vertex, size_t(3 * cl.M > 0 ? 3 * cl.M : 1) * sizeof(float));
-    if (s == SPH2D_OK) s = ensure(c, c->pres_tmp, size_t(N > 0 ? N : 1) * 6 * osz);
     if (s != SPH2D_OK) return s;
-    auto* pv = static_cast<float*>(c->pres_vertex.ptr);
+    auto* pvm = static_cast<float*>(c->pres_vertex.ptr);
     if (cl.M > 0) {
-      s = mode == SPH2D_FP64 ? mls_vertices_t<double>(c, kernel, vol, pres, pv)
-                             : mls_vertices_t<float>(c, kernel, vol, pres, pv);
+      s = mode == SPH2D_FP64 ? mls_vertices_t<double>(c, kernel, vol, pres, pvm)
+                             : mls_vertices_t<float>(c, kernel, vol, pres, pvm);
       if (s != SPH2D_OK) return s;
     }
-    char* tmp = static_cast<char*>(c->pres_tmp.ptr);
-    void* pval = tmp;                                  // [N]
-    void* pgrad = tmp + size_t(N) * osz;               // [N][2]
-    void* gam = tmp + size_t(3 * N) * osz;             // [N]
-    void* ggrad = tmp + size_t(4 * N) * osz;           // [N][2]
-    s = launch_fields(c, kernel, mode, pv, 1, pval, pgrad);
-    if (s != SPH2D_OK) return s;
-    s = launch_integrals(c, kernel, -1, mode, gam, ggrad, nullptr);
-    if (s != SPH2D_OK) return s;
-    if (N > 0) {
-      if (mode == SPH2D_FP64)
-        SPH2D_LAUNCH(c, (pressure_combine_kernel<double>), unsigned((N + 255) / 256), 256, N,
-                     static_cast<const double*>(pgrad), static_cast<const double*>(ggrad), rho, pres, rho0b,
-                     static_cast<double*>(accel));
-      else
-        SPH2D_LAUNCH(c, (pressure_combine_kernel<float>), unsigned((N + 255) / 256), 256, N,
-                     static_cast<const float*>(pgrad), static_cast<const float*>(ggrad), rho, pres, rho0b,
-                     static_cast<float*>(accel));
-    }
-  } else {
-    s = ensure(c, c->pres_tmp, size_t(N > 0 ? N : 1) * 6 * osz);
-    if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
-    if (s != SPH2D_OK) return s;
-    FieldArgs f{};
-    IntArgs& a = f.a;
-    a.parts = reinterpret_cast<const float4*>(cl.particles);
-    a.tris = cl.tris;
-    a.pair_tri = static_cast<const int32_t*>(c->pair_tri.ptr);
-    a.pair_pid = static_cast<const int32_t*>(c->pair_pid.ptr);
-    a.pair_off = static_cast<const int64_t*>(c->pair_off.ptr);
-    a.P = cl.P;
-    a.N = N;
-    a.H = cl.H;
-    a.invH = 1.0 / cl.H;
-    a.C = kernel_C(kernel);
-    a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr);
-    e = cudaMemsetAsync(a.nfix, 0, sizeof(unsigned long long), c->stream);
-    if (e != cudaSuccess) return cuda_err(c, e, "memset");
-    f.values = nullptr;
-    f.nf = 1;
-    f.value = c->pres_tmp.ptr;                         // sum_T w_iT gamma_iT (unused)
-    f.grad = accel;
-    PressArgs pa{pgrid_of(c), vol, pres, rho, rho0b};
-    s = mode == SPH2D_FP64 ? run_contact<double>(c, kernel, f, pa) : run_contact<float>(c, kernel, f, pa);
-    if (s != SPH2D_OK) return s;
-    e = cudaMemcpyAsync(c->pinned + 8, a.nfix, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) return cuda_err(c, e, "fixup count copy");
-    c->stats.n_pairs = cl.P;
-    c->stats.n_fallback = 0;
-    c->fixup_pending = true;
-    c->fallback_pending = false;
+    pv = pvm;
   }
+  FieldArgs f{};
+  IntArgs& a = f.a;
+  a.parts = reinterpret_cast<const float4*>(cl.particles);
+  a.tris = cl.tris;
+  a.pair_tri = static_cast<const int32_t*>(c->pair_tri.ptr);
+  a.pair_pid = static_cast<const int32_t*>(c->pair_pid.ptr);
+  a.pair_off = static_cast<const int64_t*>(c->pair_off.ptr);
+  a.P = cl.P;
+  a.N = N;
+  a.H = cl.H;
+  a.invH = 1.0 / cl.H;
+  a.C = kernel_C(kernel);
+  a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr);
+  a.work = a.nfix + 1;                               // chunk counter
+  cudaError_t e = cudaMemsetAsync(a.nfix, 0, 2 * sizeof(unsigned long long), c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "memset");
+  f.values = nullptr;
+  f.nf = 1;
+  f.value = c->pres_tmp.ptr;                         // per particle: model 1 <p>, model 2 sum_T w_iT gamma_iT
+  f.grad = accel;
+  PressArgs pa{pgrid_of(c), vol, pres, rho, rho0b};
+  s = mode == SPH2D_FP64 ? run_pressure_pass<double>(c, kernel, model, f, pa, pv)
+                         : run_pressure_pass<float>(c, kernel, model, f, pa, pv);
+  if (s != SPH2D_OK) return s;
+  e = cudaMemcpyAsync(c->pinned + 8, a.nfix, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fixup count copy");
+  c->stats.n_pairs = cl.P;
+  c->stats.n_fallback = 0;
+  c->fixup_pending = true;
+  c->fallback_pending = false;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "boundary pressure launch");
   return SPH2D_OK;
