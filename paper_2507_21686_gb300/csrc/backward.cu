@@ -6,9 +6,9 @@
 // second-order counterpart (pair_math.cuh); d grad gamma_i / d x_i = -sum_j d grad gamma_i /
 // d nu_j.  The vertex gradients are summed triangle-major: the particle-major pair list is
 // transposed into per-triangle lists of pair indices, each sorted ascending (= particle
-// order), and one warp walks a triangle's list in that order and reduces with a fixed
-// butterfly; the second-order particle terms are written per pair and summed particle-major
-// in pair order.  Results do not depend on scheduling.  Nothing from the forward call is
+// order); warps take 32 consecutive entries of that list and reduce them with segmented sums
+// by triangle (vertex_grad_kernel); the second-order particle terms are written per pair and
+// summed particle-major in pair order.  Results do not depend on scheduling.  Nothing from the forward call is
 // stored: pair geometry is recomputed.
 #include <cuda_runtime.h>
 
@@ -22,7 +22,10 @@ struct BwdArgs {
   const int64_t* tri_off;
   const int32_t* tri_q;       // per-triangle pair indices, ascending
   const int32_t* pair_pid;
-  int64_t M;
+  const int32_t* pair_tri;
+  int64_t M, P;
+  void* slots;                // per-chunk partial sums of triangles that cross chunks
+  unsigned long long* work;   // zeroed chunk counter
   double invH, C;
   const void* d_gamma;
   const void* d_grad;         // [N][2] or null
@@ -37,25 +40,34 @@ __device__ __forceinline__ int pair_vertex_grad(const BwdArgs& a, int pid, const
   return vertex_grad_pair<OT, KID>(a.parts[pid], t, a.invH, a.C, g);
 }
 
+// vertex gradients pair-parallel over the triangle-sorted pair list: 32 consecutive positions
+// per warp chunk (taken dynamically), each lane one pair's weighted vertex gradients, segmented
+// suffix sums by triangle; a triangle whose pairs lie in one chunk is written here, the partial
+// sums of triangles that cross chunks go to per-chunk slots (the chunk's first and last
+// segment) for tri_finalize_kernel.  The order of every sum is fixed by the list.
 template <typename OT, int KID, bool SECOND>
 __global__ void __launch_bounds__(128) vertex_grad_kernel(BwdArgs a) {
   const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const OT* dg = static_cast<const OT*>(a.d_gamma);
   const OT* dgr = static_cast<const OT*>(a.d_grad);
   unsigned long long fixes = 0;
-  for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < a.M; t += nw) {
-    OT acc[6] = {OT(0), OT(0), OT(0), OT(0), OT(0), OT(0)};
-    const int64_t s0 = __ldg(a.tri_off + t), s1 = __ldg(a.tri_off + t + 1);
-    const float* tp = a.tris + 6 * t;
-    for (int64_t k = s0 + lane; k < s1; k += 32) {
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t k = ch * 32 + lane;
+    int t = -1;
+    OT v[6] = {OT(0), OT(0), OT(0), OT(0), OT(0), OT(0)};
+    if (k < a.P) {
       const int32_t q = __ldg(a.tri_q + k);
       const int pid = __ldg(a.pair_pid + q);
+      t = __ldg(a.pair_tri + q);
+      const float* tp = a.tris + 6 * int64_t(t);
       OT g[6];
       fixes += pair_vertex_grad<OT, KID>(a, pid, tp, g);
       const OT w = dg[pid];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) acc[i] += w * g[i];
+      for (int i = 0; i < 6; ++i) v[i] = w * g[i];
       if (SECOND) {
         OT J[12];
         fixes += grad_jacobian_pair<OT, KID>(a.parts[pid], tp, a.invH, a.C, J);
@@ -66,8 +78,8 @@ __global__ void __launch_bounds__(128) vertex_grad_kernel(BwdArgs a) {
           // (J_j^T G)_a = sum_b J[j][b][a] G_b
           const OT vx = J[4 * j + 0] * Gx + J[4 * j + 2] * Gy;
           const OT vy = J[4 * j + 1] * Gx + J[4 * j + 3] * Gy;
-          acc[2 * j] += vx;
-          acc[2 * j + 1] += vy;
+          v[2 * j] += vx;
+          v[2 * j + 1] += vy;
           hx -= vx;
           hy -= vy;
         }
@@ -78,17 +90,66 @@ __global__ void __launch_bounds__(128) vertex_grad_kernel(BwdArgs a) {
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const int tn = __shfl_down_sync(0xffffffffu, t, o);
+      const bool same = (lane + o < 32) && (tn == t);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+      for (int i = 0; i < 6; ++i) {
+        const OT x = __shfl_down_sync(0xffffffffu, v[i], o);
+        if (same) v[i] += x;
+      }
     }
-    if (lane == 0) {
-      OT* out = static_cast<OT*>(a.d_tris) + 6 * t;
+    const int tprev = __shfl_up_sync(0xffffffffu, t, 1);
+    const bool head = t >= 0 && (lane == 0 || tprev != t);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int last_head = 31 - __clz(heads);
+    if (head) {
+      const int64_t cs = ch * 32;
+      const int64_t s0 = __ldg(a.tri_off + t), s1 = __ldg(a.tri_off + t + 1);
+      if (s0 >= cs && s1 <= cs + 32) {
+        OT* out = static_cast<OT*>(a.d_tris) + 6 * int64_t(t);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) out[i] = acc[i];
+        for (int i = 0; i < 6; ++i) out[i] = v[i];
+      }
+      OT* slots = static_cast<OT*>(a.slots);
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) slots[(ch * 2) * 6 + i] = v[i];
+      }
+      if (lane == last_head) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) slots[(ch * 2 + 1) * 6 + i] = v[i];
+      }
     }
+    ch = chunk_next(a.work, ch, nw, nx);
   }
-  if (fixes) atomicAdd(a.nfix, fixes);
+  if ((threadIdx.x & 31) == 0 && fixes) atomicAdd(a.nfix, fixes);
+}
+
+// triangles without pairs get zeros; triangles whose pairs cross chunks add their partials in
+// chunk order
+template <typename OT>
+__global__ void tri_finalize_kernel(const int64_t* __restrict__ tri_off, int64_t M, const OT* __restrict__ slots,
+                                    OT* __restrict__ d_tris) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= M) return;
+  const int64_t s0 = tri_off[t], s1 = tri_off[t + 1];
+  OT v[6] = {OT(0), OT(0), OT(0), OT(0), OT(0), OT(0)};
+  if (s1 > s0) {
+    const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
+    if (c0 == c1) return;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = slots[(c0 * 2 + 1) * 6 + i];
+    for (int64_t cc = c0 + 1; cc < c1; ++cc) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] += slots[(cc * 2) * 6 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] += slots[(c1 * 2) * 6 + i];
+  }
+  OT* out = d_tris + 6 * t;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out[i] = v[i];
 }
 
 __global__ void tri_pair_count_kernel(const int32_t* __restrict__ pair_tri, int64_t P,
@@ -129,13 +190,19 @@ static void launch_vertex_grads(Ctx* c, const BwdArgs& a) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vertex_grad_kernel<OT, KID, SECOND>, 128, 0);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  const int64_t want = (a.M + 3) / 4;
-  SPH2D_LAUNCH(c, (vertex_grad_kernel<OT, KID, SECOND>), unsigned(want < cap ? want : cap), 128, a);
+  const int64_t want = (((a.P + 31) >> 5) + 3) / 4;
+  if (a.P > 0) SPH2D_LAUNCH(c, (vertex_grad_kernel<OT, KID, SECOND>), unsigned(want < cap ? want : cap), 128, a);
+  SPH2D_LAUNCH(c, (tri_finalize_kernel<OT>), unsigned((a.M + 255) / 256), 256, a.tri_off, a.M,
+               static_cast<const OT*>(a.slots), static_cast<OT*>(a.d_tris));
 }
 
 template <typename OT>
-static sph2d_status run_vertex_grads(Ctx* c, int kernel, const BwdArgs& a) {
+static sph2d_status run_vertex_grads(Ctx* c, int kernel, BwdArgs a) {
   if (a.M == 0) return SPH2D_OK;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * 6 + 1) * sizeof(OT));
+  if (s != SPH2D_OK) return s;
+  a.slots = c->slots.ptr;
   const bool second = a.d_grad != nullptr;
   switch (kernel) {
     case KID_WC2: second ? launch_vertex_grads<OT, KID_WC2, true>(c, a) : launch_vertex_grads<OT, KID_WC2, false>(c, a); break;
@@ -222,15 +289,18 @@ sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma, 
     a.tri_off = toff;
     a.tri_q = tq;
     a.pair_pid = static_cast<const int32_t*>(c->pair_pid.ptr);
+    a.pair_tri = ptri;
     a.M = M;
+    a.P = P;
     a.invH = 1.0 / cl.H;
     a.C = kernel_C(kernel);
     a.d_gamma = d_gamma;
     a.d_grad = d_grad;
     a.d_tris = d_tris;
     a.pair_terms = second ? c->pair_vals.ptr : nullptr;
-    a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 1;
-    e = cudaMemsetAsync(a.nfix, 0, sizeof(unsigned long long), st);
+    a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 2;
+    a.work = a.nfix + 1;                               // chunk counter
+    e = cudaMemsetAsync(a.nfix, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     s = mode == SPH2D_FP64 ? run_vertex_grads<double>(c, kernel, a) : run_vertex_grads<float>(c, kernel, a);
     if (s != SPH2D_OK) return s;
