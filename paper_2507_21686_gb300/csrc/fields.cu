@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) field_kernel(FieldArgs f)
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   unsigned long long fixes = 0;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+       ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
     const int64_t q = ch * 32 + lane;
     int pid = -1;
     OT v[NV];
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) field_kernel(FieldArgs f)
     }
     fixes += __popc(__ballot_sync(0xffffffffu, fix));
     field_warp_sum<OT>(f, ch, pid, v);
+    ch = chunk_next(a.work, ch, nw, nx);
   }
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
@@ -150,7 +153,8 @@ sph2d_status launch_fields(Ctx* c, int kernel, int mode, const float* values, in
   sph2d_status s = ensure(c, c->host_flags_dev, 64);
   if (s != SPH2D_OK) return s;
   a.nfix = static_cast<unsigned long long*>(c->host_flags_dev.ptr);
-  cudaError_t e = cudaMemsetAsync(a.nfix, 0, sizeof(unsigned long long), c->stream);
+  a.work = a.nfix + 1;                               // chunk counter
+  cudaError_t e = cudaMemsetAsync(a.nfix, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   const bool g = grad != nullptr;
   if (mode == SPH2D_FP64) s = g ? dispatch_fields<double, true>(c, kernel, f) : dispatch_fields<double, false>(c, kernel, f);

@@ -164,7 +164,9 @@ __global__ void __launch_bounds__(128) field_p_kernel(FieldArgs f) {
   const IntArgs& a = f.a;
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+       ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
     const int64_t q = ch * 32 + (threadIdx.x & 31);
     int pid = -1;
     double v[NV];
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(128) field_p_kernel(FieldArgs f) {
       field_p_pair64<KID, ORDER, GRAD>(f, pid, __ldg(a.pair_tri + q), v);
     }
     field_warp_sum<double>(f, ch, pid, v);
+    ch = chunk_next(a.work, ch, nw, nx);
   }
 }
 
@@ -287,8 +290,12 @@ static sph2d_status run_fields_p(Ctx* c, int mode, FieldArgs f) {
   const int64_t nchunks = (f.a.P + 31) >> 5;
   if (mode == SPH2D_FP64) {
     sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(double));
+    if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
     if (s != SPH2D_OK) return s;
     f.a.slots = c->slots.ptr;
+    f.a.work = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 1;   // chunk counter
+    cudaError_t e0 = cudaMemsetAsync(f.a.work, 0, sizeof(unsigned long long), c->stream);
+    if (e0 != cudaSuccess) return cuda_err(c, e0, "memset");
     if (f.a.P > 0)
       SPH2D_LAUNCH(c, (field_p_kernel<KID, ORDER, GRAD>),
                    field_p_blocks(c, field_p_kernel<KID, ORDER, GRAD>, (nchunks + 3) / 4), 128, f);
