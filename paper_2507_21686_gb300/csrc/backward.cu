@@ -280,7 +280,7 @@ sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma, 
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     SPH2D_LAUNCH(c, (tri_pair_fill_kernel), pb, 256, ptri, P, toff, cnt, tq);
     launch_sort_segments(c, toff, tq, M);
-    // vertex gradients, one warp per triangle
+    // vertex gradients: segmented per-triangle sums over the transposed list
     s = ensure(c, c->host_flags_dev, 64);
     if (s != SPH2D_OK) return s;
     BwdArgs a;

@@ -374,8 +374,9 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
 // second piece has support H/2 and is exactly zero for a triangle at distance >= H/2, which
 // holds for most pairs; evaluated in place it would still run on every lane of a warp that
 // holds one near pair.  So: (1) every pair's first piece into a per-pair value buffer, pairs
-// within H/2 appended to a list; (2) the second piece over the compacted list, added to the
-// pair's value; (3) per-particle sums over the per-pair values in pair order (chunk
+// within H/2 appended to a list, FP32 pairs that need the FP64 fix-up to another (both pieces
+// then in FP64 by cubic_fixup_kernel); (2) the second piece over the compacted list, added to
+// the pair's value; (3) per-particle sums over the per-pair values in pair order (chunk
 // reduction and crossing slots as integrals_kernel).  Each pair's value is piece1 + piece2 in
 // that order, so results do not depend on the list order.
 // ---------------------------------------------------------------------------------------
