@@ -177,6 +177,17 @@ def dram_traffic(kernel: str, digest: str) -> dict:
     return {"bytes": k["bytes"], "note": f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {rec.get('command')}"}
 
 
+def culling_report(st, cull_ms, digest):
+    """Cells + cull of one step: grid size, incidences, time and (from the committed ncu
+    capture of the same sources) DRAM bytes and throughput."""
+    out = {"cells": st["n_cells"], "incidences": st["n_candidates"], "ms": cull_ms}
+    t = dram_traffic("cells_and_cull", digest)
+    out["dram_bytes"] = t["bytes"]
+    out["dram_gbs"] = t["bytes"] / (cull_ms * 1e6) if t["bytes"] else None
+    out["traffic_note"] = t["note"]
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -469,7 +480,7 @@ def run_ours(args):
         "fixup_pairs_per_step": fix,
         "fixup_rate": fix / max(P, 1),   # of the last pass of the step (cubic spline)
         "case_histogram": case_hist,
-        "culling": {"cells": st["n_cells"], "incidences": st["n_candidates"]},
+        "culling": culling_report(st, cull_ms, B.source_digest()),
         "gamma_grad_only": gamma_grad_only,
         "hybrid": hybrid,
         "fields": fields,
