@@ -39,6 +39,7 @@ def mls_at(kernel, H, xs, vol, p, b):
     if not np.any(m):
         return 0.0
     C = oracle.kernel_C(kernel)
+    vol = np.asarray(vol, dtype=np.float64)               # FP64 weights whatever the input type
     w = np.array([vol[j] * C / (H * H) * oracle.kernel_k(kernel, r[j]) for j in np.nonzero(m)[0]])
     dj = d[m]
     pj = np.asarray(p, dtype=np.float64)[m]

@@ -363,7 +363,10 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   unsigned int hb[5];
   memcpy(hb, c->pinned, sizeof(hb));
   if (hb[4]) return set_err(c, SPH2D_ERR_NONFINITE_INPUT, "non-finite particle or vertex coordinate");
-  if (N == 0 || M == 0) {
+  if (N == 0) {
+    // no particles: an empty grid (the particle grid of the MLS pressure is empty too)
+    cl.nx = cl.ny = 0;
+    cl.n_cells = 0;
     e = cudaMemsetAsync(c->pair_off.ptr, 0, size_t(N + 1) * sizeof(int64_t), st);
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     cl.built = true;
@@ -395,6 +398,14 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   cl.ny = g.ny;
   const int64_t C = int64_t(g.nx) * g.ny;
   cl.n_cells = C;
+
+  if (M == 0) {
+    // no triangles: no pairs; the grid above still serves the particle grid of the MLS pressure
+    e = cudaMemsetAsync(c->pair_off.ptr, 0, size_t(N + 1) * sizeof(int64_t), st);
+    if (e != cudaSuccess) return cuda_err(c, e, "memset");
+    cl.built = true;
+    return SPH2D_OK;
+  }
 
   // ---- 2. bin triangles
   s = ensure(c, c->cell_cursor, size_t(C) * sizeof(unsigned long long));
