@@ -7,8 +7,11 @@
 //   3. cull: every particle tests the triangles of its own cell.  A conservative FP32 test
 //      decides clear cases; pairs near the threshold (or with far-away geometry) use the
 //      exact FP64 predicate whose operation order is fixed in include/sph2d.h, so the pair
-//      list is bit-identical to an independent FP64 evaluation.  Two passes (count, fill)
-//      produce a particle-major CSR list, ascending triangle id within each particle.
+//      list is bit-identical to an independent FP64 evaluation.  One pass writes each
+//      particle's kept triangles, compacted, into a scratch segment sized by its candidate
+//      count (the total is known from particles per cell x list lengths at the binning
+//      readback); a scan of the kept counts and a copy give the particle-major CSR list,
+//      ascending triangle id within each particle.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -282,34 +285,75 @@ struct CullArgs {
   float Hf, H2lo, H2hi;
 };
 
-template <bool FILL>
+// particles per cell (for the candidate total of the single-pass cull)
+__global__ void part_cell_count_kernel(Grid g, const float4* __restrict__ parts, int64_t N,
+                                       unsigned long long* __restrict__ npart) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 p = parts[i];
+  atomicAdd(npart + particle_cell(g, p.x, p.y), 1ull);
+}
+
+// sum over cells of (particles in the cell) x (triangles in its list): the scratch size of the
+// cull's candidate lists
+__global__ void cand_total_kernel(const unsigned long long* __restrict__ npart,
+                                  const int64_t* __restrict__ cell_start, int64_t C,
+                                  unsigned long long* __restrict__ total) {
+  unsigned long long acc = 0;
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += int64_t(gridDim.x) * blockDim.x)
+    acc += npart[c] * (unsigned long long)(cell_start[c + 1] - cell_start[c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+// candidates of each particle: the length of its cell's triangle list
+__global__ void cand_count_kernel(Grid g, const float4* __restrict__ parts, int64_t N,
+                                  const int64_t* __restrict__ cell_start, int64_t* __restrict__ cand) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 p = parts[i];
+  const int64_t c = particle_cell(g, p.x, p.y);
+  cand[i] = cell_start[c + 1] - cell_start[c];
+}
+
+// the pair predicate over each particle's candidates, once: the kept triangles (ascending id,
+// the cell list's order) go compacted to the particle's scratch segment, their number to counts
 __global__ void cull_kernel(CullArgs a, const float4* __restrict__ parts, int64_t N,
                             const float* __restrict__ tris, const int64_t* __restrict__ cell_start,
-                            const int32_t* __restrict__ cell_tris, int64_t* __restrict__ counts,
-                            const int64_t* __restrict__ pair_off, int32_t* __restrict__ pair_tri,
-                            int32_t* __restrict__ pair_pid) {
+                            const int32_t* __restrict__ cell_tris, const int64_t* __restrict__ cand_off,
+                            int32_t* __restrict__ kept, int64_t* __restrict__ counts) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float4 p = parts[i];
   const int64_t c = particle_cell(a.g, p.x, p.y);
   const int64_t s = cell_start[c], e = cell_start[c + 1];
-  int64_t n = 0, w = FILL ? pair_off[i] : 0;
+  int32_t* out = kept + cand_off[i];
+  int64_t n = 0;
   for (int64_t k = s; k < e; ++k) {
     const int32_t t = __ldg(cell_tris + k);
     const float* tp = tris + 6 * int64_t(t);
     int r = keep_screen(p.x, p.y, tp, a.Hf, a.H2lo, a.H2hi);
     if (r < 0) r = keep_exact(double(p.x), double(p.y), tp, a.H2) ? 1 : 0;
-    if (r) {
-      if (FILL) {
-        pair_tri[w] = t;
-        pair_pid[w] = int32_t(i);
-        ++w;
-      } else {
-        ++n;
-      }
-    }
+    if (r) out[n++] = t;
   }
-  if (!FILL) counts[i] = n;
+  counts[i] = n;
+}
+
+// the compacted lists into the particle-major pair list
+__global__ void pair_copy_kernel(int64_t N, const int64_t* __restrict__ cand_off, const int32_t* __restrict__ kept,
+                                 const int64_t* __restrict__ pair_off, int32_t* __restrict__ pair_tri,
+                                 int32_t* __restrict__ pair_pid) {
+  // one warp per particle, lanes over its pairs
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  const int64_t s0 = pair_off[i], n = pair_off[i + 1] - s0;
+  const int32_t* src = kept + cand_off[i];
+  for (int64_t k = lane; k < n; k += 32) {
+    pair_tri[s0 + k] = src[k];
+    pair_pid[s0 + k] = int32_t(i);
+  }
 }
 
 // sort the int32 segments data[start[i] .. start[i+1]) ascending (used for cell lists and,
@@ -413,20 +457,35 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   if (s != SPH2D_OK) return s;
   auto* ccount = static_cast<unsigned long long*>(c->cell_cursor.ptr);
   auto* cstart = static_cast<int64_t*>(c->cell_start.ptr);
+  // particles per cell and the candidate total, read back with the incidence count
+  s = ensure(c, c->part_cursor, size_t(C) * sizeof(unsigned long long) + 64);
+  if (s != SPH2D_OK) return s;
+  auto* npart = static_cast<unsigned long long*>(c->part_cursor.ptr);
+  auto* cand_total = npart + C;
   e = cudaMemsetAsync(ccount, 0, size_t(C) * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(npart, 0, size_t(C) * sizeof(unsigned long long) + 64, st);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   const unsigned tblocks = unsigned((M + kBlock - 1) / kBlock);
+  const unsigned pblocks = unsigned((N + kBlock - 1) / kBlock);
+  const float4* parts4 = reinterpret_cast<const float4*>(particles);
   SPH2D_LAUNCH(c, (tri_count_kernel), tblocks, kBlock, g, tris, M, ccount);
+  SPH2D_LAUNCH(c, (part_cell_count_kernel), pblocks, kBlock, g, parts4, N, npart);
   s = exclusive_scan_i64(c, reinterpret_cast<const int64_t*>(ccount), cstart, C);
   if (s != SPH2D_OK) return s;
+  {
+    const int64_t want = (C + kBlock - 1) / kBlock;
+    SPH2D_LAUNCH(c, (cand_total_kernel), unsigned(want < 1024 ? (want > 0 ? want : 1) : 1024), kBlock, npart, cstart,
+                 C, cand_total);
+  }
   e = cudaMemcpyAsync(c->pinned, cstart + C, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->pinned + 1, cand_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_err(c, e, "triangle binning");
-  const int64_t n_incid = c->pinned[0];
+  const int64_t n_incid = c->pinned[0], n_cand = c->pinned[1];
   cl.n_incid = n_incid;
   c->stats.n_cells = C;
   c->stats.n_candidates = n_incid;
-  s = ensure(c, c->cell_tris, size_t(n_incid) * sizeof(int32_t));
+  s = ensure(c, c->cell_tris, size_t(n_incid > 0 ? n_incid : 1) * sizeof(int32_t));
   if (s != SPH2D_OK) return s;
   e = cudaMemsetAsync(ccount, 0, size_t(C) * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
@@ -437,7 +496,7 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
     SPH2D_LAUNCH(c, (sort_cells_kernel), blocks, 256, cstart, ctris, C);
   }
 
-  // ---- 3. cull: count, scan, fill
+  // ---- 3. cull: each particle's candidates once into a scratch segment, then scan and copy
   CullArgs a;
   a.g = g;
   a.H2 = H * H;
@@ -446,13 +505,17 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   a.H2lo = H2f * (1.0f - 1.0f / 1024.0f);
   a.H2hi = H2f * (1.0f + 1.0f / 1024.0f);
   s = ensure(c, c->counts, size_t(N) * sizeof(int64_t));
+  if (s == SPH2D_OK) s = ensure(c, c->cand_off, size_t(N + 1) * sizeof(int64_t));
+  if (s == SPH2D_OK) s = ensure(c, c->cand_kept, size_t(n_cand > 0 ? n_cand : 1) * sizeof(int32_t));
   if (s != SPH2D_OK) return s;
   auto* cnt = static_cast<int64_t*>(c->counts.ptr);
+  auto* coff = static_cast<int64_t*>(c->cand_off.ptr);
+  auto* kept = static_cast<int32_t*>(c->cand_kept.ptr);
   auto* poff = static_cast<int64_t*>(c->pair_off.ptr);
-  const unsigned pblocks = unsigned((N + kBlock - 1) / kBlock);
-  const float4* parts4 = reinterpret_cast<const float4*>(particles);
-  SPH2D_LAUNCH(c, (cull_kernel<false>), pblocks, kBlock, a, parts4, N, tris, cstart, ctris, cnt, nullptr,
-                                                  nullptr, nullptr);
+  SPH2D_LAUNCH(c, (cand_count_kernel), pblocks, kBlock, g, parts4, N, cstart, cnt);
+  s = exclusive_scan_i64(c, cnt, coff, N);
+  if (s != SPH2D_OK) return s;
+  SPH2D_LAUNCH(c, (cull_kernel), pblocks, kBlock, a, parts4, N, tris, cstart, ctris, coff, kept, cnt);
   s = exclusive_scan_i64(c, cnt, poff, N);
   if (s != SPH2D_OK) return s;
   e = cudaMemcpyAsync(c->pinned, poff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
@@ -461,12 +524,14 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   const int64_t P = c->pinned[0];
   if (P > (int64_t(1) << 31) - 64)
     return set_err(c, SPH2D_ERR_UNSUPPORTED, "more than 2^31 pairs in one call");
-  s = ensure(c, c->pair_tri, size_t(P) * sizeof(int32_t));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_pid, size_t(P) * sizeof(int32_t));
+  s = ensure(c, c->pair_tri, size_t(P > 0 ? P : 1) * sizeof(int32_t));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_pid, size_t(P > 0 ? P : 1) * sizeof(int32_t));
   if (s != SPH2D_OK) return s;
-  SPH2D_LAUNCH(c, (cull_kernel<true>), pblocks, kBlock, a, parts4, N, tris, cstart, ctris, nullptr, poff,
-                                                 static_cast<int32_t*>(c->pair_tri.ptr),
-                                                 static_cast<int32_t*>(c->pair_pid.ptr));
+  {
+    const int64_t threads = N * 32;
+    SPH2D_LAUNCH(c, (pair_copy_kernel), unsigned((threads + kBlock - 1) / kBlock), kBlock, N, coff, kept, poff,
+                 static_cast<int32_t*>(c->pair_tri.ptr), static_cast<int32_t*>(c->pair_pid.ptr));
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "cull launch");
   cl.P = P;

@@ -46,6 +46,8 @@ struct Ctx {
   DevBuf sur_prm, sur_split, sur_act, sur_data, sur_idx, sur_vals, sur_fb;
   // boundary pressure coupling: particle grid (cell starts, cursors, ids) and scratch
   DevBuf part_start, part_cursor, part_ids, pres_vertex, pres_tmp;
+  // single-pass cull: per-particle candidate offsets and the compacted kept triangles
+  DevBuf cand_off, cand_kept;
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
   bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
   bool fallback_pending = false;  // pinned[10] holds the fallback count of the last surrogate call
