@@ -275,15 +275,6 @@ __global__ void __launch_bounds__(128) field_p_sum_kernel(FieldArgs f, const flo
   }
 }
 
-template <typename K>
-static unsigned field_p_blocks(Ctx* c, K kern, int64_t wanted) {
-  int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
-}
-
 template <int KID, int ORDER, bool GRAD>
 static sph2d_status run_fields_p(Ctx* c, int mode, FieldArgs f) {
   constexpr int NV = 3 * kMaxFields;
@@ -298,7 +289,7 @@ static sph2d_status run_fields_p(Ctx* c, int mode, FieldArgs f) {
     if (e0 != cudaSuccess) return cuda_err(c, e0, "memset");
     if (f.a.P > 0)
       SPH2D_LAUNCH(c, (field_p_kernel<KID, ORDER, GRAD>),
-                   field_p_blocks(c, field_p_kernel<KID, ORDER, GRAD>, (nchunks + 3) / 4), 128, f);
+                   resident_blocks(c, field_p_kernel<KID, ORDER, GRAD>, (nchunks + 3) / 4), 128, f);
     if (f.a.N > 0) SPH2D_LAUNCH(c, (field_finalize_kernel<double>), unsigned((f.a.N + 255) / 256), 256, f);
   } else {
     const int64_t cap = f.a.P > 0 ? f.a.P : 1;
@@ -318,11 +309,11 @@ static sph2d_status run_fields_p(Ctx* c, int mode, FieldArgs f) {
       fq.a.work = count + 4;
       fl.a.work = count + 5;
       SPH2D_LAUNCH(c, (field_p_quad_kernel<KID, ORDER, GRAD>),
-                   field_p_blocks(c, field_p_quad_kernel<KID, ORDER, GRAD>, blocks), 128, fq, quad_rule(), vals, list,
+                   resident_blocks(c, field_p_quad_kernel<KID, ORDER, GRAD>, blocks), 128, fq, quad_rule(), vals, list,
                    count);
       SPH2D_LAUNCH(c, (field_p_list_kernel<KID, ORDER, GRAD>),
-                   field_p_blocks(c, field_p_list_kernel<KID, ORDER, GRAD>, blocks), 128, fl, vals, list, count);
-      SPH2D_LAUNCH(c, field_p_sum_kernel, field_p_blocks(c, field_p_sum_kernel, (nchunks + 3) / 4), 128, f, vals);
+                   resident_blocks(c, field_p_list_kernel<KID, ORDER, GRAD>, blocks), 128, fl, vals, list, count);
+      SPH2D_LAUNCH(c, field_p_sum_kernel, resident_blocks(c, field_p_sum_kernel, (nchunks + 3) / 4), 128, f, vals);
     }
     if (f.a.N > 0) SPH2D_LAUNCH(c, (field_finalize_kernel<float>), unsigned((f.a.N + 255) / 256), 256, f);
     e = cudaMemcpyAsync(c->pinned + 10, count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);

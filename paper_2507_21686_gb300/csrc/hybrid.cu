@@ -165,15 +165,6 @@ __global__ void __launch_bounds__(128, int_minb<float>()) hybrid_second_kernel(I
   if (fixes) atomicAdd(a.nfix, fixes);
 }
 
-template <typename K>
-static unsigned blocks_for(Ctx* c, K kern, int64_t wanted) {
-  int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
-}
-
 template <int KID, int MD>
 static sph2d_status run_hybrid(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
@@ -198,22 +189,22 @@ static sph2d_status run_hybrid(Ctx* c, IntArgs a) {
     aq.work = count + 4;
     al.work = count + 5;
     a2.work = count + 6;
-    SPH2D_LAUNCH(c, (hybrid_first_kernel<KID, MD>), blocks_for(c, hybrid_first_kernel<KID, MD>, blocks), 128, aq,
+    SPH2D_LAUNCH(c, (hybrid_first_kernel<KID, MD>), resident_blocks(c, hybrid_first_kernel<KID, MD>, blocks), 128, aq,
                  quad_rule(), vals, list, count, near, count + 1);
     if constexpr (KID == KID_CUBIC) {
       // the cubic spline's pieces over the list, as its closed-form path (the second piece also
       // for the quadrature pairs already in near)
-      SPH2D_LAUNCH(c, (cubic_first_kernel<float, MD>), blocks_for(c, cubic_first_kernel<float, MD>, blocks), 128,
+      SPH2D_LAUNCH(c, (cubic_first_kernel<float, MD>), resident_blocks(c, cubic_first_kernel<float, MD>, blocks), 128,
                    al, vals, list, count, near, count + 1, fix_list, count + 2);
-      SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), blocks_for(c, cubic_fixup_kernel<MD>, blocks), 128, a, vals,
+      SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), resident_blocks(c, cubic_fixup_kernel<MD>, blocks), 128, a, vals,
                    fix_list, count + 2);
-      SPH2D_LAUNCH(c, (cubic_second_kernel<float, MD>), blocks_for(c, cubic_second_kernel<float, MD>, blocks), 128,
+      SPH2D_LAUNCH(c, (cubic_second_kernel<float, MD>), resident_blocks(c, cubic_second_kernel<float, MD>, blocks), 128,
                    a2, vals, near, count + 1);
     } else {
-      SPH2D_LAUNCH(c, (hybrid_second_kernel<KID, MD>), blocks_for(c, hybrid_second_kernel<KID, MD>, blocks), 128, al,
+      SPH2D_LAUNCH(c, (hybrid_second_kernel<KID, MD>), resident_blocks(c, hybrid_second_kernel<KID, MD>, blocks), 128, al,
                    vals, list, count);
     }
-    SPH2D_LAUNCH(c, (reduce_pairs_kernel<float, MD>), blocks_for(c, reduce_pairs_kernel<float, MD>, (nchunks + 3) / 4),
+    SPH2D_LAUNCH(c, (reduce_pairs_kernel<float, MD>), resident_blocks(c, reduce_pairs_kernel<float, MD>, (nchunks + 3) / 4),
                  128, a, vals);
   }
   if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<float, MD>), unsigned((a.N + 255) / 256), 256, a);

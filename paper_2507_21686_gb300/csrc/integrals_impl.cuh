@@ -441,7 +441,7 @@ __device__ __forceinline__ bool cubic_first_pair(const IntArgs& a, int64_t q, OT
   const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
   OT* out = vals + q * NV;
   need = false;
-  if (sizeof(OT) == sizeof(float)) {
+  if constexpr (sizeof(OT) == sizeof(float)) {
     const float ih = float(a.invH);
     float lf[6];
     bool ok = true;
@@ -470,24 +470,25 @@ __device__ __forceinline__ bool cubic_first_pair(const IntArgs& a, int64_t q, OT
 #pragma unroll
     for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
     return false;
-  }
-  double ld[6], w[13];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-    ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-  }
-  const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-  if (s == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) w[i] = 0.0;
   } else {
-    cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
-    need = near_half<double>(ld);
-  }
+    double ld[6], w[13];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
-  return false;
+    for (int j = 0; j < 3; ++j) {
+      ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+      ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+    }
+    const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+    if (s == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) w[i] = 0.0;
+    } else {
+      cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
+      need = near_half<double>(ld);
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
+    return false;
+  }
 }
 
 // the FP64 fix-up of the FP32 pairs cubic_first_kernel listed: both pieces of each pair

@@ -754,7 +754,7 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
 template <typename R, class P, int MD, bool UNROLL_FANS>
 SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   R x0 = ax, y0 = ay, x1 = bx, y1 = by, x2 = cx, y2 = cy;
-  if (UNROLL_FANS) {
+  if constexpr (UNROLL_FANS) {
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       add_fan<R, P, MD>(x0, y0, x1, y1, o);
@@ -766,18 +766,18 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
       x2 = tx;
       y2 = ty;
     }
-    return;
-  }
+  } else {
 #pragma unroll 1
-  for (int e = 0; e < 3; ++e) {
-    add_fan<R, P, MD>(x0, y0, x1, y1, o);
-    const R tx = x0, ty = y0;
-    x0 = x1;
-    y0 = y1;
-    x1 = x2;
-    y1 = y2;
-    x2 = tx;
-    y2 = ty;
+    for (int e = 0; e < 3; ++e) {
+      add_fan<R, P, MD>(x0, y0, x1, y1, o);
+      const R tx = x0, ty = y0;
+      x0 = x1;
+      y0 = y1;
+      x1 = x2;
+      y1 = y2;
+      x2 = tx;
+      y2 = ty;
+    }
   }
 }
 

@@ -338,15 +338,6 @@ __global__ void __launch_bounds__(128) vertex_pressure_kernel(FieldArgs f, Press
   if ((threadIdx.x & 31) == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
 
-template <typename K>
-static unsigned press_blocks(Ctx* c, K kern, int64_t wanted) {
-  int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
-}
-
 template <typename R>
 static sph2d_status mls_points_t(Ctx* c, int kernel, const float* vol, const float* pres, const float* pts,
                                  int64_t Q, void* out) {
@@ -397,10 +388,10 @@ template <typename OT, int KID>
 static sph2d_status launch_pass(Ctx* c, int model, const FieldArgs& f, const PressArgs& pa, const float* pv,
                                 int64_t want) {
   if (model == 1)
-    SPH2D_LAUNCH(c, (vertex_pressure_kernel<OT, KID>), press_blocks(c, vertex_pressure_kernel<OT, KID>, want), 128,
+    SPH2D_LAUNCH(c, (vertex_pressure_kernel<OT, KID>), resident_blocks(c, vertex_pressure_kernel<OT, KID>, want), 128,
                  f, pa, pv);
   else
-    SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID>), press_blocks(c, contact_pressure_kernel<OT, KID>, want), 128,
+    SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID>), resident_blocks(c, contact_pressure_kernel<OT, KID>, want), 128,
                  f, pa);
   return SPH2D_OK;
 }
