@@ -370,15 +370,23 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
 }
 
 // ---------------------------------------------------------------------------------------
-// cubic spline in three launches.  k = 2 (1-q)^3_+ - (1-2q)^3_+ (scaled as in tri_raw): the
-// second piece has support H/2 and is exactly zero for a triangle at distance >= H/2, which
-// holds for most pairs; evaluated in place it would still run on every lane of a warp that
-// holds one near pair.  So: (1) every pair's first piece into a per-pair value buffer, pairs
-// within H/2 appended to a list, FP32 pairs that need the FP64 fix-up to another (both pieces
-// then in FP64 by cubic_fixup_kernel); (2) the second piece over the compacted list, added to
-// the pair's value; (3) per-particle sums over the per-pair values in pair order (chunk
-// reduction and crossing slots as integrals_kernel).  Each pair's value is piece1 + piece2 in
-// that order, so results do not depend on the list order.
+// cubic spline.  k = 2 (1-q)^3_+ - (1-2q)^3_+ (scaled as in tri_raw): the second piece has
+// support H/2 and is exactly zero for a triangle at distance >= H/2, which holds for most pairs;
+// evaluated in place it would still run on every lane of a warp that holds one near pair.
+//
+// Per-particle path (run_cubic): a stable partition of the pair list puts the pairs within H/2
+// of their triangle first and the others after them, each part in pair order.  One chunk kernel
+// runs over the partition: both pieces for a near pair (piece1 + piece2, in that order), the
+// first piece for a far pair, with the segmented sums and crossing slots of integrals_kernel
+// keyed by (particle, part).  The finalize adds each particle's near-part sum and far-part sum
+// in that order.  Every order is fixed, so results are deterministic run to run.
+//
+// Sparse lists (the hybrid mode's closed-form pairs): (1) every listed pair's first piece into a
+// per-pair value buffer, pairs within H/2 appended to a list, FP32 pairs that need the FP64
+// fix-up to another (both pieces then in FP64 by cubic_fixup_kernel); (2) the second piece over
+// the compacted list, added to the pair's value; (3) per-particle sums over the per-pair values
+// in pair order (reduce_pairs_kernel).  Each pair's value is piece1 + piece2 in that order, so
+// results do not depend on the list order.
 // ---------------------------------------------------------------------------------------
 // origin within 1/2 (+ a small margin) of the local triangle: inside, or an edge segment
 // closer than that (no division)
@@ -715,6 +723,252 @@ __global__ void finalize_kernel(IntArgs a) {
   write_particle<OT, MD>(a, i, v);
 }
 
+// ---------------------------------------------------------------------------------------
+// cubic spline over the near/far partition of the pair list
+// ---------------------------------------------------------------------------------------
+struct CubicSplit {
+  const uint32_t* mask;    // [nchunks] bit l of word ch: pair 32 ch + l lies within H/2
+  const int64_t* coff;     // [nchunks + 1] near pairs before chunk ch; coff[nchunks] = all
+  const int64_t* order;    // [P] pair at each position of the partition
+  void* part;              // [2][N][NV] sums of a particle's near / far part held in one chunk
+  int64_t nchunks;
+};
+
+// near pairs before pair q (0 <= q <= P)
+__device__ __forceinline__ int64_t near_before(const CubicSplit& s, int64_t q) {
+  const int64_t ch = q >> 5;
+  if (ch >= s.nchunks) return s.coff[s.nchunks];
+  return s.coff[ch] + __popc(s.mask[ch] & ((1u << (q & 31)) - 1u));
+}
+
+// positions [s0, s1) of particle pid's part r (0 near, 1 far) in the partition
+__device__ __forceinline__ void part_range(const IntArgs& a, const CubicSplit& s, int64_t pid, int r,
+                                           int64_t& s0, int64_t& s1) {
+  const int64_t q0 = __ldg(a.pair_off + pid), q1 = __ldg(a.pair_off + pid + 1);
+  const int64_t n0 = near_before(s, q0), n1 = near_before(s, q1);
+  const int64_t pn = s.coff[s.nchunks];
+  s0 = r ? pn + (q0 - n0) : n0;
+  s1 = r ? pn + (q1 - n1) : n1;
+}
+
+// near flags of every 32-pair chunk (one warp per chunk) and their counts
+template <typename OT>
+__global__ void __launch_bounds__(128) cubic_near_mask_kernel(IntArgs a, uint32_t* __restrict__ mask,
+                                                              int64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (a.P + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+    const int64_t q = ch * 32 + lane;
+    bool near = false;
+    if (q < a.P) {
+      const float4 p = a.parts[__ldg(a.pair_pid + q)];
+      const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
+      OT l[6];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if constexpr (sizeof(OT) == sizeof(float)) {
+          l[2 * j] = (__ldg(t + 2 * j) - p.x) * float(a.invH);
+          l[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * float(a.invH);
+        } else {
+          l[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+          l[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+        }
+      }
+      near = near_half<OT>(l);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, near);
+    if (lane == 0) {
+      mask[ch] = m;
+      cnt[ch] = __popc(m);
+    }
+  }
+}
+
+// the partition: near pairs at their near rank, far pairs after all near pairs at their far rank
+static __global__ void __launch_bounds__(128) cubic_partition_kernel(CubicSplit s, int64_t P, int64_t* __restrict__ order) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5, pn = s.coff[s.nchunks];
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < s.nchunks; ch += nw) {
+    const int64_t q = ch * 32 + lane;
+    if (q >= P) continue;
+    const unsigned m = s.mask[ch];
+    const int64_t nb = s.coff[ch] + __popc(m & ((1u << lane) - 1u));
+    order[(m >> lane) & 1u ? nb : pn + (q - nb)] = q;
+  }
+}
+
+// one pair of the partition: the first piece, plus the second for a near pair; FP32 pairs whose
+// coordinates leave the FP32 range or whose result is not finite take the whole kernel in FP64
+// (eval_fixup64, out of line).  Returns 1 for a fix-up.
+template <typename OT, int MD>
+__device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int tid, bool near, OT* v) {
+  constexpr int NV = nv_of(MD);
+  const float4 p = a.parts[pid];
+  const float* t = a.tris + 6 * int64_t(tid);
+  if constexpr (sizeof(OT) == sizeof(float)) {
+    const float ih = float(a.invH);
+    float lf[6];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+      lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+      ok = ok && fabsf(lf[2 * j]) <= kFixupCoordLimit && fabsf(lf[2 * j + 1]) <= kFixupCoordLimit;
+    }
+    if (ok) {
+      const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = 0.0f;
+      if (s == 0) return 0;
+      const int npieces = near ? 2 : 1;
+#pragma unroll 1
+      for (int piece = 0; piece < npieces; ++piece) {
+        float w[13];
+        cubic_piece<float, MD>(lf, piece, s, a.C, a.invH, w);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = piece ? v[i] + w[i] : w[i];
+      }
+#pragma unroll
+      for (int i = 0; i < NV; ++i) ok = ok && isfinite(v[i]);
+      if (ok) return 0;
+    }
+    eval_fixup64<KID_CUBIC, MD>(p, t, a.invH, a.C, v);
+    return 1;
+  } else {
+    double ld[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+      ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+    }
+    const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = 0.0;
+    if (s == 0) return 0;
+    const int npieces = near ? 2 : 1;
+#pragma unroll 1
+    for (int piece = 0; piece < npieces; ++piece) {
+      double w[13];
+      cubic_piece<double, MD>(ld, piece, s, a.C, a.invH, w);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = piece ? v[i] + w[i] : w[i];
+    }
+    return 0;
+  }
+}
+
+// chunks of 32 positions of the partition; segmented sums keyed by 2 pid + part
+// With all ten moments the cubic spline's pair code spills at 128 registers (~100 B per thread:
+// both pieces and the keyed sums); 3 resident blocks per SM (<= 168 registers, 12 warps) measured
+// 6% faster for it, while the Wendland kernels lose ~30% at that cap.
+template <typename OT, int MD> constexpr int cubic_split_minb() {
+  return sizeof(OT) == sizeof(float) && MD >= 3 ? 3 : int_minb<OT>();
+}
+
+template <typename OT, int MD>
+__global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_split_kernel(IntArgs a, CubicSplit sp) {
+  constexpr int NV = nv_of(MD);
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t pn = sp.coff[sp.nchunks];
+  unsigned long long fixes = 0;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t i = ch * 32 + lane;
+    bool valid = false;
+    unsigned key = 0;
+    OT v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = OT(0);
+    int fix = 0;
+    if (i < a.P) {
+      const int64_t q = sp.order[i];
+      const int pid = __ldg(a.pair_pid + q);
+      const bool near = i < pn;
+      valid = true;
+      key = 2u * unsigned(pid) + (near ? 0u : 1u);
+      fix = cubic_split_pair<OT, MD>(a, pid, __ldg(a.pair_tri + q), near, v);
+    }
+    fixes += __popc(__ballot_sync(0xffffffffu, fix));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned kn = __shfl_down_sync(0xffffffffu, key, o);
+      const bool same = (lane + o < 32) && (kn == key);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const OT t = __shfl_down_sync(0xffffffffu, v[k], o);
+        if (same) v[k] += t;
+      }
+    }
+    const unsigned kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = valid && (lane == 0 || kprev != key);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int last_head = 31 - __clz(heads);
+    if (head) {
+      const int64_t cs = ch * 32, pid = key >> 1;
+      const int r = key & 1u;
+      int64_t s0, s1;
+      part_range(a, sp, pid, r, s0, s1);
+      if (s0 >= cs && s1 <= cs + 32) {
+        OT* w = static_cast<OT*>(sp.part) + (int64_t(r) * a.N + pid) * NV;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = v[k];
+      }
+      OT* slots = static_cast<OT*>(a.slots);
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) slots[(ch * 2) * NV + k] = v[k];
+      }
+      if (lane == last_head) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) slots[(ch * 2 + 1) * NV + k] = v[k];
+      }
+    }
+    ch = chunk_next(a.work, ch, nw, nx);
+  }
+  if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
+}
+
+// per particle: near-part sum + far-part sum, each from its chunk or its crossing slots
+template <typename OT, int MD>
+__global__ void cubic_split_finalize_kernel(IntArgs a, CubicSplit sp) {
+  constexpr int NV = nv_of(MD);
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  OT v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = OT(0);
+  if (a.pair_off[i + 1] > a.pair_off[i]) {
+    const OT* slots = static_cast<const OT*>(a.slots);
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+      int64_t s0, s1;
+      part_range(a, sp, i, r, s0, s1);
+      if (s1 <= s0) continue;
+      OT w[NV];
+      const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
+      if (c0 == c1) {
+        const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = src[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = slots[(c0 * 2 + 1) * NV + k];
+        for (int64_t c = c0 + 1; c < c1; ++c) {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) w[k] += slots[(c * 2) * NV + k];
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] += slots[(c1 * 2) * NV + k];
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] = r ? v[k] + w[k] : w[k];
+    }
+  }
+  write_particle<OT, MD>(a, i, v);
+}
+
 // independent pairs: [P][8] doubles -> [P][3+nm]
 template <typename OT, int KID, int MD>
 __global__ void __launch_bounds__(256) pair_entry_kernel(const double* __restrict__ pairs, int64_t P,
@@ -765,36 +1019,36 @@ template <typename OT, int MD>
 static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
   const int64_t nchunks = (a.P + 31) >> 5;
-  const int64_t cap = a.P > 0 ? a.P : 1;
+  // scratch: header (chunk counter at [4]) | order [P] | counts [nchunks + 1] | offsets
+  // [nchunks + 1] | masks [nchunks]
+  const size_t list_bytes = 64 + size_t(a.P + 2 * (nchunks + 1)) * sizeof(int64_t) + size_t(nchunks + 1) * 4;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(cap) * NV * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, size_t(cap) * 2 * sizeof(int64_t) + 64);
+  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(2 * (a.N > 0 ? a.N : 1)) * NV * sizeof(OT));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, list_bytes);
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
-  OT* vals = static_cast<OT*>(c->pair_vals.ptr);
-  // header: count of the near list [0] and of the fix-up list [2]; lists from byte 64
   auto* hdr = static_cast<unsigned long long*>(c->pair_list2.ptr);
-  int64_t* list = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
-  int64_t* fix_list = list + cap;
-  cudaError_t e = cudaMemsetAsync(hdr, 0, 64, c->stream);
-  if (e != cudaSuccess) return cuda_err(c, e, "memset");
+  int64_t* order = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
+  int64_t* cnt = order + a.P;
+  int64_t* coff = cnt + (nchunks + 1);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(coff + (nchunks + 1));
+  CubicSplit sp{mask, coff, order, c->pair_vals.ptr, nchunks};
   if (a.P > 0) {
-    const int64_t blocks = (a.P + 127) / 128;
-    IntArgs a1 = a, a2 = a;
-    a1.work = hdr + 4;                                 // chunk counters (zeroed with the header)
-    a2.work = hdr + 5;
-    SPH2D_LAUNCH(c, (cubic_first_kernel<OT, MD>), resident_blocks(c, cubic_first_kernel<OT, MD>, blocks), 128,
-                 a1, vals, nullptr, nullptr, list, hdr, fix_list, hdr + 2);
-    if (sizeof(OT) == sizeof(float))
-      SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), resident_blocks(c, cubic_fixup_kernel<MD>, blocks), 128, a,
-                   reinterpret_cast<float*>(vals), fix_list, hdr + 2);
-    SPH2D_LAUNCH(c, (cubic_second_kernel<OT, MD>), resident_blocks(c, cubic_second_kernel<OT, MD>, blocks), 128,
-                 a2, vals, list, hdr);
-    SPH2D_LAUNCH(c, (reduce_pairs_kernel<OT, MD>), resident_blocks(c, reduce_pairs_kernel<OT, MD>, (nchunks + 3) / 4),
-                 128, a, vals);
+    cudaError_t e = cudaMemsetAsync(hdr, 0, 64, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "memset");
+    a.work = hdr + 4;
+    const unsigned gb = resident_blocks(c, cubic_near_mask_kernel<OT>, (nchunks + 3) / 4);
+    SPH2D_LAUNCH(c, (cubic_near_mask_kernel<OT>), gb, 128, a, mask, cnt);
+    s = exclusive_scan_i64(c, cnt, coff, nchunks);
+    if (s != SPH2D_OK) return s;
+    SPH2D_LAUNCH(c, (cubic_partition_kernel), resident_blocks(c, cubic_partition_kernel, (nchunks + 3) / 4), 128,
+                 sp, a.P, order);
+    SPH2D_LAUNCH(c, (cubic_split_kernel<OT, MD>),
+                 resident_blocks(c, cubic_split_kernel<OT, MD>, (nchunks + 3) / 4), 128, a, sp);
   }
-  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a);
-  e = cudaGetLastError();
+  if (a.N > 0)
+    SPH2D_LAUNCH(c, (cubic_split_finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a, sp);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
   return SPH2D_OK;
 }

@@ -266,9 +266,12 @@ def test_orientation_and_degenerate_triangles(ctx):
         assert np.all(mo.cpu().numpy() == 0)
 
 
-def test_deterministic_bitwise(ctx):
+@pytest.mark.parametrize("kernel", ["wendland_c2", "cubic_spline"])
+def test_deterministic_bitwise(ctx, kernel):
+    """repeated calls give identical bits (dynamic chunk scheduling; for the cubic spline also
+    its near/far partition)"""
     w = W.box_obstacle(n=128)
-    r = [ctx.boundary_integrals(_t(w.particles), _t(w.triangles), "wendland_c2", w.H, 3, m)
+    r = [ctx.boundary_integrals(_t(w.particles), _t(w.triangles), kernel, w.H, 3, m)
          for m in ("fp32_fixup", "fp32_fixup", "fp64", "fp64")]
     for i in (0, 2):
         for x, y in zip(r[i], r[i + 1]):
