@@ -15,10 +15,13 @@
 // otherwise left to the closed form of that piece alone.  On the box benchmark this covers
 // most pairs at a fifth of the closed form's arithmetic.
 //
-// Three launches, as the cubic spline's path: quadrature for eligible pairs into a per-pair
-// buffer and a warp-aggregated list of the others; the closed form (FP32 + fix-up) over that
-// list; per-particle sums of the per-pair values in pair order (deterministic).  The cubic
-// spline's closed form takes its two launches over the list (second piece only within H/2).
+// Launch structure: the pair list is partitioned (stable, in pair order within each region)
+// into region 0, the pairs left to the closed form (FP32 + FP64 fix-up); region 1, the cubic
+// spline's near pairs whose second piece the finer rule takes in the doubled frame; region 2,
+// the other quadrature pairs.  A class pass stores each pair's region, apex and inner flag; a
+// scan and the partition pass order the pairs; two chunk kernels evaluate the positions, the
+// closed form over the leading chunks and the quadrature over the rest, summing per (particle,
+// region); the finalize adds the region sums in region order (deterministic).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,13 +33,14 @@ namespace sph2d {
 
 // quadrature of one pair -> v (gamma, grad, moments), world-scaled like eval_local.
 // Conical product with the apex at vertex `apex`: p = v0 + s d(t), d(t) = (v1 - v0) + t (v2 - v1),
-// Jacobian s |(v1 - v0) x (v2 - v0)|; along each ray s runs to min(1, s+), s+ the exit from
-// the unit disk (|v0| < 1), taken as -c / (b + sqrt(b^2 - a c)) with a = |d|^2, b = v0 . d,
-// c = |v0|^2 - 1 (no cancellation: b + sqrt(.) > 0 whenever c < 0).
-template <int KID, int MD>
-__device__ __forceinline__ void quad_pair(const QuadRule& qr, const float* vin, const QuadClass& qc, double C,
-                                          double invH, float* out) {
-  const int i0 = qc.apex, i1 = i0 == 2 ? 0 : i0 + 1, i2 = i1 == 2 ? 0 : i1 + 1;
+// Jacobian s |(v1 - v0) x (v2 - v0)|; rays t from the rule rt, s from the 6-node rule qs; along
+// each ray s runs to min(1, s+), s+ the exit from the unit disk (|v0| < 1), taken as
+// -c / (b + sqrt(b^2 - a c)) with a = |d|^2, b = v0 . d, c = |v0|^2 - 1 (no cancellation:
+// b + sqrt(.) > 0 whenever c < 0).
+template <int KID, int MD, class RT>
+__device__ __forceinline__ void quad_pair(const RT& rt, const QuadRule& qs, const float* vin, int apex, bool inner,
+                                          double C, double invH, float* out) {
+  const int i0 = apex, i1 = i0 == 2 ? 0 : i0 + 1, i2 = i1 == 2 ? 0 : i1 + 1;
   const float v0x = vin[2 * i0], v0y = vin[2 * i0 + 1];
   const float e1x = vin[2 * i1] - v0x, e1y = vin[2 * i1 + 1] - v0y;
   const float e2x = vin[2 * i2] - vin[2 * i1], e2y = vin[2 * i2 + 1] - vin[2 * i1 + 1];
@@ -45,20 +49,20 @@ __device__ __forceinline__ void quad_pair(const QuadRule& qr, const float* vin, 
   float g = 0.0f, gx = 0.0f, gy = 0.0f;
   float m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 2
-  for (int j = 0; j < kQuadN; ++j) {
-    const float dx = e1x + qr.u[j] * e2x, dy = e1y + qr.u[j] * e2y;
+  for (int j = 0; j < RT::N; ++j) {
+    const float dx = e1x + rt.u[j] * e2x, dy = e1y + rt.u[j] * e2y;
     const float aa = dx * dx + dy * dy, bb = v0x * dx + v0y * dy;
     const float sp = -c0 / (bb + sqrtf(fmaxf(bb * bb - aa * c0, 0.0f)));
     const float ss = fminf(1.0f, sp);
-    const float wj = qr.w[j] * ss * ss;
+    const float wj = rt.w[j] * ss * ss;
 #pragma unroll
     for (int i = 0; i < kQuadN; ++i) {
-      const float s = ss * qr.u[i];
+      const float s = ss * qs.u[i];
       const float px = v0x + s * dx, py = v0y + s * dy;
       const float r = sqrtf(px * px + py * py);
       float k, kd;
-      kernel_and_slope<KID>(r, qc.inner, k, kd);
-      const float w = wj * qr.wu[i];
+      kernel_and_slope<KID>(r, inner, k, kd);
+      const float w = wj * qs.wu[i];
       const float wk = w * k, wd = w * kd;
       g += wk;
       gx += wd * px;
@@ -94,25 +98,17 @@ __device__ __forceinline__ void quad_pair(const QuadRule& qr, const float* vin, 
   }
 }
 
-// quadrature for the pairs that qualify into vals; the others appended to list (closed form);
-// cubic spline: quadrature pairs within 1/2 of the particle (not inside r < 1/2) appended to
-// near, for the second piece in closed form
-template <int KID, int MD>
-__global__ void __launch_bounds__(128, int_minb<float>()) hybrid_first_kernel(IntArgs a, QuadRule qr,
-                                                                              float* __restrict__ vals,
-                                                                              int64_t* __restrict__ list,
-                                                                              unsigned long long* __restrict__ count,
-                                                                              int64_t* __restrict__ near,
-                                                                              unsigned long long* __restrict__ near_count) {
-  constexpr int NV = nv_of(MD);
+// region of each pair (0 closed form, 1 cubic near pair with its second piece by the finer
+// rule, 2 quadrature) into the partition masks; class byte: apex | inner << 2
+template <int KID>
+__global__ void __launch_bounds__(128) hybrid_class_kernel(IntArgs a, PairSplit sp, uint32_t* __restrict__ mask,
+                                                           int64_t* __restrict__ cnt, uint8_t* __restrict__ cls) {
   const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const float ih = float(a.invH);
-  const int64_t nchunks = (a.P + 31) >> 5, nw = stride >> 5;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
-    const unsigned long long nx = chunk_prefetch(a.work);
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < sp.nchunks; ch += nw) {
     const int64_t q = ch * 32 + lane;
-    bool analytic = false, piece2 = false;
+    int region = -1;
     if (q < a.P) {
       const float4 p = a.parts[__ldg(a.pair_pid + q)];
       const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
@@ -123,93 +119,149 @@ __global__ void __launch_bounds__(128, int_minb<float>()) hybrid_first_kernel(In
         v[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
       }
       const QuadClass qc = quad_classify<KID>(v);
-      if (qc.quad) {
-        float w[13];
-        quad_pair<KID, MD>(qr, v, qc, a.C, a.invH, w);
-        float* o = vals + q * NV;
-#pragma unroll
-        for (int i = 0; i < NV; ++i) o[i] = w[i];
-        piece2 = qc.near;
-      } else {
-        analytic = true;
-      }
+      region = !qc.quad ? 0 : (qc.near ? (qc.half ? 1 : 0) : 2);
+      cls[q] = uint8_t(qc.apex | (qc.inner ? 4 : 0));
     }
-    warp_append(analytic, q, list, count);
-    if (KID == KID_CUBIC) warp_append(piece2, q, near, near_count);
-    ch = chunk_next(a.work, ch, nw, nx);
+    store_region_masks(mask, cnt, sp.nchunks, 3, ch, region);
   }
 }
 
-// the closed form (FP32 + FP64 fix-up) over the list
-template <int KID, int MD>
-__global__ void __launch_bounds__(128, int_minb<float>()) hybrid_second_kernel(IntArgs a, float* __restrict__ vals,
-                                                                               const int64_t* __restrict__ list,
-                                                                               const unsigned long long* __restrict__ count) {
-  constexpr int NV = nv_of(MD);
-  const int64_t n = int64_t(*count);
-  const int64_t nchunks = (n + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long fixes = 0;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
-    const unsigned long long nx = chunk_prefetch(a.work);
-    const int64_t i = ch * 32 + (threadIdx.x & 31);
-    if (i < n) {
-      const int64_t q = list[i];
-      float v[NV];
-      fixes += eval_pair<float, KID, MD>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
-      float* o = vals + q * NV;
+// the cubic spline's second piece of a near pair by the finer rule in the doubled frame, added
+// to v: there the piece is (1 - r')^3_+, half the first piece's form 2 (1 - r)^3 that the rule
+// evaluates; mapped back with the weights of Sec. 2's piecewise split (2^-(m+2) for a moment
+// of degree m, -1/2 for the gradient), each halved
+template <int MD>
+__device__ __forceinline__ void add_second_piece(const QuadRaysFine& qf, const QuadRule& qs, const float* v6, int apex,
+                                                 double C, double invH, float* v) {
+  float d[6], w[13];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) o[k] = v[k];
-    }
-    ch = chunk_next(a.work, ch, nw, nx);
+  for (int j = 0; j < 6; ++j) d[j] = 2.0f * v6[j];
+  quad_pair<KID_CUBIC, MD>(qf, qs, d, apex, false, C, invH, w);
+  v[0] += -0.125f * w[0];
+  v[1] += -0.25f * w[1];
+  v[2] += -0.25f * w[2];
+  if (MD >= 1) {
+    v[3] += -0.125f * w[3];
+    v[4] += -0.0625f * w[4];
+    v[5] += -0.0625f * w[5];
   }
-  if (fixes) atomicAdd(a.nfix, fixes);
+  if (MD >= 3) {
+#pragma unroll
+    for (int i = 6; i < 9; ++i) v[i] += -0.03125f * w[i];
+#pragma unroll
+    for (int i = 9; i < 13; ++i) v[i] += -0.015625f * w[i];
+  }
+}
+
+// Chunks of 32 positions of the partition.  CLOSED: the chunks up to the one holding the last
+// closed-form position, every lane by the closed form (a boundary chunk's quadrature lanes
+// too: each position is still evaluated once and keyed by its region); else the chunks after
+// them, by quadrature.  Two kernels, so that the quadrature code keeps its own register
+// allocation (~60 registers) and occupancy rather than the closed form's 128-168.
+template <int KID, int MD, bool CLOSED>
+__device__ __forceinline__ void hybrid_chunks(const IntArgs& a, const QuadRule& qr, const QuadRaysFine& qf,
+                                              const PairSplit& sp, const uint8_t* __restrict__ cls) {
+  constexpr int NV = nv_of(MD);
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunks = (a.P + 31) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t b1 = sp.off[sp.nchunks], b2 = sp.off[2 * sp.nchunks];   // first positions of regions 1, 2
+  const int64_t cb = (b1 + 31) >> 5;                                   // chunks holding closed-form positions
+  const int64_t c0 = CLOSED ? 0 : cb, n = CLOSED ? cb : nchunks - cb;
+  const float ih = float(a.invH);
+  unsigned long long fixes = 0;
+  for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < n;) {
+    const unsigned long long nx = chunk_prefetch(a.work);
+    const int64_t ch = c0 + j;
+    const int64_t i = ch * 32 + lane;
+    bool valid = false;
+    unsigned long long key = 0;
+    float v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0f;
+    int fix = 0;
+    if (i < a.P) {
+      const int64_t q = sp.order[i];
+      const int pid = __ldg(a.pair_pid + q), tid = __ldg(a.pair_tri + q);
+      const int r = i < b1 ? 0 : (i < b2 ? 1 : 2);
+      valid = true;
+      key = 3ull * unsigned(pid) + unsigned(r);
+      const float4 p = a.parts[pid];
+      const float* t = a.tris + 6 * int64_t(tid);
+      float v6[6];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        v6[2 * jj] = (__ldg(t + 2 * jj) - p.x) * ih;
+        v6[2 * jj + 1] = (__ldg(t + 2 * jj + 1) - p.y) * ih;
+      }
+      if constexpr (CLOSED) {
+        if constexpr (KID == KID_CUBIC) fix = cubic_split_pair<float, MD>(a, pid, tid, near_half<float>(v6), v);
+        else fix = eval_pair<float, KID, MD>(a, pid, tid, v);
+      } else {
+        const unsigned c = cls[q];
+        quad_pair<KID, MD>(qr, qr, v6, int(c & 3u), (c & 4u) != 0, a.C, a.invH, v);
+        if constexpr (KID == KID_CUBIC) {
+          if (r == 1) add_second_piece<MD>(qf, qr, v6, int(c & 3u), a.C, a.invH, v);
+        }
+      }
+    }
+    if constexpr (CLOSED) fixes += __popc(__ballot_sync(0xffffffffu, fix));
+    keyed_chunk_sums<float, NV, 3, unsigned long long>(a, sp, ch, valid, key, v);
+    j = chunk_next(a.work, j, nw, nx);
+  }
+  if (CLOSED && lane == 0 && fixes) atomicAdd(a.nfix, fixes);
+}
+
+// the cubic spline's closed form takes 3 resident blocks per SM with ten moments (as its
+// chunk kernel over the near/far partition); the Wendland kernels 4
+template <int KID, int MD> constexpr int hybrid_minb() {
+  return KID == KID_CUBIC ? cubic_split_minb<float, MD>() : int_minb<float>();
+}
+
+template <int KID, int MD>
+__global__ void __launch_bounds__(128, hybrid_minb<KID, MD>()) hybrid_closed_kernel(IntArgs a, QuadRule qr,
+                                                                                   QuadRaysFine qf, PairSplit sp,
+                                                                                   const uint8_t* __restrict__ cls) {
+  hybrid_chunks<KID, MD, true>(a, qr, qf, sp, cls);
+}
+
+template <int KID, int MD>
+__global__ void __launch_bounds__(128) hybrid_quad_kernel(IntArgs a, QuadRule qr, QuadRaysFine qf, PairSplit sp,
+                                                          const uint8_t* __restrict__ cls) {
+  hybrid_chunks<KID, MD, false>(a, qr, qf, sp, cls);
 }
 
 template <int KID, int MD>
 static sph2d_status run_hybrid(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
-  constexpr int nlists = KID == KID_CUBIC ? 3 : 1;
-  const int64_t nchunks = (a.P + 31) >> 5;
-  const int64_t cap = a.P > 0 ? a.P : 1;
-  sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(float));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(cap) * NV * sizeof(float));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, size_t(cap) * nlists * sizeof(int64_t) + 64);
+  PairSplit sp;
+  int64_t* cnt;
+  unsigned long long* hdr;
+  unsigned char* cls;
+  sph2d_status s = split_scratch<float>(c, a, 3, NV, size_t(a.P > 0 ? a.P : 1), sp, cnt, hdr, cls);
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
-  float* vals = static_cast<float*>(c->pair_vals.ptr);
-  int64_t* list = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
-  int64_t* near = list + cap;                        // cubic: pairs within H/2 whose second piece is pending
-  int64_t* fix_list = list + 2 * cap;                // cubic: FP32 pairs for the FP64 fix-up
-  auto* count = static_cast<unsigned long long*>(c->pair_list2.ptr);   // [0] list, [1] near, [2] fix-up
-  cudaError_t e = cudaMemsetAsync(count, 0, 64, c->stream);
+  cudaError_t e = cudaMemsetAsync(hdr, 0, 64, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   if (a.P > 0) {
-    const int64_t blocks = (a.P + 127) / 128;
-    IntArgs aq = a, al = a, a2 = a;                  // chunk counters in the zeroed header
-    aq.work = count + 4;
-    al.work = count + 5;
-    a2.work = count + 6;
-    SPH2D_LAUNCH(c, (hybrid_first_kernel<KID, MD>), resident_blocks(c, hybrid_first_kernel<KID, MD>, blocks), 128, aq,
-                 quad_rule(), vals, list, count, near, count + 1);
-    if constexpr (KID == KID_CUBIC) {
-      // the cubic spline's pieces over the list, as its closed-form path (the second piece also
-      // for the quadrature pairs already in near)
-      SPH2D_LAUNCH(c, (cubic_first_kernel<float, MD>), resident_blocks(c, cubic_first_kernel<float, MD>, blocks), 128,
-                   al, vals, list, count, near, count + 1, fix_list, count + 2);
-      SPH2D_LAUNCH(c, (cubic_fixup_kernel<MD>), resident_blocks(c, cubic_fixup_kernel<MD>, blocks), 128, a, vals,
-                   fix_list, count + 2);
-      SPH2D_LAUNCH(c, (cubic_second_kernel<float, MD>), resident_blocks(c, cubic_second_kernel<float, MD>, blocks), 128,
-                   a2, vals, near, count + 1);
-    } else {
-      SPH2D_LAUNCH(c, (hybrid_second_kernel<KID, MD>), resident_blocks(c, hybrid_second_kernel<KID, MD>, blocks), 128, al,
-                   vals, list, count);
-    }
-    SPH2D_LAUNCH(c, (reduce_pairs_kernel<float, MD>), resident_blocks(c, reduce_pairs_kernel<float, MD>, (nchunks + 3) / 4),
-                 128, a, vals);
+    a.work = hdr + 4;                                // chunk counters in the zeroed header
+    SPH2D_LAUNCH(c, (hybrid_class_kernel<KID>), resident_blocks(c, hybrid_class_kernel<KID>, (sp.nchunks + 3) / 4),
+                 128, a, sp, const_cast<uint32_t*>(sp.mask), cnt, cls);
+    s = split_order(c, a, sp, cnt);
+    if (s != SPH2D_OK) return s;
+    IntArgs aq = a;
+    aq.work = hdr + 5;                               // the quadrature kernel's own chunk counter
+    SPH2D_LAUNCH(c, (hybrid_closed_kernel<KID, MD>),
+                 resident_blocks(c, hybrid_closed_kernel<KID, MD>, (sp.nchunks + 3) / 4), 128, a, quad_rule(),
+                 quad_rays_fine(), sp, cls);
+    SPH2D_LAUNCH(c, (hybrid_quad_kernel<KID, MD>),
+                 resident_blocks(c, hybrid_quad_kernel<KID, MD>, (sp.nchunks + 3) / 4), 128, aq, quad_rule(),
+                 quad_rays_fine(), sp, cls);
   }
-  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<float, MD>), unsigned((a.N + 255) / 256), 256, a);
-  // the number of pairs left to the closed form, as the fallback count
-  e = cudaMemcpyAsync(c->pinned + 10, count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+  if (a.N > 0) SPH2D_LAUNCH(c, (split_finalize_kernel<float, MD>), unsigned((a.N + 255) / 256), 256, a, sp);
+  // the number of pairs left to the closed form (region 0), as the fallback count
+  const void* n0 = a.P > 0 ? static_cast<const void*>(sp.off + sp.nchunks) : static_cast<const void*>(hdr);
+  e = cudaMemcpyAsync(c->pinned + 10, n0, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "fallback count copy");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "hybrid launch");

@@ -379,14 +379,8 @@ __global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs 
 // runs over the partition: both pieces for a near pair (piece1 + piece2, in that order), the
 // first piece for a far pair, with the segmented sums and crossing slots of integrals_kernel
 // keyed by (particle, part).  The finalize adds each particle's near-part sum and far-part sum
-// in that order.  Every order is fixed, so results are deterministic run to run.
-//
-// Sparse lists (the hybrid mode's closed-form pairs): (1) every listed pair's first piece into a
-// per-pair value buffer, pairs within H/2 appended to a list, FP32 pairs that need the FP64
-// fix-up to another (both pieces then in FP64 by cubic_fixup_kernel); (2) the second piece over
-// the compacted list, added to the pair's value; (3) per-particle sums over the per-pair values
-// in pair order (reduce_pairs_kernel).  Each pair's value is piece1 + piece2 in that order, so
-// results do not depend on the list order.
+// in that order.  Every order is fixed, so results are deterministic run to run.  The hybrid
+// mode's closed-form pairs (few, mostly near) take the same pair function with a per-lane flag.
 // ---------------------------------------------------------------------------------------
 // origin within 1/2 (+ a small margin) of the local triangle: inside, or an edge segment
 // closer than that (no division)
@@ -437,93 +431,6 @@ __device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double
   }
 }
 
-// first piece of pair q into vals[q]; need: the pair lies within H/2 (second piece pending).
-// FP32: returns true, writing nothing, when the pair needs the FP64 fix-up (coordinates beyond
-// the FP32 range or a non-finite result); those pairs go to cubic_fixup_kernel, which keeps the
-// FP64 working set out of this kernel's registers
-template <typename OT, int MD>
-__device__ __forceinline__ bool cubic_first_pair(const IntArgs& a, int64_t q, OT* __restrict__ vals, bool& need) {
-  constexpr int NV = nv_of(MD);
-  const int pid = __ldg(a.pair_pid + q);
-  const float4 p = a.parts[pid];
-  const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-  OT* out = vals + q * NV;
-  need = false;
-  if constexpr (sizeof(OT) == sizeof(float)) {
-    const float ih = float(a.invH);
-    float lf[6];
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
-      lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
-      ok = ok && fabsf(lf[2 * j]) <= kFixupCoordLimit && fabsf(lf[2 * j + 1]) <= kFixupCoordLimit;
-    }
-    if (!ok) return true;
-    const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
-    float w[13];
-    if (s == 0) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) w[i] = 0.0f;
-    } else {
-      cubic_piece<float, MD>(lf, 0, s, a.C, a.invH, w);
-      need = near_half<float>(lf);
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) ok = ok && isfinite(w[i]);
-    if (!ok) {
-      need = false;
-      return true;
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
-    return false;
-  } else {
-    double ld[6], w[13];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-      ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-    }
-    const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-    if (s == 0) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) w[i] = 0.0;
-    } else {
-      cubic_piece<double, MD>(ld, 0, s, a.C, a.invH, w);
-      need = near_half<double>(ld);
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) out[i] = OT(w[i]);
-    return false;
-  }
-}
-
-// the FP64 fix-up of the FP32 pairs cubic_first_kernel listed: both pieces of each pair
-template <int MD>
-__global__ void __launch_bounds__(128) cubic_fixup_kernel(IntArgs a, float* __restrict__ vals,
-                                                          const int64_t* __restrict__ list,
-                                                          const unsigned long long* __restrict__ count) {
-  constexpr int NV = nv_of(MD);
-  const int64_t n = int64_t(*count);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && n > 0) atomicAdd(a.nfix, (unsigned long long)n);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t q = list[i];
-    const float4 p = a.parts[__ldg(a.pair_pid + q)];
-    const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-    double ld[6], w[13];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-      ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-    }
-    eval_local<double, KID_CUBIC, MD>(ld, a.C, a.invH, w);
-    float* o = vals + q * NV;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) o[k] = float(w[k]);
-  }
-}
-
 // warp-aggregated append of the lanes with flag set to list (count: its length)
 __device__ __forceinline__ void warp_append(bool flag, int64_t q, int64_t* __restrict__ list,
                                             unsigned long long* __restrict__ count) {
@@ -536,116 +443,6 @@ __device__ __forceinline__ void warp_append(bool flag, int64_t q, int64_t* __res
     b = __shfl_sync(0xffffffffu, b, leader);
     if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = q;
   }
-}
-
-// first piece of every pair (src == nullptr) or of the pairs src lists (src_count entries);
-// pairs within H/2 appended to list, FP32 pairs that need the FP64 fix-up to fix_list
-template <typename OT, int MD>
-__global__ void __launch_bounds__(128, int_minb<OT>()) cubic_first_kernel(IntArgs a, OT* __restrict__ vals,
-                                                          const int64_t* __restrict__ src,
-                                                          const unsigned long long* __restrict__ src_count,
-                                                          int64_t* __restrict__ list,
-                                                          unsigned long long* __restrict__ count,
-                                                          int64_t* __restrict__ fix_list,
-                                                          unsigned long long* __restrict__ fix_count) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  const int64_t n = src ? int64_t(*src_count) : a.P;
-  const int64_t nchunks = (n + 31) >> 5, nw = stride >> 5;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
-    const unsigned long long nx = chunk_prefetch(a.work);
-    const int64_t i = ch * 32 + lane;
-    bool need = false, defer = false;
-    int64_t q = 0;
-    if (i < n) {
-      q = src ? src[i] : i;
-      defer = cubic_first_pair<OT, MD>(a, q, vals, need);
-    }
-    warp_append(need, q, list, count);
-    if (sizeof(OT) == sizeof(float)) warp_append(defer, q, fix_list, fix_count);
-    ch = chunk_next(a.work, ch, nw, nx);
-  }
-}
-
-// the second piece of one pair in FP64 (an FP32 pair whose piece did not come out finite), out
-// of line as eval_fixup64
-template <int MD>
-__device__ __noinline__ void cubic_piece2_fp64(const float4 p, const float* t, double invH, double C, float* v) {
-  double ld[6], w[13];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * invH;
-    ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * invH;
-  }
-  const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-  cubic_piece<double, MD>(ld, 1, s, C, invH, w);
-#pragma unroll
-  for (int k = 0; k < nv_of(MD); ++k) v[k] = float(w[k]);
-}
-
-template <typename OT, int MD>
-__global__ void __launch_bounds__(128, int_minb<OT>()) cubic_second_kernel(IntArgs a, OT* __restrict__ vals,
-                                                           const int64_t* __restrict__ list,
-                                                           const unsigned long long* __restrict__ count) {
-  constexpr int NV = nv_of(MD);
-  const int64_t n = int64_t(*count);
-  const int64_t nchunks = (n + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long fixes = 0;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
-    const unsigned long long nx = chunk_prefetch(a.work);
-    const int64_t i = ch * 32 + (threadIdx.x & 31);
-    if (i < n) {
-    const int64_t q = list[i];
-    const float4 p = a.parts[__ldg(a.pair_pid + q)];
-    const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-    OT v[NV];
-    bool done = false;
-    if (sizeof(OT) == sizeof(float)) {
-      const float ih = float(a.invH);
-      float lf[6], w[13];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        lf[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
-        lf[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
-      }
-      const int s = tri_orientation<float>(lf[0], lf[1], lf[2], lf[3], lf[4], lf[5]);
-      cubic_piece<float, MD>(lf, 1, s, a.C, a.invH, w);
-      bool ok = true;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) ok = ok && isfinite(w[k]);
-      if (ok) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
-        done = true;
-      }
-    }
-    if (!done) {
-      if (sizeof(OT) == sizeof(float)) {
-        float w[13];
-        cubic_piece2_fp64<MD>(p, t, a.invH, a.C, w);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
-        ++fixes;
-      } else {
-        double ld[6], w[13];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          ld[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-          ld[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-        }
-        const int s = tri_orientation<double>(ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]);
-        cubic_piece<double, MD>(ld, 1, s, a.C, a.invH, w);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = OT(w[k]);
-      }
-    }
-    OT* out = vals + q * NV;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = out[k] + v[k];
-    }
-    ch = chunk_next(a.work, ch, nw, nx);
-  }
-  if (fixes) atomicAdd(a.nfix, fixes);
 }
 
 // per-particle sums of per-pair values [P][NV] in pair order
@@ -723,43 +520,211 @@ __global__ void finalize_kernel(IntArgs a) {
   write_particle<OT, MD>(a, i, v);
 }
 
+// grid of at most the blocks of 128 threads that stay resident at once (grid-stride kernels)
+template <typename K>
+static unsigned resident_blocks(Ctx* c, K kern, int64_t wanted) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
+}
+
 // ---------------------------------------------------------------------------------------
-// cubic spline over the near/far partition of the pair list
+// Stable partition of the pair list into K regions (pair kinds that take different code),
+// each region in pair order, regions one after another.  A pass flags each pair's region per
+// 32-pair chunk (one 32-bit mask per region and chunk) and counts the flags; one exclusive scan
+// over the counts, region-major, gives every (region, chunk) its first position; the partition
+// pass writes the pair at each position.  A chunk kernel over the positions then sums per
+// (particle, region) with the segmented sums and crossing slots of integrals_kernel, and the
+// finalize adds a particle's region sums in region order.  Every order is fixed, so results
+// are deterministic run to run.
 // ---------------------------------------------------------------------------------------
-struct CubicSplit {
-  const uint32_t* mask;    // [nchunks] bit l of word ch: pair 32 ch + l lies within H/2
-  const int64_t* coff;     // [nchunks + 1] near pairs before chunk ch; coff[nchunks] = all
+struct PairSplit {
+  const uint32_t* mask;    // [K][nchunks] bit l of word (r, ch): pair 32 ch + l is of region r
+  const int64_t* off;      // [K nchunks + 1] region-major exclusive scan of the mask counts
   const int64_t* order;    // [P] pair at each position of the partition
-  void* part;              // [2][N][NV] sums of a particle's near / far part held in one chunk
+  void* part;              // [K][N][NV] sums of a particle's region held in one chunk
   int64_t nchunks;
+  int nreg;
 };
 
-// near pairs before pair q (0 <= q <= P)
-__device__ __forceinline__ int64_t near_before(const CubicSplit& s, int64_t q) {
+// position of the first pair of region r at or after pair q (0 <= q <= P)
+__device__ __forceinline__ int64_t region_before(const PairSplit& s, int r, int64_t q) {
   const int64_t ch = q >> 5;
-  if (ch >= s.nchunks) return s.coff[s.nchunks];
-  return s.coff[ch] + __popc(s.mask[ch] & ((1u << (q & 31)) - 1u));
+  if (ch >= s.nchunks) return s.off[(r + 1) * s.nchunks];
+  const int64_t w = r * s.nchunks + ch;
+  return s.off[w] + __popc(s.mask[w] & ((1u << (q & 31)) - 1u));
 }
 
-// positions [s0, s1) of particle pid's part r (0 near, 1 far) in the partition
-__device__ __forceinline__ void part_range(const IntArgs& a, const CubicSplit& s, int64_t pid, int r,
+// positions [s0, s1) of particle pid's pairs of region r
+__device__ __forceinline__ void part_range(const IntArgs& a, const PairSplit& s, int64_t pid, int r,
                                            int64_t& s0, int64_t& s1) {
-  const int64_t q0 = __ldg(a.pair_off + pid), q1 = __ldg(a.pair_off + pid + 1);
-  const int64_t n0 = near_before(s, q0), n1 = near_before(s, q1);
-  const int64_t pn = s.coff[s.nchunks];
-  s0 = r ? pn + (q0 - n0) : n0;
-  s1 = r ? pn + (q1 - n1) : n1;
+  s0 = region_before(s, r, __ldg(a.pair_off + pid));
+  s1 = region_before(s, r, __ldg(a.pair_off + pid + 1));
 }
 
-// near flags of every 32-pair chunk (one warp per chunk) and their counts
+// flags of one chunk: every valid lane sets exactly one region; lane 0 stores the masks and
+// their counts
+__device__ __forceinline__ void store_region_masks(uint32_t* __restrict__ mask, int64_t* __restrict__ cnt,
+                                                   int64_t nchunks, int nreg, int64_t ch, int region) {
+  for (int r = 0; r < nreg; ++r) {
+    const unsigned m = __ballot_sync(0xffffffffu, region == r);
+    if ((threadIdx.x & 31) == 0) {
+      mask[r * nchunks + ch] = m;
+      cnt[r * nchunks + ch] = __popc(m);
+    }
+  }
+}
+
+// the partition: each pair at its rank within its region
+static __global__ void __launch_bounds__(128) partition_kernel(PairSplit s, int64_t P, int64_t* __restrict__ order) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < s.nchunks; ch += nw) {
+    const int64_t q = ch * 32 + lane;
+    if (q >= P) continue;
+    for (int r = 0; r < s.nreg; ++r) {
+      const unsigned m = s.mask[r * s.nchunks + ch];
+      if ((m >> lane) & 1u) {
+        order[s.off[r * s.nchunks + ch] + __popc(m & ((1u << lane) - 1u))] = q;
+        break;
+      }
+    }
+  }
+}
+
+// segmented sums of one chunk of positions keyed by K pid + region (K regions), written
+// like integrals_kernel's: a key held within the chunk to part[region][pid], the chunk's first
+// and last keys to its two slots
+// (KT: the key type, 32-bit where K N stays below 2^32)
+template <typename OT, int NV, int K, typename KT>
+__device__ __forceinline__ void keyed_chunk_sums(const IntArgs& a, const PairSplit& sp, int64_t ch, bool valid,
+                                                 KT key, OT* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const KT kn = __shfl_down_sync(0xffffffffu, key, o);
+    const bool same = (lane + o < 32) && (kn == key);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const OT t = __shfl_down_sync(0xffffffffu, v[k], o);
+      if (same) v[k] += t;
+    }
+  }
+  const KT kprev = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = valid && (lane == 0 || kprev != key);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const int last_head = 31 - __clz(heads);
+  if (head) {
+    const int64_t cs = ch * 32;
+    const int64_t pid = int64_t(key / KT(K));
+    const int r = int(key - KT(K) * KT(pid));
+    int64_t s0, s1;
+    part_range(a, sp, pid, r, s0, s1);
+    if (s0 >= cs && s1 <= cs + 32) {
+      OT* w = static_cast<OT*>(sp.part) + (int64_t(r) * a.N + pid) * NV;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) w[k] = v[k];
+    }
+    OT* slots = static_cast<OT*>(a.slots);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) slots[(ch * 2) * NV + k] = v[k];
+    }
+    if (lane == last_head) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) slots[(ch * 2 + 1) * NV + k] = v[k];
+    }
+  }
+}
+
+// per particle: the region sums in region order, each from its chunk or its crossing slots
+template <typename OT, int MD>
+__global__ void split_finalize_kernel(IntArgs a, PairSplit sp) {
+  constexpr int NV = nv_of(MD);
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  OT v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = OT(0);
+  if (a.pair_off[i + 1] > a.pair_off[i]) {
+    const OT* slots = static_cast<const OT*>(a.slots);
+    bool first = true;
+#pragma unroll 1
+    for (int r = 0; r < sp.nreg; ++r) {
+      int64_t s0, s1;
+      part_range(a, sp, i, r, s0, s1);
+      if (s1 <= s0) continue;
+      OT w[NV];
+      const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
+      if (c0 == c1) {
+        const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = src[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = slots[(c0 * 2 + 1) * NV + k];
+        for (int64_t c = c0 + 1; c < c1; ++c) {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) w[k] += slots[(c * 2) * NV + k];
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] += slots[(c1 * 2) * NV + k];
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] = first ? w[k] : v[k] + w[k];
+      first = false;
+    }
+  }
+  write_particle<OT, MD>(a, i, v);
+}
+
+// scratch of a K-region partition in pair_list2: header (chunk counter at [4]) | order [P] |
+// counts [K nchunks + 1] | offsets [K nchunks + 1] | masks [K nchunks] | extra bytes; region
+// sums [K][N][NV] in pair_vals
+inline size_t split_list_bytes(int64_t P, int64_t nchunks, int K, size_t extra) {
+  return 64 + size_t(P + 2 * (K * nchunks + 1)) * sizeof(int64_t) + size_t(K * nchunks + 1) * 4 + extra;
+}
 template <typename OT>
-__global__ void __launch_bounds__(128) cubic_near_mask_kernel(IntArgs a, uint32_t* __restrict__ mask,
+static sph2d_status split_scratch(Ctx* c, const IntArgs& a, int K, int NV, size_t extra, PairSplit& sp,
+                                  int64_t*& cnt, unsigned long long*& hdr, unsigned char*& extra_ptr) {
+  const int64_t nchunks = (a.P + 31) >> 5;
+  sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(K) * size_t(a.N > 0 ? a.N : 1) * NV * sizeof(OT));
+  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, split_list_bytes(a.P, nchunks, K, extra));
+  if (s != SPH2D_OK) return s;
+  hdr = static_cast<unsigned long long*>(c->pair_list2.ptr);
+  int64_t* order = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
+  cnt = order + a.P;
+  int64_t* off = cnt + (K * nchunks + 1);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(off + (K * nchunks + 1));
+  extra_ptr = reinterpret_cast<unsigned char*>(mask + (K * nchunks + 1));
+  sp = PairSplit{mask, off, order, c->pair_vals.ptr, nchunks, K};
+  return SPH2D_OK;
+}
+
+// after the masks: scan, partition
+static sph2d_status split_order(Ctx* c, const IntArgs& a, PairSplit& sp, const int64_t* cnt) {
+  sph2d_status s = exclusive_scan_i64(c, cnt, const_cast<int64_t*>(sp.off), int64_t(sp.nreg) * sp.nchunks);
+  if (s != SPH2D_OK) return s;
+  SPH2D_LAUNCH(c, (partition_kernel), resident_blocks(c, partition_kernel, (sp.nchunks + 3) / 4), 128, sp, a.P,
+               const_cast<int64_t*>(sp.order));
+  return SPH2D_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// cubic spline over the near/far partition: region 0 the pairs within H/2 of their triangle
+// (both pieces), region 1 the others (the first piece only)
+// ---------------------------------------------------------------------------------------
+template <typename OT>
+__global__ void __launch_bounds__(128) cubic_near_mask_kernel(IntArgs a, PairSplit sp, uint32_t* __restrict__ mask,
                                                               int64_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
-  const int64_t nchunks = (a.P + 31) >> 5, nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += nw) {
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < sp.nchunks; ch += nw) {
     const int64_t q = ch * 32 + lane;
-    bool near = false;
+    int region = -1;
     if (q < a.P) {
       const float4 p = a.parts[__ldg(a.pair_pid + q)];
       const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
@@ -774,26 +739,9 @@ __global__ void __launch_bounds__(128) cubic_near_mask_kernel(IntArgs a, uint32_
           l[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
         }
       }
-      near = near_half<OT>(l);
+      region = near_half<OT>(l) ? 0 : 1;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, near);
-    if (lane == 0) {
-      mask[ch] = m;
-      cnt[ch] = __popc(m);
-    }
-  }
-}
-
-// the partition: near pairs at their near rank, far pairs after all near pairs at their far rank
-static __global__ void __launch_bounds__(128) cubic_partition_kernel(CubicSplit s, int64_t P, int64_t* __restrict__ order) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5, pn = s.coff[s.nchunks];
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < s.nchunks; ch += nw) {
-    const int64_t q = ch * 32 + lane;
-    if (q >= P) continue;
-    const unsigned m = s.mask[ch];
-    const int64_t nb = s.coff[ch] + __popc(m & ((1u << lane) - 1u));
-    order[(m >> lane) & 1u ? nb : pn + (q - nb)] = q;
+    store_region_masks(mask, cnt, sp.nchunks, 2, ch, region);
   }
 }
 
@@ -857,7 +805,6 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
   }
 }
 
-// chunks of 32 positions of the partition; segmented sums keyed by 2 pid + part
 // With all ten moments the cubic spline's pair code spills at 128 registers (~100 B per thread:
 // both pieces and the keyed sums); 3 resident blocks per SM (<= 168 registers, 12 warps) measured
 // 6% faster for it, while the Wendland kernels lose ~30% at that cap.
@@ -865,19 +812,20 @@ template <typename OT, int MD> constexpr int cubic_split_minb() {
   return sizeof(OT) == sizeof(float) && MD >= 3 ? 3 : int_minb<OT>();
 }
 
+// chunks of 32 positions of the near/far partition
 template <typename OT, int MD>
-__global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_split_kernel(IntArgs a, CubicSplit sp) {
+__global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_split_kernel(IntArgs a, PairSplit sp) {
   constexpr int NV = nv_of(MD);
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int64_t pn = sp.coff[sp.nchunks];
+  const int64_t pn = sp.off[sp.nchunks];             // first far position
   unsigned long long fixes = 0;
   for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
     const unsigned long long nx = chunk_prefetch(a.work);
     const int64_t i = ch * 32 + lane;
     bool valid = false;
-    unsigned key = 0;
+    unsigned key = 0;                                // 2 pid + part: below 2^32 for any int32 pid
     OT v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = OT(0);
@@ -891,82 +839,10 @@ __global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_split_k
       fix = cubic_split_pair<OT, MD>(a, pid, __ldg(a.pair_tri + q), near, v);
     }
     fixes += __popc(__ballot_sync(0xffffffffu, fix));
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned kn = __shfl_down_sync(0xffffffffu, key, o);
-      const bool same = (lane + o < 32) && (kn == key);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        const OT t = __shfl_down_sync(0xffffffffu, v[k], o);
-        if (same) v[k] += t;
-      }
-    }
-    const unsigned kprev = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = valid && (lane == 0 || kprev != key);
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const int last_head = 31 - __clz(heads);
-    if (head) {
-      const int64_t cs = ch * 32, pid = key >> 1;
-      const int r = key & 1u;
-      int64_t s0, s1;
-      part_range(a, sp, pid, r, s0, s1);
-      if (s0 >= cs && s1 <= cs + 32) {
-        OT* w = static_cast<OT*>(sp.part) + (int64_t(r) * a.N + pid) * NV;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] = v[k];
-      }
-      OT* slots = static_cast<OT*>(a.slots);
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) slots[(ch * 2) * NV + k] = v[k];
-      }
-      if (lane == last_head) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) slots[(ch * 2 + 1) * NV + k] = v[k];
-      }
-    }
+    keyed_chunk_sums<OT, NV, 2, unsigned>(a, sp, ch, valid, key, v);
     ch = chunk_next(a.work, ch, nw, nx);
   }
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
-}
-
-// per particle: near-part sum + far-part sum, each from its chunk or its crossing slots
-template <typename OT, int MD>
-__global__ void cubic_split_finalize_kernel(IntArgs a, CubicSplit sp) {
-  constexpr int NV = nv_of(MD);
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
-  OT v[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = OT(0);
-  if (a.pair_off[i + 1] > a.pair_off[i]) {
-    const OT* slots = static_cast<const OT*>(a.slots);
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
-      int64_t s0, s1;
-      part_range(a, sp, i, r, s0, s1);
-      if (s1 <= s0) continue;
-      OT w[NV];
-      const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
-      if (c0 == c1) {
-        const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] = src[k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] = slots[(c0 * 2 + 1) * NV + k];
-        for (int64_t c = c0 + 1; c < c1; ++c) {
-#pragma unroll
-          for (int k = 0; k < NV; ++k) w[k] += slots[(c * 2) * NV + k];
-        }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] += slots[(c1 * 2) * NV + k];
-      }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) v[k] = r ? v[k] + w[k] : w[k];
-    }
-  }
-  write_particle<OT, MD>(a, i, v);
 }
 
 // independent pairs: [P][8] doubles -> [P][3+nm]
@@ -1006,48 +882,28 @@ __global__ void __launch_bounds__(256) pair_entry_kernel(const double* __restric
 // ---------------------------------------------------------------------------------------
 // host launchers for one output precision
 // ---------------------------------------------------------------------------------------
-template <typename K>
-static unsigned resident_blocks(Ctx* c, K kern, int64_t wanted) {
-  int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  return unsigned(wanted < cap ? (wanted > 0 ? wanted : 1) : cap);
-}
-
 template <typename OT, int MD>
 static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
-  const int64_t nchunks = (a.P + 31) >> 5;
-  // scratch: header (chunk counter at [4]) | order [P] | counts [nchunks + 1] | offsets
-  // [nchunks + 1] | masks [nchunks]
-  const size_t list_bytes = 64 + size_t(a.P + 2 * (nchunks + 1)) * sizeof(int64_t) + size_t(nchunks + 1) * 4;
-  sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(2 * (a.N > 0 ? a.N : 1)) * NV * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_list2, list_bytes);
+  PairSplit sp;
+  int64_t* cnt;
+  unsigned long long* hdr;
+  unsigned char* extra;
+  sph2d_status s = split_scratch<OT>(c, a, 2, NV, 0, sp, cnt, hdr, extra);
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
-  auto* hdr = static_cast<unsigned long long*>(c->pair_list2.ptr);
-  int64_t* order = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
-  int64_t* cnt = order + a.P;
-  int64_t* coff = cnt + (nchunks + 1);
-  uint32_t* mask = reinterpret_cast<uint32_t*>(coff + (nchunks + 1));
-  CubicSplit sp{mask, coff, order, c->pair_vals.ptr, nchunks};
   if (a.P > 0) {
     cudaError_t e = cudaMemsetAsync(hdr, 0, 64, c->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     a.work = hdr + 4;
-    const unsigned gb = resident_blocks(c, cubic_near_mask_kernel<OT>, (nchunks + 3) / 4);
-    SPH2D_LAUNCH(c, (cubic_near_mask_kernel<OT>), gb, 128, a, mask, cnt);
-    s = exclusive_scan_i64(c, cnt, coff, nchunks);
+    SPH2D_LAUNCH(c, (cubic_near_mask_kernel<OT>), resident_blocks(c, cubic_near_mask_kernel<OT>, (sp.nchunks + 3) / 4),
+                 128, a, sp, const_cast<uint32_t*>(sp.mask), cnt);
+    s = split_order(c, a, sp, cnt);
     if (s != SPH2D_OK) return s;
-    SPH2D_LAUNCH(c, (cubic_partition_kernel), resident_blocks(c, cubic_partition_kernel, (nchunks + 3) / 4), 128,
-                 sp, a.P, order);
     SPH2D_LAUNCH(c, (cubic_split_kernel<OT, MD>),
-                 resident_blocks(c, cubic_split_kernel<OT, MD>, (nchunks + 3) / 4), 128, a, sp);
+                 resident_blocks(c, cubic_split_kernel<OT, MD>, (sp.nchunks + 3) / 4), 128, a, sp);
   }
-  if (a.N > 0)
-    SPH2D_LAUNCH(c, (cubic_split_finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a, sp);
+  if (a.N > 0) SPH2D_LAUNCH(c, (split_finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a, sp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
   return SPH2D_OK;

@@ -13,7 +13,16 @@ constexpr int kQuadN = 6;
 // rule passed by value (kernel-parameter constant bank): Gauss-Legendre nodes u on [0, 1],
 // their weights w, and w u (the collapsed coordinate's Jacobian factor)
 struct QuadRule {
+  static constexpr int N = kQuadN;
   float u[kQuadN], w[kQuadN], wu[kQuadN];
+};
+
+// a finer rule across the rays (their directions), for the cubic spline's second piece: nodes
+// on [0, 1] and their weights
+constexpr int kQuadFineN = 10;
+struct QuadRaysFine {
+  static constexpr int N = kQuadFineN;
+  float u[kQuadFineN], w[kQuadFineN];
 };
 
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n (host)
@@ -63,6 +72,20 @@ static inline const QuadRule& quad_rule() {
   return r;
 }
 
+static inline const QuadRaysFine& quad_rays_fine() {
+  static QuadRaysFine r = [] {
+    QuadRaysFine q{};
+    double x[kQuadFineN], w[kQuadFineN];
+    gauss_legendre_nodes(kQuadFineN, x, w);
+    for (int i = 0; i < kQuadFineN; ++i) {
+      q.u[i] = float(0.5 * (x[i] + 1.0));
+      q.w[i] = float(0.5 * w[i]);
+    }
+    return q;
+  }();
+  return r;
+}
+
 // k(r) and k'(r)/r in factored form: (1 - r)^n times a positive polynomial keeps FP32 relative
 // accuracy near the support edge, where the expanded polynomials cancel (C4's coefficients
 // reach 150 while k(0.9) ~ 1e-6).  Cubic spline: inner (r < 1/2, both pieces)
@@ -102,12 +125,21 @@ __device__ __forceinline__ constexpr float cross_lmax2() {
   return KID == KID_WC2 ? 0.6f * 0.6f : KID == KID_WC4 ? 0.75f * 0.75f : KID == KID_WC6 ? 0.7f * 0.7f : 0.45f * 0.45f;
 }
 
+// Longest edge (squared, local units) below which the cubic spline's second piece of a near
+// pair is taken by quadrature too: in the doubled frame, where that piece is (1 - r')^3_+, the
+// triangle crosses r' = 1 with its apex inside; with 10 rays of 6 nodes each, measured over
+// generic triangles within H of the particle, the pair stays within 7.8e-7 of the output scales
+// at this size (2.1e-6 with 8 rays, 5.5e-6 with 6).
+constexpr float kHalfQuadLmax2 = 0.45f * 0.45f;
+
 // Classification of a pair for the hybrid mode.  quad: the first (or only) kernel piece by
 // quadrature, apex = index of the innermost vertex.  Cubic spline only: inner = the triangle
 // lies inside r < 1/2 (one polynomial there, by quadrature too); near = otherwise within 1/2
-// of the particle, so the second piece (support 1/2) is left to the closed form.
+// of the particle, so the second piece (support 1/2) needs its own integral; half = a near
+// pair whose apex lies inside r < 1/2 and whose longest edge is below kHalfQuadLmax2, so that
+// the second piece can be taken by the finer rule in the doubled frame.
 struct QuadClass {
-  bool quad, inner, near;
+  bool quad, inner, near, half;
   int apex;
 };
 
@@ -148,6 +180,7 @@ __device__ __forceinline__ QuadClass quad_classify(const float* v) {
            (rmax2 < 1.0f || (rmin2 < 1.0f && lmax2 < cross_lmax2<KID>()));
   c.inner = KID == KID_CUBIC && rmax2 < 0.25f;
   c.near = KID == KID_CUBIC && !c.inner && dmin2 < 0.25f;
+  c.half = c.near && rmin2 < 0.25f && lmax2 < kHalfQuadLmax2;
   return c;
 }
 

@@ -41,7 +41,7 @@ struct Ctx {
   // scratch buffers (named slots)
   DevBuf cell_start, cell_cursor, cell_tris, block_tmp, scan_tmp, pair_off, pair_tri, pair_pid,
       counts, slots, host_flags_dev, misc, tri_off, tri_pid, tri_cursor, bwd_g, bwd_grad,
-      pair_vals, pair_list2;   // per-pair values and second-piece list of the cubic spline
+      pair_vals, pair_list2;   // per-pair values or per-(particle, region) sums; partition scratch
   // learned surrogate: parameters (+ Adam state), training data and scratch, serving scratch
   DevBuf sur_prm, sur_split, sur_act, sur_data, sur_idx, sur_vals, sur_fb;
   // boundary pressure coupling: particle grid (cell starts, cursors, ids) and scratch

@@ -103,3 +103,64 @@ def test_hybrid_deterministic_and_unsupported_paths(ctx):
     with pytest.raises(Sph2dError, match="UNSUPPORTED"):
         ctx.backward(_t(w.particles), _t(w.triangles), "wendland_c2", w.H,
                      torch.zeros(len(w.particles), device="cuda"), "fp32_hybrid")
+
+
+def cubic_near_pairs(seed, count, lmax_lo, lmax_hi):
+    """one generic triangle per particle (particles 3 H apart, H = 1) that lies within H/2 of its
+    particle but not inside r < H/2, innermost vertex inside r < H/2, at least 0.55 of its longest
+    edge from the particle, longest edge in [lmax_lo, lmax_hi) H"""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        r0 = rng.uniform(0.05, 0.46)
+        a0 = rng.uniform(0, 2 * np.pi)
+        v0 = r0 * np.array([np.cos(a0), np.sin(a0)])
+        L = rng.uniform(0.1, 0.5, 2)
+        ang = a0 + rng.uniform(-1.4, 1.4, 2)
+        v = np.stack([v0, v0 + L[0] * np.array([np.cos(ang[0]), np.sin(ang[0])]),
+                      v0 + L[1] * np.array([np.cos(ang[1]), np.sin(ang[1])])])
+        r = np.hypot(v[:, 0], v[:, 1])
+        lmax = max(np.hypot(*(v[(i + 1) % 3] - v[i])) for i in range(3))
+        d = _tri_dist(v)
+        if (np.argmin(r) == 0 and r.max() > 0.52 and d < 0.48 and d >= 0.55 * lmax and lmax_lo <= lmax < lmax_hi
+                and abs((v[1, 0] - v[0, 0]) * (v[2, 1] - v[0, 1]) - (v[1, 1] - v[0, 1]) * (v[2, 0] - v[0, 0])) > 1e-3):
+            out.append(v)
+    loc = np.array(out)
+    n = int(np.ceil(np.sqrt(count)))
+    centres = 3.0 * np.stack(np.meshgrid(np.arange(n), np.arange(n)), -1).reshape(-1, 2)[:count]
+    parts = np.zeros((count, 4), dtype=np.float32)
+    parts[:, :2] = centres
+    tris = (loc + centres[:, None, :]).reshape(count, 6).astype(np.float32)
+    return W.Workload(f"cubic_near_{count}", 1.0, ["cubic_spline"], 3, parts, tris)
+
+
+def _tri_dist(v):
+    """distance from the origin to the triangle v (3 x 2), 0 inside"""
+    s = [(v[(e + 1) % 3, 0] - v[e, 0]) * (-v[e, 1]) - (v[(e + 1) % 3, 1] - v[e, 1]) * (-v[e, 0]) for e in range(3)]
+    if all(x >= 0 for x in s) or all(x <= 0 for x in s):
+        return 0.0
+    best = np.inf
+    for e in range(3):
+        a, b = v[e], v[(e + 1) % 3]
+        t = np.clip(-a @ (b - a) / ((b - a) @ (b - a)), 0.0, 1.0)
+        best = min(best, np.hypot(*(a + t * (b - a))))
+    return best
+
+
+def test_hybrid_cubic_second_piece_by_quadrature(ctx):
+    """cubic spline pairs within H/2 whose second piece the finer rule takes in the doubled frame
+    (longest edge below 0.45 H): every pair by quadrature, each within 2e-6 of the output scales
+    (the rule's 7.8e-7 in exact arithmetic plus FP32 rounding)"""
+    w = cubic_near_pairs(31, 400, 0.1, 0.43)
+    err, st = check(ctx, w, "cubic_spline", 3, 400)
+    assert st["n_pairs"] == 400 and st["n_fallback"] == 0
+    assert err <= 2e-6, err
+
+
+def test_hybrid_cubic_near_large_to_closed_form(ctx):
+    """the same class with longest edges of 0.46-0.5 H: beyond the finer rule's size, so the
+    closed form takes them (within the FP32 tolerance)"""
+    w = cubic_near_pairs(32, 200, 0.46, 0.5)
+    err, st = check(ctx, w, "cubic_spline", 3, 200)
+    assert st["n_pairs"] == 200 and st["n_fallback"] == 200
+    assert err <= TOL_FP32, err
