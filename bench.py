@@ -59,6 +59,8 @@ def parse():
                     help="profiling runs: timed FP32 path only (no FP64 leg, e2e, CPU baseline, L2 flush)")
     ap.add_argument("--quick-mode", default="fp32_fixup", choices=["fp32_fixup", "fp32_hybrid"],
                     help="the mode a --quick run times (the headline's FP32 + fix-up, or the hybrid mode)")
+    ap.add_argument("--only-leg", default=None, choices=["fields", "fields_p", "pressure", "adjoint"],
+                    help="profiling runs: only this widened leg, FP32 modes only, on the benchmark workload")
     return ap.parse_args()
 
 
@@ -322,6 +324,22 @@ def run_ours(args):
             kms = [[t[i][0].elapsed_time(t[i][1]) for t in kt] for i in range(len(KERNELS) + 1)]
         return ms, kms, launches, clocks
 
+    if args.only_leg:
+        flush = torch.empty(16, dtype=torch.uint8, device=dev)
+        ctx.build_cells(parts, tris, w.H)
+        P = ctx.pair_count()
+        if args.only_leg == "fields":
+            res = run_fields(ctx, parts, tris, w, stream, flush, P, reps=2, modes=("fp32_fixup",))
+        elif args.only_leg == "fields_p":
+            res = run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=2, modes=("fp32_hybrid",))
+        elif args.only_leg == "pressure":
+            res = run_pressure(ctx, parts, tris, w, stream, flush, P, reps=2, modes=("fp32_fixup",))
+        else:
+            res = run_adjoint(ctx, dev, stream, flush, steps=2, modes=("fp32_fixup",))
+        if rank == 0:
+            print(json.dumps({args.only_leg: res}), flush=True)
+        return
+
     if args.only_surrogate:
         flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
         res = run_surrogate(ctx, dev, stream, flush, n=args.surrogate_n, train_pairs=args.surrogate_train_pairs)
@@ -535,7 +553,7 @@ def run_hybrid(ctx, parts, tris, w, stream, flush, P, step, timed, reps=3):
                     "its edge below a per-kernel size"}
 
 
-def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):
+def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3, modes=("fp32_fixup", "fp64")):
     """<A> and <grad A> of two per-vertex fields (rho = 1 + x y / 4 and rho u, u = sin 3x +
     cos 2y) on the benchmark pair list, FP32 + fix-up and FP64."""
     import torch
@@ -546,7 +564,7 @@ def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):
     vv = torch.from_numpy(np.stack([rho, rho * u], axis=-1).astype(np.float32)).to(parts.device)
     k = "wendland_c4"
     out, res = {}, {"kernel": k, "fields": 2, "pairs": P}
-    for mode in ("fp32_fixup", "fp64"):
+    for mode in modes:
         out[mode] = ctx.field_integrals(vv, k, mode)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         for a_, b_ in ev:
@@ -557,6 +575,8 @@ def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):
         torch.cuda.synchronize()
         ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
         res[mode] = {"ms": ms, "pairs_per_s": P / (ms / 1e3)}
+    if len(modes) < 2:
+        return res
     a32, g32 = out["fp32_fixup"]
     a64, g64 = out["fp64"]
     sa = float(np.max(np.abs(vv.cpu().numpy())))
@@ -569,7 +589,7 @@ def run_fields(ctx, parts, tris, w, stream, flush, P, reps=3):
     return res
 
 
-def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3):
+def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3, modes=("fp32_hybrid", "fp64")):
     """<A> and <grad A> of two Lagrange fields of order 2 and 3 (the fields of run_fields
     sampled at the element nodes) on the benchmark pair list, hybrid FP32 and FP64."""
     import torch
@@ -584,7 +604,7 @@ def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3):
         u = np.sin(3 * v[..., 0]) + np.cos(2 * v[..., 1])
         vv = torch.from_numpy(np.stack([rho, rho * u], axis=-1).astype(np.float32)).to(parts.device)
         out, r = {}, {}
-        for mode in ("fp32_hybrid", "fp64"):
+        for mode in modes:
             out[mode] = ctx.field_integrals(vv, k, mode, order=order)
             if mode == "fp32_hybrid":
                 r["closed_form_share"] = ctx.stats()["n_fallback"] / max(P, 1)
@@ -597,6 +617,9 @@ def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3):
             torch.cuda.synchronize()
             ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
             r[mode] = {"ms": ms, "pairs_per_s": P / (ms / 1e3)}
+        if len(modes) < 2:
+            res[f"order{order}"] = r
+            continue
         a32, g32 = out["fp32_hybrid"]
         a64, g64 = out["fp64"]
         sa = float(np.max(np.abs(vv.cpu().numpy())))
@@ -610,7 +633,7 @@ def run_fields_p(ctx, parts, tris, w, stream, flush, P, reps=3):
     return res
 
 
-def run_pressure(ctx, parts, tris, w, stream, flush, P, reps=3):
+def run_pressure(ctx, parts, tris, w, stream, flush, P, reps=3, modes=("fp32_fixup", "fp64")):
     """Boundary pressure acceleration (Appendix A) of every particle of the benchmark workload
     under a hydrostatic fluid state: both models, FP32 + fix-up and FP64, Wendland C4."""
     import torch
@@ -627,7 +650,7 @@ def run_pressure(ctx, parts, tris, w, stream, flush, P, reps=3):
     sc = (2.0 * pmax / 1000.0) * scales(k, w.H, 0)[1]
     for model in (1, 2):
         out, r = {}, {}
-        for mode in ("fp32_fixup", "fp64"):
+        for mode in modes:
             out[mode] = ctx.boundary_pressure(rho, pr, vol, st["rho0_b"], k, mode, model)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
             for a_, b_ in ev:
@@ -638,7 +661,8 @@ def run_pressure(ctx, parts, tris, w, stream, flush, P, reps=3):
             torch.cuda.synchronize()
             ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
             r[mode] = {"ms": ms, "particles_per_s": len(w.particles) / (ms / 1e3), "pairs_per_s": P / (ms / 1e3)}
-        r["max_err_fp32_vs_fp64"] = float((out["fp32_fixup"].double() - out["fp64"]).abs().max() / sc)
+        if len(modes) == 2:
+            r["max_err_fp32_vs_fp64"] = float((out["fp32_fixup"].double() - out["fp64"]).abs().max() / sc)
         res[f"model{model}"] = r
         del out
     res["note"] = ("times include the MLS pressures (model 1: 3 per triangle; model 2: one per pair) and, for "
@@ -647,7 +671,7 @@ def run_pressure(ctx, parts, tris, w, stream, flush, P, reps=3):
     return res
 
 
-def run_adjoint(ctx, dev, stream, flush, steps=3):
+def run_adjoint(ctx, dev, stream, flush, steps=3, modes=("fp32_fixup", "fp64")):
     """Forward + backward of L = sum (gamma - gamma*)^2 on the adjoint workload."""
     import torch
     from paper_2507_21686_gb300 import workloads as W
@@ -656,7 +680,7 @@ def run_adjoint(ctx, dev, stream, flush, steps=3):
     tris = torch.from_numpy(w.triangles).to(dev)
     star = torch.from_numpy(w.extra["target_triangles"]).to(dev)
     out = {"workload": w.name, "kernel": "wendland_c4"}
-    for mode in ("fp32_fixup", "fp64"):
+    for mode in modes:
         gs, _, _ = ctx.boundary_integrals(parts, star, "wendland_c4", w.H, -1, mode)
         g, _, _ = ctx.boundary_integrals(parts, tris, "wendland_c4", w.H, -1, mode)
         P = ctx.pair_count()

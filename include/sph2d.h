@@ -94,11 +94,14 @@ typedef struct sph2d_ctx sph2d_ctx;
  * size (Wendland C2 0.6 H, C4 0.75 H, C6 0.7 H, cubic spline 0.45 H), is integrated in FP32
  * by a 36-point conical-product Gauss-Legendre rule whose rays stop at the support circle
  * (measured error <= 1.5e-6 of the output scales per pair for every output, moments
- * included, against 1e-5 for SPH2D_FP32_FIXUP); the cubic spline's second piece (support
- * H/2) joins the quadrature inside H/2 and otherwise takes its closed form.  Every other pair
- * takes the SPH2D_FP32_FIXUP closed form.  Float outputs; n_fallback counts the pairs left to
- * the closed form.  Per-particle paths only (not sph2d_pair_integrals, the adjoint or the
- * field integrals: UNSUPPORTED). */
+ * included, against 1e-5 for SPH2D_FP32_FIXUP).  The cubic spline's second piece (support
+ * H/2) joins the quadrature for a triangle inside H/2 and is zero for one at least H/2 away;
+ * for a triangle in between with a vertex inside H/2 and a longest edge below 0.45 H, a
+ * 60-point rule of the same form integrates it in the doubled frame, where its support is the
+ * unit circle (measured <= 7.8e-7).  Every other pair takes the SPH2D_FP32_FIXUP closed form.
+ * Float outputs; n_fallback counts the pairs left to the closed form.  Per-particle paths only
+ * (sph2d_pair_integrals, the adjoint and the piecewise-linear sph2d_field_integrals return
+ * UNSUPPORTED; sph2d_field_integrals_p has its own hybrid form, below). */
 
 /* Statistics of the most recent integral call on a context. */
 typedef struct {

@@ -8,7 +8,10 @@
 //     the linear-field gradient of the vertex pressures and grad gamma from one evaluation)
 //   2 (contact pressure): per pair one value p(x_iT) at the point of the triangle's boundary
 //     closest to x_i;  a_i = - sum_T rho_0b (p(x_iT)/rho_0b^2 + p_i/rho_i^2) grad gamma_iT
-//     (one fused pair pass: contact point, MLS, grad gamma_iT, weighted segmented sum).
+//     (two pair passes: contact point, MLS and the pair's weight into a per-pair buffer; then
+//     grad gamma_iT and the weighted segmented sum.  Fused, the MLS loops and the closed form
+//     together overran the instruction cache: ncu showed 9.3 warps per issue stalled on
+//     instruction fetch and the FMA pipe 25% active).
 //
 // MLS at a point b: the linear fit a + g . d_j, d_j = (x_j - b)/H, to the pressures p_j of the
 // particles within H, weighted by w_j = V_j k(|d_j|) (the kernel's constant cancels); p(b) = a
@@ -221,9 +224,28 @@ struct PressArgs {
   const float* pres;
   const float* rho;
   double rho0b;
+  const void* wts;           // model 2: per-pair weights of contact_weight_kernel (OT [P])
 };
 
-// model 2: one warp per 32 consecutive pairs; v[0] = sum_T w_iT gamma_iT, v[1..2] = a_i
+// model 2, first pass, one thread per pair: the contact point, the MLS pressure there and the
+// pair's weight rho_0b (p(x_iT)/rho_0b^2 + p_i/rho_i^2)
+template <typename OT, int KID>
+__global__ void __launch_bounds__(128) contact_weight_kernel(IntArgs a, PressArgs pa, OT* __restrict__ wts) {
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < a.P; q += int64_t(gridDim.x) * blockDim.x) {
+    const int pid = __ldg(a.pair_pid + q);
+    const int tid = __ldg(a.pair_tri + q);
+    const float4 p = a.parts[pid];
+    OT cx, cy;
+    closest_on_boundary<OT>(OT(p.x), OT(p.y), a.tris + 6 * int64_t(tid), cx, cy);
+    const OT pc = mls_eval<OT, KID>(pa.g, a.parts, pa.vol, pa.pres, cx, cy);
+    const OT r = OT(__ldg(pa.rho + pid));
+    const OT rb = OT(pa.rho0b);
+    wts[q] = rb * (pc / (rb * rb) + OT(__ldg(pa.pres + pid)) / (r * r));
+  }
+}
+
+// model 2, second pass: one warp per 32 consecutive pairs; v[0] = sum_T w_iT gamma_iT,
+// v[1..2] = a_i
 template <typename OT, int KID>
 __global__ void __launch_bounds__(128) contact_pressure_kernel(FieldArgs f, PressArgs pa) {
   constexpr int NV = 3 * kMaxFields;
@@ -243,13 +265,7 @@ __global__ void __launch_bounds__(128) contact_pressure_kernel(FieldArgs f, Pres
       const int tid = __ldg(a.pair_tri + q);
       OT w[nv_of(0)];
       fix = eval_pair<OT, KID, 0>(a, pid, tid, w);
-      const float4 p = a.parts[pid];
-      OT cx, cy;
-      closest_on_boundary<OT>(OT(p.x), OT(p.y), a.tris + 6 * int64_t(tid), cx, cy);
-      const OT pc = mls_eval<OT, KID>(pa.g, a.parts, pa.vol, pa.pres, cx, cy);
-      const OT r = OT(__ldg(pa.rho + pid));
-      const OT rb = OT(pa.rho0b);
-      const OT wt = rb * (pc / (rb * rb) + OT(__ldg(pa.pres + pid)) / (r * r));
+      const OT wt = static_cast<const OT*>(pa.wts)[q];
       v[0] = wt * w[0];
       v[1] = -wt * w[1];
       v[2] = -wt * w[2];
@@ -387,12 +403,16 @@ static sph2d_status mls_vertices_t(Ctx* c, int kernel, const float* vol, const f
 template <typename OT, int KID>
 static sph2d_status launch_pass(Ctx* c, int model, const FieldArgs& f, const PressArgs& pa, const float* pv,
                                 int64_t want) {
-  if (model == 1)
+  if (model == 1) {
     SPH2D_LAUNCH(c, (vertex_pressure_kernel<OT, KID>), resident_blocks(c, vertex_pressure_kernel<OT, KID>, want), 128,
                  f, pa, pv);
-  else
+  } else {
+    OT* wts = static_cast<OT*>(const_cast<void*>(pa.wts));
+    SPH2D_LAUNCH(c, (contact_weight_kernel<OT, KID>),
+                 resident_blocks(c, contact_weight_kernel<OT, KID>, (f.a.P + 127) / 128), 128, f.a, pa, wts);
     SPH2D_LAUNCH(c, (contact_pressure_kernel<OT, KID>), resident_blocks(c, contact_pressure_kernel<OT, KID>, want), 128,
                  f, pa);
+  }
   return SPH2D_OK;
 }
 
@@ -461,7 +481,11 @@ sph2d_status launch_boundary_pressure(Ctx* c, int kernel, int mode, int model, c
   f.nf = 1;
   f.value = c->pres_tmp.ptr;                         // per particle: model 1 <p>, model 2 sum_T w_iT gamma_iT
   f.grad = accel;
-  PressArgs pa{pgrid_of(c), vol, pres, rho, rho0b};
+  if (model == 2) {
+    s = ensure(c, c->pair_vals, size_t(cl.P > 0 ? cl.P : 1) * osz);   // per-pair weights
+    if (s != SPH2D_OK) return s;
+  }
+  PressArgs pa{pgrid_of(c), vol, pres, rho, rho0b, model == 2 ? c->pair_vals.ptr : nullptr};
   s = mode == SPH2D_FP64 ? run_pressure_pass<double>(c, kernel, model, f, pa, pv)
                          : run_pressure_pass<float>(c, kernel, model, f, pa, pv);
   if (s != SPH2D_OK) return s;
