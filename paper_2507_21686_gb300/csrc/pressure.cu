@@ -127,41 +127,41 @@ __device__ __forceinline__ void mls_pass(const PGrid& g, const float4* __restric
                                          const float* __restrict__ pres, R bx, R by, R* acc, R cx, R cy, R pb) {
   const R ih = R(1.0 / g.H);
   const int ix = int(floor((double(bx) - g.x0) * g.inv_cs)), iy = int(floor((double(by) - g.y0) * g.inv_cs));
+  // the (up to) three cells of a row are consecutive in the grid, so their particles form one
+  // range of ids: cells in row order, each cell's particles ascending
+  const int x_lo = ix - 1 < 0 ? 0 : ix - 1, x_hi = ix + 1 >= g.nx ? g.nx - 1 : ix + 1;
   for (int cyi = iy - 1; cyi <= iy + 1; ++cyi) {
-    if (cyi < 0 || cyi >= g.ny) continue;
-    for (int cxi = ix - 1; cxi <= ix + 1; ++cxi) {
-      if (cxi < 0 || cxi >= g.nx) continue;
-      const int64_t cidx = int64_t(cyi) * g.nx + cxi;
-      const int64_t j0 = __ldg(g.start + cidx), j1 = __ldg(g.start + cidx + 1);
-      for (int64_t jj = j0; jj < j1; ++jj) {
-        const int j = __ldg(g.ids + jj);
-        const float4 q = parts[j];
-        const R dx = (R(q.x) - bx) * ih, dy = (R(q.y) - by) * ih;
-        const R r2 = dx * dx + dy * dy;
-        if (!(r2 < R(1))) continue;
-        const R w = R(__ldg(vol + j)) * kernel_k<R, KID>(sqrt(r2));
-        const R pj = R(__ldg(pres + j));
-        if (!SECOND) {
-          acc[0] += w;
-          acc[1] += w * dx;
-          acc[2] += w * dy;
-          acc[3] += w * pj;
-        } else {
-          const R ex = dx - cx, ey = dy - cy, wq = w * (pj - pb);
-          acc[0] += w * ex * ex;
-          acc[1] += w * ex * ey;
-          acc[2] += w * ey * ey;
-          acc[3] += wq * ex;
-          acc[4] += wq * ey;
-        }
+    if (cyi < 0 || cyi >= g.ny || x_lo > x_hi) continue;
+    const int64_t row = int64_t(cyi) * g.nx;
+    const int64_t j0 = __ldg(g.start + row + x_lo), j1 = __ldg(g.start + row + x_hi + 1);
+    for (int64_t jj = j0; jj < j1; ++jj) {
+      const int j = __ldg(g.ids + jj);
+      const float4 q = parts[j];
+      const R dx = (R(q.x) - bx) * ih, dy = (R(q.y) - by) * ih;
+      const R r2 = dx * dx + dy * dy;
+      if (!(r2 < R(1))) continue;
+      const R w = R(__ldg(vol + j)) * kernel_k<R, KID>(sqrt(r2));
+      const R pj = R(__ldg(pres + j));
+      if (!SECOND) {
+        acc[0] += w;
+        acc[1] += w * dx;
+        acc[2] += w * dy;
+        acc[3] += w * pj;
+      } else {
+        const R ex = dx - cx, ey = dy - cy, wq = w * (pj - pb);
+        acc[0] += w * ex * ex;
+        acc[1] += w * ex * ey;
+        acc[2] += w * ey * ey;
+        acc[3] += wq * ex;
+        acc[4] += wq * ey;
       }
     }
   }
 }
 
 template <typename R, int KID>
-__device__ R mls_eval(const PGrid& g, const float4* __restrict__ parts, const float* __restrict__ vol,
-                      const float* __restrict__ pres, R bx, R by) {
+__device__ __forceinline__ R mls_eval(const PGrid& g, const float4* __restrict__ parts, const float* __restrict__ vol,
+                                      const float* __restrict__ pres, R bx, R by) {
   R m[4] = {R(0), R(0), R(0), R(0)};
   mls_pass<R, KID, false>(g, parts, vol, pres, bx, by, m, R(0), R(0), R(0));
   const R s0 = m[0];
