@@ -37,7 +37,7 @@ KERNELS = ["wendland_c2", "wendland_c4", "cubic_spline"]
 MOMENT_DEGREE = 3
 
 
-def parse():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -61,7 +61,11 @@ def parse():
                     help="the mode a --quick run times (the headline's FP32 + fix-up, or the hybrid mode)")
     ap.add_argument("--only-leg", default=None, choices=["fields", "fields_p", "pressure", "adjoint"],
                     help="profiling runs: only this widened leg, FP32 modes only, on the benchmark workload")
-    return ap.parse_args()
+    return ap
+
+
+def parse(argv=None):
+    return build_parser().parse_args(argv)
 
 
 # ---------------------------------------------------------------------------------------
