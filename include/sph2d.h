@@ -247,7 +247,7 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* ctx, const float* part
  *   gamma       device real [N];  grad_gamma device real [N][2] or NULL
  *   stream      cudaStream_t (NULL = legacy default stream); runs on the current device
  * Limit: P <= 32 * floor((SPH2D_NOALLOC_SCRATCH_BYTES - 256) / (6 * sizeof(real))), i.e.
- * 5,592,405 pairs in SPH2D_FP64 and 11,184,810 in SPH2D_FP32_FIXUP; larger lists return
+ * 5,592,224 pairs in SPH2D_FP64 and 11,184,448 in SPH2D_FP32_FIXUP; larger lists return
  * SPH2D_ERR_CAPACITY before any work is enqueued.
  * All calls share the array: calls that overlap on the GPU (other streams or host threads at
  * the same time) race.  The first call on a device resolves the array's address with that

@@ -7,8 +7,7 @@ Appendix A: the boundary's pressure acceleration of particle i is
 with the boundary density held at its rest value rho_0b, and the boundary pressure p(x') from
 a moving-least-squares fit to the fluid particles' pressures (the appendix cites Band et al.'s
 MLS extrapolation), in one of two models:
-  model 1 (vertex pressure):  p at each triangle vertex by MLS (stored as float32, the layout of
-      the vertex table), interpolated barycentrically;
+  model 1 (vertex pressure):  p at each triangle vertex by MLS, interpolated barycentrically;
       a_i = -(1/rho_0b) sum_T int_T p_T grad_x W  -  rho_0b p_i/rho_i^2 grad gamma_i
   model 2 (contact pressure): per pair one value p(x_iT) at the point of the triangle's
       boundary closest to x_i;
@@ -95,8 +94,7 @@ def boundary_pressure(kernel, H, particles, triangles, off, pair_tri, density, p
         used = np.unique(pt)
         pv = np.zeros((len(tris), 3))
         for t in used:
-            # the vertex pressure table is float32 (the layout of the GPU's field pass input)
-            pv[t] = np.float32(mls_pressure(kernel, H, xs, volume, pressure, tris[t].reshape(3, 2).astype(np.float64)))
+            pv[t] = mls_pressure(kernel, H, xs, volume, pressure, tris[t].reshape(3, 2).astype(np.float64))
         fld = oracle.pairs_field(kernel, H, pairs, pv[pt])
         for q in range(len(pt)):
             i = pid[q]

@@ -914,22 +914,14 @@ static sph2d_status run_integrals(Ctx* c, IntArgs a) {
   if constexpr (KID == KID_CUBIC) {
     return run_cubic<OT, MD>(c, a);
   } else {
-  static int grid_blocks = 0;
-  if (grid_blocks == 0) {
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrals_kernel<OT, KID, MD>, 128, 0);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    grid_blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
   constexpr int NV = nv_of(MD);
   const int64_t nchunks = (a.P + 31) >> 5;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
   if (a.P > 0) {
-    int64_t want = (nchunks + 3) / 4;                    // 4 warps per block
-    const unsigned blocks = unsigned(want < grid_blocks ? (want > 0 ? want : 1) : grid_blocks);
-    SPH2D_LAUNCH(c, (integrals_kernel<OT, KID, MD>), blocks, 128, a);
+    const int64_t want = (nchunks + 3) / 4;              // 4 warps per block
+    SPH2D_LAUNCH(c, (integrals_kernel<OT, KID, MD>), resident_blocks(c, integrals_kernel<OT, KID, MD>, want), 128, a);
   }
   if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a);
   cudaError_t e = cudaGetLastError();

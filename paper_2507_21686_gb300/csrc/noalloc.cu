@@ -44,6 +44,24 @@ cudaError_t scratch_address(int dev, void** out) {
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
 }
+
+// occupancy-sized grid of kernel `kern` on device dev (resolved once per device and kernel;
+// slot: the kernel's index among the noalloc instantiations)
+constexpr int kNoallocKernels = 8;
+int g_grid_blocks[kMaxDevices][kNoallocKernels] = {};
+
+template <typename K>
+int grid_blocks_for(int dev, int slot, K kern) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  int& gb = g_grid_blocks[dev][slot];
+  if (gb == 0) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    gb = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  return gb;
+}
 }  // namespace
 
 // Same chunked warp reduction as integrals_kernel (gamma and grad gamma, no moments), except
@@ -105,15 +123,9 @@ __global__ void __launch_bounds__(128) integrals_noalloc_kernel(IntArgs a) {
 }
 
 template <typename OT, int KID>
-static cudaError_t launch_noalloc(const IntArgs& a, cudaStream_t st) {
-  static int grid_blocks = 0;   // occupancy-sized grid, computed once (no allocation)
-  if (grid_blocks == 0) {
-    int per_sm = 0, sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrals_noalloc_kernel<OT, KID>, 128, 0);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid_blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
+static cudaError_t launch_noalloc(int dev, const IntArgs& a, cudaStream_t st) {
+  const int grid_blocks =
+      grid_blocks_for(dev, KID + (sizeof(OT) == sizeof(double) ? 4 : 0), integrals_noalloc_kernel<OT, KID>);
   const int64_t nchunks = (a.P + 31) >> 5;
   if (a.P > 0) {
     const int64_t want = (nchunks + 3) / 4;
@@ -125,12 +137,12 @@ static cudaError_t launch_noalloc(const IntArgs& a, cudaStream_t st) {
 }
 
 template <typename OT>
-static cudaError_t dispatch_noalloc(int kernel, const IntArgs& a, cudaStream_t st) {
+static cudaError_t dispatch_noalloc(int dev, int kernel, const IntArgs& a, cudaStream_t st) {
   switch (kernel) {
-    case KID_WC2: return launch_noalloc<OT, KID_WC2>(a, st);
-    case KID_WC4: return launch_noalloc<OT, KID_WC4>(a, st);
-    case KID_WC6: return launch_noalloc<OT, KID_WC6>(a, st);
-    default: return launch_noalloc<OT, KID_CUBIC>(a, st);
+    case KID_WC2: return launch_noalloc<OT, KID_WC2>(dev, a, st);
+    case KID_WC4: return launch_noalloc<OT, KID_WC4>(dev, a, st);
+    case KID_WC6: return launch_noalloc<OT, KID_WC6>(dev, a, st);
+    default: return launch_noalloc<OT, KID_CUBIC>(dev, a, st);
   }
 }
 
@@ -186,7 +198,7 @@ extern "C" sph2d_status sph2d_pair_list_integrals_noalloc(
     cudaGetLastError();
     return SPH2D_ERR_CUDA;
   }
-  const cudaError_t e = mode == SPH2D_FP64 ? dispatch_noalloc<double>(kernel, a, st)
-                                           : dispatch_noalloc<float>(kernel, a, st);
+  const cudaError_t e = mode == SPH2D_FP64 ? dispatch_noalloc<double>(dev, kernel, a, st)
+                                           : dispatch_noalloc<float>(dev, kernel, a, st);
   return e == cudaSuccess ? SPH2D_OK : SPH2D_ERR_CUDA;
 }

@@ -1,8 +1,12 @@
 // Algorithmic operation count of the pair formula.  The closed-form pair integrals of
 // pair_math.cuh are instantiated with a scalar type that counts every floating-point
-// operation it performs, so the count is of exactly the formula the CUDA kernels execute
-// (FP64 path: double; FP32 path: float with compensated FF radial sums).  Host code only;
-// the benchmark uses it for the roofline's algorithmic FLOPs per pair.
+// operation it performs, so the count is of exactly the formula the CUDA kernels execute.
+// Three instantiations:
+//   fp64    the FP64 path as it runs (double; double-double sums for Wendland C6)
+//   fp32    the compensated FP32 form (float with compensated FF radial sums)
+//   method  the closed form in plain arithmetic for every kernel: no compensation terms, the
+//           method's own work (the roofline's algorithmic FLOPs per pair)
+// Host code only.
 //
 // Counting convention: add/sub, mul, div, sqrt and each transcendental call (atan2, log)
 // count 1 flop, fma counts 2; comparisons, min/max, abs and selects count 0 flops (reported
@@ -23,6 +27,7 @@ struct Counted {
   Counted(double x) : v(T(x)) {}
   Counted(float x) : v(T(x)) {}
   Counted(int x) : v(T(x)) {}
+  Counted(long double x) : v(T(x)) {}
   explicit operator bool() const { return v != 0; }
 };
 template <typename T> inline Counted<T> mk(T x) { Counted<T> r; r.v = x; return r; }
@@ -67,6 +72,10 @@ inline Counted<double> fma_f(Counted<double> a, Counted<double> b, Counted<doubl
   ++g_tally.fma;
   return mk<double>(std::fma(a.v, b.v, c.v));
 }
+inline Counted<long double> fma_f(Counted<long double> a, Counted<long double> b, Counted<long double> c) {
+  ++g_tally.fma;
+  return mk<long double>(std::fma(a.v, b.v, c.v));
+}
 inline Counted<double> frexp_f(Counted<double> x, int* e) { return mk<double>(std::frexp(x.v, e)); }
 inline Counted<double> ldexp_f(Counted<double> x, int e) { return mk<double>(std::ldexp(x.v, e)); }
 inline Counted<float> frexp_f(Counted<float> x, int* e) { return mk<float>(std::frexp(x.v, e)); }
@@ -86,10 +95,39 @@ inline Counted<float> diff_of_products(Counted<float> a, Counted<float> b, Count
 inline Counted<double> diff_of_products(Counted<double> a, Counted<double> b, Counted<double> c, Counted<double> d) {
   return a * b - c * d;
 }
+inline Counted<long double> diff_of_products(Counted<long double> a, Counted<long double> b, Counted<long double> c,
+                                             Counted<long double> d) {
+  return a * b - c * d;
+}
+template <> struct Tiny<Counted<long double>> { static Counted<long double> v() { return Counted<long double>(1e-150); } };
 template <> struct Tiny<Counted<double>> { static Counted<double> v() { return Counted<double>(1e-150); } };
 template <> struct Tiny<Counted<float>> { static Counted<float> v() { return Counted<float>(1e-18f); } };
 template <> struct Acc<Counted<double>> {
   using R = Counted<double>;
+  using T = R;
+  static R c(double v) { return R(v); }
+  static R c2(double num, double den) { return R(num / den); }
+  static R from(R v) { return v; }
+  static R sq(R v) { return v * v; }
+  static R root(R v) { return sqrt(v); }
+  static R out(R v) { return v; }
+  static R mulr(R a, R b) { return a * b; }
+  static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
+  using Sum = R;
+  static R zero() { return R(0.0); }
+  template <class P>
+  static R madd(R acc, R x, int row, int slot) {
+    const NumDen c = edge_coef<P>(row - 1, slot);
+    const double k = c.num / c.den;
+    if (k == 0.0) return acc;
+    return fma_f(x, R(k), acc);
+  }
+  static R result(R a) { return a; }
+  static R recip1(int, R iq) { return iq; }
+};
+// the method count: the plain closed form (uncompensated sums) for every kernel
+template <> struct Acc<Counted<long double>> {
+  using R = Counted<long double>;
   using T = R;
   static R c(double v) { return R(v); }
   static R c2(double num, double den) { return R(num / den); }
@@ -184,11 +222,13 @@ static void count_kernel(int kid, int md, const double* l) {
 extern "C" {
 // Count the operations of one pair (local-frame triangle l[6], H = 1) with moments up to
 // `moment_degree` (-1..3; 2 and 3 compute all ten, 1 the first three, as the kernels do).
+// kind: 0 the FP64 path, 1 the compensated FP32 form, 2 the method (plain closed form).
 // out[7] = add, mul, fma, div, sqrt, transcendental, other.  Returns flops (fma = 2).
-int64_t sph2d_count_pair_ops(int kernel, int moment_degree, int fp32, const double* l, int64_t* out) {
+int64_t sph2d_count_pair_ops(int kernel, int moment_degree, int kind, const double* l, int64_t* out) {
   sph2d::g_tally = sph2d::OpTally{};
   const int md = moment_degree >= 2 ? 3 : (moment_degree == 1 ? 1 : 0);
-  if (fp32) sph2d::count_kernel<sph2d::Counted<float>>(kernel, md, l);
+  if (kind == 1) sph2d::count_kernel<sph2d::Counted<float>>(kernel, md, l);
+  else if (kind == 2) sph2d::count_kernel<sph2d::Counted<long double>>(kernel, md, l);
   else sph2d::count_kernel<sph2d::Counted<double>>(kernel, md, l);
   const sph2d::OpTally& t = sph2d::g_tally;
   if (out) {

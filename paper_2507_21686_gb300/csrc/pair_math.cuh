@@ -140,8 +140,9 @@ template <typename R> struct Tiny;
 template <> struct Tiny<double> { SPH2D_HD static constexpr double v() { return 1e-150; } };
 template <> struct Tiny<float> { SPH2D_HD static constexpr float v() { return 1e-18f; } };
 
-// a*b - c*d.  In FP32 Kahan's compensated form (error <= 1.5 ulp of the result), so that a
-// cross product of nearly parallel vectors keeps its relative accuracy.
+// a*b - c*d.  In FP32 Kahan's compensated form (W. Kahan's algorithm for ad - bc; error bound
+// 1.5 ulp of the result from C.-P. Jeannerod, N. Louvet, J.-M. Muller, Math. Comp. 82 (2013)),
+// so that a cross product of nearly parallel vectors keeps its relative accuracy.
 SPH2D_HD double diff_of_products(double a, double b, double c, double d) { return a * b - c * d; }
 SPH2D_HD float diff_of_products(float a, float b, float c, float d) {
 #if defined(__CUDA_ARCH__)
@@ -176,6 +177,13 @@ SPH2D_HD R asinh_diff(R t1, R t2, R r1, R r2, R d) {
 // error-free transformations.  Used for the radial recurrence and the kernel-coefficient
 // sums of the FP32 path, whose alternating coefficients (sum |b_k|/(k+2) is 140x to 9000x
 // the result for C2..C6) would otherwise amplify FP32 rounding by the same factor.
+// Published sources of the building blocks: two-sum (D. E. Knuth, TAOCP vol. 2, Sec. 4.2.2),
+// fast two-sum and the splitting of a double into two halves (T. J. Dekker, "A floating-point
+// technique for extending the available precision", Numer. Math. 18, 1971), the FMA two-product
+// (the exact residual fma(a, b, -a*b); see T. Ogita, S. M. Rump, S. Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005), and pair addition, multiplication and division
+// by two quotient digits (Dekker 1971, in the double-length arithmetic of D. H. Bailey's
+// double-double libraries).
 // ---------------------------------------------------------------------------------------
 template <typename F>
 struct FFT {
@@ -437,7 +445,8 @@ SPH2D_ROWS(PolyCube, g_rows_cube)
 #undef SPH2D_ROWS
 
 // compensated running sum for the FF / double-double paths: s + c, where every product
-// x*k is formed to ~2^-2p and every addition's rounding error goes into c
+// x*k is formed to ~2^-2p and every addition's rounding error goes into c (compensated
+// summation with two-sum, the "Dot2" scheme of Ogita, Rump and Oishi 2005)
 template <typename F>
 struct CSum {
   F s, c;
@@ -453,40 +462,42 @@ SPH2D_HD CSum<F> csum_madd(CSum<F> a, FFT<F> x, F khi, F klo) {
   return CSum<F>{s, a.c + (err + pl)};
 }
 
-// accumulation type of the radial part: double for the FP64 path, FF for the FP32 path
-template <typename R> struct Acc;
-template <> struct Acc<double> {
-  using T = double;
-  SPH2D_HD static constexpr double c(double v) { return v; }
-  SPH2D_HD static constexpr double c2(double num, double den) { return num / den; }
-  SPH2D_HD static double from(double v) { return v; }
-  SPH2D_HD static double sq(double v) { return v * v; }
-  SPH2D_HD static double root(double v) { return sqrt(v); }
-  SPH2D_HD static double out(double v) { return v; }
-  SPH2D_HD static double mulr(double a, double b) { return a * b; }
-  using Sum = double;
-  SPH2D_HD static double zero() { return 0.0; }
+// accumulation type of the radial part: plain arithmetic in the base precision F (the FP64
+// path, and the bulk FP32 path), or FF compensated FP32 (the FP32 path's compensated form)
+template <typename F>
+struct AccPlain {
+  using T = F;
+  SPH2D_HD static constexpr F c(double v) { return F(v); }
+  SPH2D_HD static constexpr F c2(double num, double den) { return F(num / den); }
+  SPH2D_HD static F from(F v) { return v; }
+  SPH2D_HD static F sq(F v) { return v * v; }
+  SPH2D_HD static F root(F v) { return sqrt(v); }
+  SPH2D_HD static F out(F v) { return v; }
+  SPH2D_HD static F mulr(F a, F b) { return a * b; }
+  using Sum = F;
+  SPH2D_HD static F zero() { return F(0); }
   template <class P>
-  SPH2D_HD static double madd(double acc, double x, int row, int slot) {
+  SPH2D_HD static F madd(F acc, F x, int row, int slot) {
 #if SPH2D_Q_UNROLL
     const NumDen c = edge_coef<P>(row - 1, slot);
-    const double k = c.num / c.den;
+    const F k = F(c.num / c.den);
 #else
-    const double k = edge_rows<P>().d[row][slot];
+    const F k = sizeof(F) == sizeof(double) ? F(edge_rows<P>().d[row][slot]) : F(edge_rows<P>().fhi[row][slot]);
 #endif
-    return k == 0.0 ? acc : fma_f(x, k, acc);      // zero test is uniform across the warp
+    return k == F(0) ? acc : fma_f(x, k, acc);      // zero test is uniform across the warp
   }
-  SPH2D_HD static double recip1(int, double iq) { return iq; }
-  SPH2D_HD static double maddc(double acc, double x, double num, double den) {
-    return num == 0.0 ? acc : fma_f(x, num / den, acc);
+  SPH2D_HD static F recip1(int, F iq) { return iq; }
+  SPH2D_HD static F maddc(F acc, F x, double num, double den) {
+    return num == 0.0 ? acc : fma_f(x, F(num / den), acc);
   }
-  SPH2D_HD static double result(double acc) { return acc; }
-  SPH2D_HD static double jm1(double t1, double t2, double r1, double r2, double d, double ra,
-                             double rb) {
+  SPH2D_HD static F result(F acc) { return acc; }
+  SPH2D_HD static F jm1(F t1, F t2, F r1, F r2, F d, F ra, F rb) {
     (void)ra; (void)rb;
     return asinh_diff(t1, t2, r1, r2, d);
   }
 };
+template <typename R> struct Acc;
+template <> struct Acc<double> : AccPlain<double> {};
 // FP32 (or an FP32-like scalar F): compensated accumulation
 template <typename F>
 struct AccFF {
@@ -577,16 +588,19 @@ struct AccDD {
   SPH2D_HD static D result(CSum<D> a) { return a.s + a.c; }
 };
 
-// accumulation type per precision and kernel polynomial
-template <typename R, class P> struct AccSel { using type = Acc<R>; };
-template <> struct AccSel<double, PolyWC6> { using type = AccDD<double>; };
+// accumulation type per precision and kernel polynomial (PLAIN: the uncompensated form of
+// the FP32 path)
+template <typename R, class P, bool PLAIN = false> struct AccSel { using type = Acc<R>; };
+template <> struct AccSel<double, PolyWC6, false> { using type = AccDD<double>; };
+template <class P> struct AccSel<float, P, true> { using type = AccPlain<float>; };
 
 // ---------------------------------------------------------------------------------------
 // one edge (fan (0, A, B)) of a triangle for the polynomial kernel P; accumulates the
 // signed fan integrals into o (global frame, raw)
 // ---------------------------------------------------------------------------------------
-// MD: moment degree computed, 0 (none), 1 (M00, M10, M01) or 3 (all ten)
-template <typename R, class P, int MD>
+// MD: moment degree computed, 0 (none), 1 (M00, M10, M01) or 3 (all ten); PLAIN: the FP32
+// path's uncompensated form
+template <typename R, class P, int MD, bool PLAIN = false>
 SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   const R ex = bx - ax, ey = by - ay;
   const R l2 = ex * ex + ey * ey;
@@ -652,7 +666,7 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   // same side (or d >= 1); it is then skipped, which keeps every power rho^q <= 1 and makes
   // its contribution exactly zero whatever the compiler contracts into FMAs.
   if (t1 != t2) {
-    using AC = typename AccSel<R, P>::type;
+    using AC = typename AccSel<R, P, PLAIN>::type;
     using A = typename AC::T;
     const A d2a = AC::sq(d);
     const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
@@ -751,13 +765,13 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
 }
 
 // signed sum over the three fans of one local-frame triangle, single polynomial piece
-template <typename R, class P, int MD, bool UNROLL_FANS>
+template <typename R, class P, int MD, bool UNROLL_FANS, bool PLAIN = false>
 SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   R x0 = ax, y0 = ay, x1 = bx, y1 = by, x2 = cx, y2 = cy;
   if constexpr (UNROLL_FANS) {
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      add_fan<R, P, MD>(x0, y0, x1, y1, o);
+      add_fan<R, P, MD, PLAIN>(x0, y0, x1, y1, o);
       const R tx = x0, ty = y0;
       x0 = x1;
       y0 = y1;
@@ -769,7 +783,7 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   } else {
 #pragma unroll 1
     for (int e = 0; e < 3; ++e) {
-      add_fan<R, P, MD>(x0, y0, x1, y1, o);
+      add_fan<R, P, MD, PLAIN>(x0, y0, x1, y1, o);
       const R tx = x0, ty = y0;
       x0 = x1;
       y0 = y1;
@@ -783,12 +797,12 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
 
 // raw integrals of kernel KID over the local-frame triangle, in input orientation
 // (multiply by the orientation sign for the unsigned integral)
-template <typename R, int KID, int MD>
+template <typename R, int KID, int MD, bool PLAIN = false>
 SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   clear(o);
-  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, true>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, true>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, true>(ax, ay, bx, by, cx, cy, o);
+  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, true, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, true, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, true, PLAIN>(ax, ay, bx, by, cx, cy, o);
   else {
     // k(q) = 2 k1(q) - k1(2q), k1 = (1-q)^3_+.  With p' = 2p:
     //   int f(p) k1(2|p|) dA = 1/4 int f(p'/2) k1(|p'|) dA',  f = p^m -> 2^-m
@@ -799,7 +813,7 @@ SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
       const R sc = piece ? R(2) : R(1);
       PairOut<R> h;
       clear(h);
-      tri_poly<R, PolyCube, MD, false>(sc * ax, sc * ay, sc * bx, sc * by, sc * cx, sc * cy, h);
+      tri_poly<R, PolyCube, MD, false, PLAIN>(sc * ax, sc * ay, sc * bx, sc * by, sc * cx, sc * cy, h);
       const R wg = piece ? R(-0.25) : R(2);     // 2^-(m+2), m = 0
       const R wd = piece ? R(-0.5) : R(2);      // gradient
       o.g += wg * h.g;

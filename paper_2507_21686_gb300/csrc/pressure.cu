@@ -184,14 +184,14 @@ __global__ void mls_points_kernel(PGrid g, const float4* __restrict__ parts, con
   out[i] = mls_eval<R, KID>(g, parts, vol, pres, R(pts[2 * i]), R(pts[2 * i + 1]));
 }
 
-// model 1: pressures at the triangle vertices (float, the field pass's input type)
+// model 1: pressures at the triangle vertices, in the mode's precision (double for FP64)
 template <typename R, int KID>
 __global__ void mls_vertices_kernel(PGrid g, const float4* __restrict__ parts, const float* __restrict__ vol,
                                     const float* __restrict__ pres, const float* __restrict__ tris, int64_t M3,
-                                    float* __restrict__ out) {
+                                    R* __restrict__ out) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= M3) return;
-  out[i] = float(mls_eval<R, KID>(g, parts, vol, pres, R(tris[2 * i]), R(tris[2 * i + 1])));
+  out[i] = mls_eval<R, KID>(g, parts, vol, pres, R(tris[2 * i]), R(tris[2 * i + 1]));
 }
 
 // point of the triangle's boundary closest to (x, y)
@@ -280,9 +280,12 @@ __global__ void __launch_bounds__(128) contact_pressure_kernel(FieldArgs f, Pres
 // model 1, one pair: the linear vertex-pressure field's gradient term and the pair's grad gamma
 // from one closed-form evaluation; v[1..2] = -(1/rho_0b) <grad p>_T - rho_0b p_i/rho_i^2 grad
 // gamma_T (the field gradient as in the linear-field pass: (a/H) gamma - sum_j p_j d gamma /
-// d nu_j); v[0] = <p>_T
+// d nu_j); v[0] = <p>_T.  The vertex sum is taken relative to the first vertex's pressure:
+// sum_j p_j d gamma/d nu_j = -p_0 grad gamma_T + sum_j (p_j - p_0) d gamma/d nu_j, because the
+// vertex gradients of a triangle sum to -grad gamma_T (translation invariance).  The same value,
+// without the cancelling sum p_0 sum_j d gamma/d nu_j (terms of size 1/H summing to grad gamma).
 template <typename OT, int KID>
-__device__ __forceinline__ int vertex_pressure_pair(const IntArgs& a, const PressArgs& pa, const float* pv, int pid,
+__device__ __forceinline__ int vertex_pressure_pair(const IntArgs& a, const PressArgs& pa, const OT* pv, int pid,
                                                     int tid, OT* v) {
   OT w[nv_of(1)];                           // gamma, grad gamma, M00, M10, M01
   int fix = eval_pair<OT, KID, 1>(a, pid, tid, w);
@@ -315,13 +318,13 @@ __device__ __forceinline__ int vertex_pressure_pair(const IntArgs& a, const Pres
   const OT kg = OT(pa.rho0b) * OT(__ldg(pa.pres + pid)) / (r * r);
   const OT ib = OT(1.0 / pa.rho0b);
   const OT iD = OT(1) / D;
-  const float* P = pv + 3 * int64_t(tid);
-  const OT a0 = OT(__ldg(P)), a1 = OT(__ldg(P + 1)), a2 = OT(__ldg(P + 2));
+  const OT* P = pv + 3 * int64_t(tid);
+  const OT a0 = __ldg(P), a1 = __ldg(P + 1), a2 = __ldg(P + 2);
   const OT d1 = a1 - a0, d2 = a2 - a0;
   const OT gx = (d1 * e2y - d2 * e1y) * iD, gy = (d2 * e1x - d1 * e2x) * iD;
   const OT ih = OT(a.invH);
-  const OT fx = gx * ih * w[0] - (a0 * g[0] + a1 * g[2] + a2 * g[4]);
-  const OT fy = gy * ih * w[0] - (a0 * g[1] + a1 * g[3] + a2 * g[5]);
+  const OT fx = gx * ih * w[0] + a0 * w[1] - (d1 * g[2] + d2 * g[4]);
+  const OT fy = gy * ih * w[0] + a0 * w[2] - (d1 * g[3] + d2 * g[5]);
   v[0] = a0 * w[0] + gx * (w[4] - l[0] * w[0]) + gy * (w[5] - l[1] * w[0]);
   v[1] = -ib * fx - kg * w[1];
   v[2] = -ib * fy - kg * w[2];
@@ -330,7 +333,7 @@ __device__ __forceinline__ int vertex_pressure_pair(const IntArgs& a, const Pres
 
 // model 1: one fused pair pass, segmented sums as contact_pressure_kernel
 template <typename OT, int KID>
-__global__ void __launch_bounds__(128) vertex_pressure_kernel(FieldArgs f, PressArgs pa, const float* __restrict__ pv) {
+__global__ void __launch_bounds__(128) vertex_pressure_kernel(FieldArgs f, PressArgs pa, const OT* __restrict__ pv) {
   constexpr int NV = 3 * kMaxFields;
   const IntArgs& a = f.a;
   const int64_t nchunks = (a.P + 31) >> 5;
@@ -385,7 +388,7 @@ sph2d_status launch_mls_points(Ctx* c, int kernel, int mode, const float* vol, c
 }
 
 template <typename R>
-static sph2d_status mls_vertices_t(Ctx* c, int kernel, const float* vol, const float* pres, float* out) {
+static sph2d_status mls_vertices_t(Ctx* c, int kernel, const float* vol, const float* pres, R* out) {
   const PGrid g = pgrid_of(c);
   const auto* parts = reinterpret_cast<const float4*>(c->cells.particles);
   const int64_t M3 = 3 * c->cells.M;
@@ -401,7 +404,7 @@ static sph2d_status mls_vertices_t(Ctx* c, int kernel, const float* vol, const f
 }
 
 template <typename OT, int KID>
-static sph2d_status launch_pass(Ctx* c, int model, const FieldArgs& f, const PressArgs& pa, const float* pv,
+static sph2d_status launch_pass(Ctx* c, int model, const FieldArgs& f, const PressArgs& pa, const OT* pv,
                                 int64_t want) {
   if (model == 1) {
     SPH2D_LAUNCH(c, (vertex_pressure_kernel<OT, KID>), resident_blocks(c, vertex_pressure_kernel<OT, KID>, want), 128,
@@ -418,7 +421,7 @@ static sph2d_status launch_pass(Ctx* c, int model, const FieldArgs& f, const Pre
 
 // one fused pair pass of model 1 (pv: vertex pressures) or model 2
 template <typename OT>
-static sph2d_status run_pressure_pass(Ctx* c, int kernel, int model, FieldArgs f, PressArgs pa, const float* pv) {
+static sph2d_status run_pressure_pass(Ctx* c, int kernel, int model, FieldArgs f, PressArgs pa, const OT* pv) {
   constexpr int NV = 3 * kMaxFields;
   const int64_t nchunks = (f.a.P + 31) >> 5;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
@@ -448,18 +451,17 @@ sph2d_status launch_boundary_pressure(Ctx* c, int kernel, int mode, int model, c
   s = ensure(c, c->pres_tmp, size_t(N > 0 ? N : 1) * osz);
   if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
   if (s != SPH2D_OK) return s;
-  const float* pv = nullptr;
+  const void* pv = nullptr;
   if (model == 1) {
-    // vertex pressures (float, as the field tables), three per triangle
-    s = ensure(c, c->pres_vertex, size_t(3 * cl.M > 0 ? 3 * cl.M : 1) * sizeof(float));
+    // vertex pressures in the mode's precision, three per triangle
+    s = ensure(c, c->pres_vertex, size_t(3 * cl.M > 0 ? 3 * cl.M : 1) * osz);
     if (s != SPH2D_OK) return s;
-    auto* pvm = static_cast<float*>(c->pres_vertex.ptr);
     if (cl.M > 0) {
-      s = mode == SPH2D_FP64 ? mls_vertices_t<double>(c, kernel, vol, pres, pvm)
-                             : mls_vertices_t<float>(c, kernel, vol, pres, pvm);
+      s = mode == SPH2D_FP64 ? mls_vertices_t<double>(c, kernel, vol, pres, static_cast<double*>(c->pres_vertex.ptr))
+                             : mls_vertices_t<float>(c, kernel, vol, pres, static_cast<float*>(c->pres_vertex.ptr));
       if (s != SPH2D_OK) return s;
     }
-    pv = pvm;
+    pv = c->pres_vertex.ptr;
   }
   FieldArgs f{};
   IntArgs& a = f.a;
@@ -486,8 +488,8 @@ sph2d_status launch_boundary_pressure(Ctx* c, int kernel, int mode, int model, c
     if (s != SPH2D_OK) return s;
   }
   PressArgs pa{pgrid_of(c), vol, pres, rho, rho0b, model == 2 ? c->pair_vals.ptr : nullptr};
-  s = mode == SPH2D_FP64 ? run_pressure_pass<double>(c, kernel, model, f, pa, pv)
-                         : run_pressure_pass<float>(c, kernel, model, f, pa, pv);
+  s = mode == SPH2D_FP64 ? run_pressure_pass<double>(c, kernel, model, f, pa, static_cast<const double*>(pv))
+                         : run_pressure_pass<float>(c, kernel, model, f, pa, static_cast<const float*>(pv));
   if (s != SPH2D_OK) return s;
   e = cudaMemcpyAsync(c->pinned + 8, a.nfix, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "fixup count copy");

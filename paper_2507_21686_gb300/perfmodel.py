@@ -2,7 +2,11 @@
 
 The op counts come from ``libsph2d_opcount.so``, which instantiates the same closed-form
 pair code as the CUDA kernels with an operation-counting scalar type (add, mul, div, sqrt and
-each transcendental = 1 flop, fma = 2).  Peaks are derived from GB300 unit counts and clocks.
+each transcendental = 1 flop, fma = 2).  Three counts per pair:
+    "method"  the closed form in plain arithmetic: the algorithmic work of the roofline
+    "fp32"    the compensated FP32 form (error-free transformations counted as work)
+    "fp64"    the FP64 path as it runs
+Peaks are derived from GB300 unit counts and clocks.
 """
 from __future__ import annotations
 
@@ -53,21 +57,31 @@ def _degree(moments) -> int:
     return int(moments)
 
 
-def pair_ops(kernel, moments, fp32: bool, local_tri) -> tuple[int, np.ndarray]:
+COUNT_KINDS = {"fp64": 0, "fp32": 1, "method": 2}
+
+
+def _kind(kind) -> int:
+    """'fp64' | 'fp32' | 'method' (True / False: the compensated FP32 form / the FP64 path)."""
+    if isinstance(kind, bool):
+        return 1 if kind else 0
+    return COUNT_KINDS[kind]
+
+
+def pair_ops(kernel, moments, kind, local_tri) -> tuple[int, np.ndarray]:
     """(flops, [add, mul, fma, div, sqrt, transcendental, other]) for one local-frame pair."""
     lib = _load()
     l = np.ascontiguousarray(local_tri, dtype=np.float64).reshape(6)
     out = np.zeros(7, dtype=np.int64)
     k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    f = lib.sph2d_count_pair_ops(k, _degree(moments), int(bool(fp32)), l.ctypes.data, out.ctypes.data)
+    f = lib.sph2d_count_pair_ops(k, _degree(moments), _kind(kind), l.ctypes.data, out.ctypes.data)
     return int(f), out
 
 
-def mean_flops_per_pair(kernel, moments: bool, fp32: bool, local_tris: np.ndarray) -> float:
+def mean_flops_per_pair(kernel, moments, kind, local_tris: np.ndarray) -> float:
     """Average over a sample of real pairs (rows of local-frame triangles, H = 1)."""
-    return float(np.mean([pair_ops(kernel, moments, fp32, t)[0] for t in local_tris]))
+    return float(np.mean([pair_ops(kernel, moments, kind, t)[0] for t in local_tris]))
 
 
-def mean_ops_per_pair(kernel, moments: bool, fp32: bool, local_tris: np.ndarray) -> float:
+def mean_ops_per_pair(kernel, moments, kind, local_tris: np.ndarray) -> float:
     """Floating-point operations per pair with fma counted once (lane-operations)."""
-    return float(np.mean([pair_ops(kernel, moments, fp32, t)[1][:6].sum() for t in local_tris]))
+    return float(np.mean([pair_ops(kernel, moments, kind, t)[1][:6].sum() for t in local_tris]))

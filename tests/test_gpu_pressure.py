@@ -9,7 +9,7 @@ import pytest
 import oracle
 from oracle import pressure as OP
 from paper_2507_21686_gb300 import workloads as W
-from tests.helpers import scales
+from tests.helpers import TOL_FP32, TOL_FP64, scales
 
 pytestmark = pytest.mark.gpu
 
@@ -78,10 +78,7 @@ def test_boundary_pressure_vs_oracle(ctx, hydro, kernel, model, mode):
     ref = OP.boundary_pressure(kernel, w.H, w.particles, w.triangles, off, pt, ex["density"], ex["pressure"],
                                ex["volume"], ex["rho0_b"], model, sample=sample)
     sc = accel_scale(kernel, w, ex)
-    # model 1 stores the vertex pressures as float32 (the field pass's input): the FP64 MLS of
-    # the two sides may round a vertex value to neighbouring floats (6e-8 of p), which the
-    # field gradient carries into the acceleration at up to a few times that
-    tol = (3e-7 if model == 1 else 1e-9) if mode == "fp64" else 2e-5
+    tol = TOL_FP64 if mode == "fp64" else TOL_FP32
     err = np.max(np.abs(acc[sample] - ref)) / sc
     assert err <= tol, err
     assert np.max(np.abs(ref)) > 1e-3 * sc
