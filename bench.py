@@ -57,8 +57,8 @@ def build_parser() -> argparse.ArgumentParser:
                          "smaller values only for profiling captures)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: timed FP32 path only (no FP64 leg, e2e, CPU baseline, L2 flush)")
-    ap.add_argument("--quick-mode", default="fp32_fixup", choices=["fp32_fixup", "fp32_hybrid"],
-                    help="the mode a --quick run times (the headline's FP32 + fix-up, or the hybrid mode)")
+    ap.add_argument("--quick-mode", default="fp32_fixup", choices=["fp32_fixup", "fp32_hybrid", "fp64"],
+                    help="the mode a --quick run times (the headline's FP32 + fix-up, the hybrid mode or FP64)")
     ap.add_argument("--only-leg", default=None, choices=["fields", "fields_p", "pressure", "adjoint"],
                     help="profiling runs: only this widened leg, FP32 modes only, on the benchmark workload")
     return ap
@@ -266,6 +266,19 @@ def run_ours(args):
     from paper_2507_21686_gb300.api import Context
 
     dev = torch.device("cuda", local)
+    # measured FMA peaks of this GPU (the library's microbenchmark), clocks sampled meanwhile
+    from paper_2507_21686_gb300.api import measure_fma_peak
+    if args.quick or args.only_leg or args.only_surrogate:      # profiling runs: derived peaks
+        fma_peaks = {"fp32_tflops": PM.fp32_peak_tflops(), "fp64_tflops": PM.FP64_PEAK_TFLOPS_NOMINAL,
+                     "how": "not measured in profiling runs: derived FP32 and nominal FP64 figures"}
+    else:
+        ps = ClockSampler(local)
+        ps.start()
+        fma_peaks = {"fp32_tflops": measure_fma_peak(local, "fp32", 0.3),
+                     "fp64_tflops": measure_fma_peak(local, "fp64", 0.3)}
+        fma_peaks["clocks"] = ps.stop()
+        fma_peaks["how"] = ("sph2d_measure_fma_peak: 8 independent fma chains per thread, occupancy-sized grid, "
+                            "~0.3 s launch timed with CUDA events, best of 3 (burst figure)")
     w = W.box_obstacle(2, args.box_n) if args.box_n != 1024 else W.box_obstacle()
     N, M = len(w.particles), len(w.triangles)
     parts_h = torch.from_numpy(w.particles).pin_memory()
@@ -394,7 +407,7 @@ def run_ours(args):
     kmeans = [float(np.mean(x)) for x in kms[1:]]
     dom = int(np.argmax(kmeans))
     dom_k = KERNELS[dom]
-    peak = PM.fp32_peak_tflops()
+    peak = fma_peaks["fp32_tflops"]
     achieved = method[dom_k] * P / (kmeans[dom] / 1e3) / 1e12
     lane_peak = PM.fp32_lane_op_peak_tops()
     achieved_tops = ops32[dom_k] * P / (kmeans[dom] / 1e3) / 1e12
@@ -498,8 +511,8 @@ def run_ours(args):
                      "derivation": (f"achieved = {method[dom_k]:.0f} method flops per pair (plain closed form, "
                                     f"fma = 2, op counter's method instantiation) x {P} pairs / "
                                     f"{kmeans[dom]:.3f} ms (CUDA events)"),
-                     "peak_basis": ("derived FP32 FMA-flop peak: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz "
-                                    "(unit counts and max clock; no measured FP32 peak)"),
+                     "peak_basis": ("measured FP32 FMA peak of this GPU (fma_peaks; the derived figure "
+                                    f"152 SMs x 128 lanes x 2 x 2070 MHz is {PM.fp32_peak_tflops():.1f} TFLOP/s)"),
                      "per_kernel_frac": {k: method[k] * P / (t / 1e3) / 1e12 / peak for k, t in zip(KERNELS, kmeans)},
                      "pipe_util": {"issued_lane_ops_per_pair": ops32[dom_k],
                                    "method_lane_ops_per_pair": method_ops[dom_k],
@@ -511,7 +524,10 @@ def run_ours(args):
         "cull_ms": cull_ms,
         "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
                       "per_kernel_ms": dict(zip(KERNELS, k64)),
-                      "achieved_tflops": achieved64, "nominal_peak_tflops": PM.FP64_PEAK_TFLOPS_NOMINAL,
+                      "achieved_tflops": achieved64, "peak_tflops": fma_peaks["fp64_tflops"],
+                      "frac": achieved64 / fma_peaks["fp64_tflops"],
+                      "peak_basis": "measured FP64 FMA peak of this GPU (fma_peaks)",
+                      "nominal_peak_tflops": PM.FP64_PEAK_TFLOPS_NOMINAL,
                       "frac_of_nominal": achieved64 / PM.FP64_PEAK_TFLOPS_NOMINAL,
                       "flops_per_pair": flops64[KERNELS[dom64]]},
         "speedup_vs_fp64_path": agg["value"] / value64,
@@ -529,6 +545,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "measured_peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+        "fma_peaks": fma_peaks,
     }
     print(json.dumps(line), flush=True)
 
@@ -747,6 +764,7 @@ def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3
     gen_s = time.time() - t0
     tpd = torch.from_numpy(tp).to(dev)
     ctx.surrogate_init(k, 5)
+    ctx.set_surrogate_audit(64, 1e-3)
     epochs, batch, lr = 60, 16384, 5e-3
     torch.cuda.synchronize()
     t0 = time.time()
@@ -774,6 +792,11 @@ def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3
         res[mode] = {"ms": ms, "pairs_per_s": P / (ms / 1e3)}
         if mode == "surrogate":
             res[mode]["fallback_rate"] = st["n_fallback"] / max(P, 1)
+            res[mode]["audit"] = {"period": 64, "tol": 1e-3, "pairs": st["n_audit"],
+                                  "rate": st["n_audit"] / max(P, 1), "over_tol": st["n_audit_over"],
+                                  "max_err": st["audit_max_err"], "redo_pairs": st["n_redo"],
+                                  "note": "audited pairs are re-evaluated by the analytic FP32 path and return "
+                                          "its value; an audited error above tol re-evaluates the whole call"}
     ref = torch.cat([outs["fp64"][0][:, None], outs["fp64"][1]], 1).cpu().numpy()
     for mode in ("surrogate", "fp32_fixup"):
         got = torch.cat([outs[mode][0][:, None], outs[mode][1]], 1).double().cpu().numpy()

@@ -113,6 +113,11 @@ typedef struct {
   int64_t n_cells;          /* cells of the culling grid */
   int64_t n_candidates;     /* (triangle, cell) incidences of the culling grid */
   int64_t n_launches;       /* kernels this context has launched since sph2d_init (cumulative) */
+  /* SPH2D_SURROGATE serving audit (see sph2d_surrogate_set_audit) of the last surrogate call: */
+  int64_t n_audit;          /* accepted pairs also evaluated by the analytic path */
+  int64_t n_audit_over;     /* audited pairs whose network error exceeded the bound */
+  double audit_max_err;     /* largest audited network error, in units of the output scales */
+  int64_t n_redo;           /* pairs re-evaluated analytically because the audit failed (0 or all) */
 } sph2d_stats;
 
 /* Create a context on CUDA device `device`; `stream` is a cudaStream_t (NULL = legacy
@@ -368,7 +373,7 @@ sph2d_status sph2d_boundary_pressure(sph2d_ctx* ctx, int kernel, int mode, int m
 #define SPH2D_SURROGATE_PARAMS 8963
 #define SPH2D_SURROGATE_MIN_SIZE 0.1
 #define SPH2D_SURROGATE_MAX_SIZE 0.45
-#define SPH2D_SURROGATE_MIN_CENTROID 0.2
+#define SPH2D_SURROGATE_MIN_CENTROID 0.3
 #define SPH2D_SURROGATE_MAX_RADIUS 1.5
 
 /* (Re)initialise the surrogate for `kernel`: Glorot-uniform weights from `seed` (64-bit
@@ -416,6 +421,21 @@ sph2d_status sph2d_surrogate_forward(sph2d_ctx* ctx, const float* x, int64_t B, 
 sph2d_status sph2d_surrogate_grad(sph2d_ctx* ctx, const float* x, const float* t, int64_t B,
                                   float* grad, float* loss);
 
+/*
+ * Serving-time audit of the network by the analytic path (sph2d_surrogate_pairs and the
+ * SPH2D_SURROGATE mode).  Of the pairs the guard accepts, those whose index hashes into one of
+ * `period` buckets (about 1 in `period`) are also evaluated by the analytic FP32 path, which
+ * judges the network: the pair's error is the largest over gamma and grad gamma of
+ * |network - analytic| / max(|analytic|, S), S = 1 for gamma and 2 C int_0^1 k(q) dq / H for
+ * the gradient, and the pair returns its analytic value.  If any audited pair's error exceeds
+ * `tol`, the network is not trusted for the call: every pair of the call is re-evaluated by the
+ * analytic path (accepted[] reports 0 for all, n_redo = the pair count).  sph2d_last_stats
+ * reports n_audit, n_audit_over, audit_max_err and n_redo.  period: 0 (off) or a power of two
+ * in [1, 65536]; tol > 0 and finite.  Default for a new context: period 64, tol 1e-3.
+ * Errors: INVALID_ARG.
+ */
+sph2d_status sph2d_surrogate_set_audit(sph2d_ctx* ctx, int period, double tol);
+
 /* Copy the FP32 parameters to / from host memory (n = SPH2D_SURROGATE_PARAMS).  get returns
  * CAPACITY if cap is smaller.  Synchronise.  Errors: NOT_BUILT, INVALID_ARG, CAPACITY, CUDA. */
 sph2d_status sph2d_surrogate_get_params(sph2d_ctx* ctx, float* host, int64_t cap);
@@ -430,6 +450,17 @@ sph2d_status sph2d_surrogate_set_params(sph2d_ctx* ctx, const float* host, int64
  */
 sph2d_status sph2d_surrogate_save(sph2d_ctx* ctx, const char* path);
 sph2d_status sph2d_surrogate_load(sph2d_ctx* ctx, const char* path);
+
+/*
+ * Measurement aid (the paper has no counterpart): FMA throughput of device `device` in
+ * TFLOP/s (2 flops per fma), FP64 (precision 0) or FP32 (precision 1), from eight independent
+ * fma chains per thread over an occupancy-sized grid, timed with CUDA events on a launch of
+ * about `seconds` (0 < seconds <= 10) after a calibration launch; best of three.  Allocates and
+ * frees its own small output buffer and synchronises the device.  The benchmark reports the
+ * pair kernels' FP32 and FP64 arithmetic against these measured peaks.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_measure_fma_peak(int device, int precision, double seconds, double* tflops);
 
 #ifdef __cplusplus
 }

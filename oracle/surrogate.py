@@ -35,7 +35,7 @@ SHAPES = [("W1", (N_HID, N_IN)), ("b1", (N_HID,)), ("W2", (N_HID, N_HID)), ("b2"
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)      # 8963
 
 MIN_SIZE, MAX_SIZE = 0.1, 0.45
-MIN_CENTROID, MAX_RADIUS = 0.2, 1.5
+MIN_CENTROID, MAX_RADIUS = 0.3, 1.5
 SIN_MIN_ANGLE = math.sin(math.radians(15.0))
 
 GELU_K = math.sqrt(2.0 / math.pi)

@@ -293,6 +293,12 @@ class Context:
         check(self.lib, self.h, self.lib.sph2d_surrogate_get_params(self.h, _ptr(p), p.numel()))
         return p
 
+    def set_surrogate_audit(self, period: int = 64, tol: float = 1e-3):
+        """Serving audit: about 1 in `period` accepted pairs (0: off) judged by the analytic path;
+        a call with an audited error above `tol` is evaluated analytically throughout."""
+        check(self.lib, self.h, self.lib.sph2d_surrogate_set_audit(self.h, int(period), float(tol)))
+        return self
+
     def set_surrogate_params(self, p):
         q = torch.as_tensor(p, dtype=torch.float32).contiguous().cpu()
         self._bind_stream()
@@ -306,6 +312,16 @@ class Context:
         self._bind_stream()
         check(self.lib, self.h, self.lib.sph2d_surrogate_load(self.h, str(path).encode()))
         return self
+
+
+def measure_fma_peak(device: int = 0, precision: str = "fp64", seconds: float = 0.2) -> float:
+    """Measured FMA throughput (TFLOP/s) of one GPU in FP64 or FP32 (the library's microbenchmark)."""
+    lib = _lib.load()
+    out = ctypes.c_double()
+    st = lib.sph2d_measure_fma_peak(int(device), 0 if precision == "fp64" else 1, float(seconds), ctypes.byref(out))
+    if st != 0:
+        raise _lib.Sph2dError(f"sph2d_measure_fma_peak: {_lib.STATUS.get(st, st)}")
+    return float(out.value)
 
 
 _contexts: dict[int, Context] = {}

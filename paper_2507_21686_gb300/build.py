@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsph2d.so")
 OPCOUNT_LIB = os.path.join(BUILD, "libsph2d_opcount.so")
 SOURCES = ["sph2d_api.cu", "cells.cu", "integrals.cu", "integrals_fp64.cu", "integrals_fp32.cu",
-           "backward.cu", "noalloc.cu", "surrogate.cu", "fields.cu", "hybrid.cu", "fields_p.cu", "pressure.cu"]
+           "backward.cu", "noalloc.cu", "surrogate.cu", "fields.cu", "hybrid.cu", "fields_p.cu", "pressure.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -56,7 +56,7 @@ SPH2D_HD void edge_poly_integrals(R d, R t1, R t2, R* I) {
       // (q + 1) J_q = t rho^q + q d^2 J_{q-2}
       const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);
       const R qf = R(q), iq = R(1) / R(q + 1);
-      const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);
+      const A dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);
       if (q <= P::K) s0 = AC::maddc(s0, dJ, bk<P>(q), 1.0);
       if (q >= 2) s2 = AC::maddc(s2, dJ, bk<P>(q - 2), 1.0);
       dJq2 = dJq1;

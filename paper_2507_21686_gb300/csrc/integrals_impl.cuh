@@ -410,7 +410,7 @@ __device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double
   const R sc = piece ? R(2) : R(1);
   PairOut<R> h;
   clear(h);
-  tri_poly<R, PolyCube, MD, true>(sc * l[0], sc * l[1], sc * l[2], sc * l[3], sc * l[4], sc * l[5], h);
+  tri_poly<R, PolyCube, MD, false>(sc * l[0], sc * l[1], sc * l[2], sc * l[3], sc * l[4], sc * l[5], h);
   const R k = R(C) * R(s);
   const R wg = piece ? R(-0.25) : R(2), wd = piece ? R(-0.5) : R(2);
   v[0] = (k * wg) * h.g;

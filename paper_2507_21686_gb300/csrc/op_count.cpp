@@ -76,6 +76,7 @@ inline Counted<long double> fma_f(Counted<long double> a, Counted<long double> b
   ++g_tally.fma;
   return mk<long double>(std::fma(a.v, b.v, c.v));
 }
+template <typename T> inline T raw_f(Counted<T> x) { return x.v; }
 inline Counted<double> frexp_f(Counted<double> x, int* e) { return mk<double>(std::frexp(x.v, e)); }
 inline Counted<double> ldexp_f(Counted<double> x, int e) { return mk<double>(std::ldexp(x.v, e)); }
 inline Counted<float> frexp_f(Counted<float> x, int* e) { return mk<float>(std::frexp(x.v, e)); }
@@ -123,7 +124,9 @@ template <> struct Acc<Counted<double>> {
     return fma_f(x, R(k), acc);
   }
   static R result(R a) { return a; }
+  static R resultA(R a) { return a; }
   static R recip1(int, R iq) { return iq; }
+  static R divq(R x, int, R iq) { return x * iq; }
 };
 // the method count: the plain closed form (uncompensated sums) for every kernel
 template <> struct Acc<Counted<long double>> {
@@ -147,7 +150,9 @@ template <> struct Acc<Counted<long double>> {
     return fma_f(x, R(k), acc);
   }
   static R result(R a) { return a; }
+  static R resultA(R a) { return a; }
   static R recip1(int, R iq) { return iq; }
+  static R divq(R x, int, R iq) { return x * iq; }
 };
 template <> struct Acc<Counted<float>> : AccFF<Counted<float>> {};
 template <> struct AccSel<Counted<double>, PolyWC6> { using type = AccDD<Counted<double>>; };

@@ -30,6 +30,8 @@
 
 #include <math.h>
 
+#include "log_table.h"
+
 #if defined(__CUDACC__)
 #define SPH2D_HD __host__ __device__ __forceinline__
 #else
@@ -39,13 +41,19 @@
 
 // Code shape (measured on GB300): the radial recurrence is unrolled with compile-time
 // coefficients (zero terms vanish) -- SPH2D_Q_UNROLL=0 selects a loop over rows of a
-// constant-memory table instead, which measured 15-40% slower.  The three fans of a triangle
-// are inlined for the single-polynomial kernels (more independent work to hide latency) and
-// looped for the two-piece cubic spline, whose six inlined fans overflow the instruction
-// cache (3.5x slower measured).
+// constant-memory table instead, which measured 15-40% slower.  Whether the three fans of a
+// triangle are a loop or inlined is chosen per instantiation (FanLoop below); the two-piece
+// cubic spline loops over its pieces and their fans (six inlined fans overflow the instruction
+// cache: 3.5x slower measured).
 #ifndef SPH2D_Q_UNROLL
 #define SPH2D_Q_UNROLL 1
 #endif
+// compensated division of the recurrence by q + 1: exact small-integer division (1) or a
+// multiplication by the compensated reciprocal (0)
+#ifndef SPH2D_DIVQ
+#define SPH2D_DIVQ 1
+#endif
+
 
 namespace sph2d {
 
@@ -113,6 +121,14 @@ SPH2D_HD constexpr double kappa_grad() {
   double s = 0.0;
   for (int k = 1; k <= P::K; ++k) s += double(k) * P::b(k) / double(k + 1);
   return s;
+}
+
+// int_0^1 k(q) dq (the cubic spline: 2 int (1-q)^3 - int_0^(1/2) (1-2q)^3 = (2 - 1/2) int_0^1 (1-q)^3)
+SPH2D_HD constexpr double kernel_int0(int kid) {
+  return kid == KID_WC2 ? kappa<PolyWC2>(1)
+       : kid == KID_WC4 ? kappa<PolyWC4>(1)
+       : kid == KID_WC6 ? kappa<PolyWC6>(1)
+                        : 1.5 * kappa<PolyCube>(1);
 }
 
 // 2-D normalisation constants C (int W = 1)
@@ -313,10 +329,6 @@ SPH2D_HD double ldexp_f(double x, int e) {
   return std::ldexp(x, e);
 #endif
 }
-// highest odd power of the atanh series for the compensated log: |z|^(k+2)/(k+2) must stay
-// below the compensated unit roundoff (2^-48 for float pairs, 2^-104 for double pairs)
-template <typename F> struct LogTerms { static constexpr int top = 19; };
-template <> struct LogTerms<double> { static constexpr int top = 43; };
 SPH2D_HD float ldexp_f(float x, int e) {
 #if defined(__CUDA_ARCH__)
   return ldexpf(x, e);
@@ -324,24 +336,76 @@ SPH2D_HD float ldexp_f(float x, int e) {
   return std::ldexp(x, e);
 #endif
 }
-// natural log of x > 0 in compensated arithmetic: x = m 2^e with m in [1/sqrt2, sqrt2),
-// log m = 2 atanh(z), z = (m-1)/(m+1), |z| <= 0.1716, odd series through z^top (Horner).
+// the machine value of a scalar (the op counter's counted types define their own)
+SPH2D_HD float raw_f(float x) { return x; }
+SPH2D_HD double raw_f(double x) { return x; }
+
+// argument-reduction table of ff_log (log_table.h, written by gen_log_table.py): entry i holds
+// inv = 1/c_i rounded to the working precision (c_i = (64 + i)/128) and -ln(inv) as hi + lo
+template <typename B> struct LogEnt { B inv, hi, lo; };
+#if defined(__CUDACC__)
+static __device__ const LogEnt<float> g_log_table_f_dev[128] = {SPH2D_LOG_TABLE_F};
+static __device__ const LogEnt<double> g_log_table_d_dev[128] = {SPH2D_LOG_TABLE_D};
+#endif
+static const LogEnt<float> g_log_table_f_host[128] = {SPH2D_LOG_TABLE_F};
+static const LogEnt<double> g_log_table_d_host[128] = {SPH2D_LOG_TABLE_D};
+template <bool DBL> struct LogEntType { using type = LogEnt<float>; };
+template <> struct LogEntType<true> { using type = LogEnt<double>; };
+template <bool DBL>
+SPH2D_HD typename LogEntType<DBL>::type log_entry(int i) {
+  if constexpr (DBL) {
+#if defined(__CUDA_ARCH__)
+    return g_log_table_d_dev[i];
+#else
+    return g_log_table_d_host[i];
+#endif
+  } else {
+#if defined(__CUDA_ARCH__)
+    return g_log_table_f_dev[i];
+#else
+    return g_log_table_f_host[i];
+#endif
+  }
+}
+
+// natural log of x > 0 in compensated arithmetic (float pairs, or double pairs for B = double).
+// Table reduction (Tang's method): x = 2^e m with m in [1/sqrt2, sqrt2), and c_i = (64 + i)/128
+// the table point nearest m, so that
+//   ln x = e ln 2 + L_i + ln(1 + r),   r = m inv_i - 1,
+// with inv_i = 1/c_i rounded, L_i = -ln(inv_i) exact for the stored inv_i, r formed from the
+// two-products of both words of m with inv_i (|r| <= 2^-7.5), and ln(1 + r) = sum_k (-1)^(k+1) r^k / k.  The
+// terms through r^NP run in pair arithmetic, the rest (through r^NT) in the base precision:
+// relative to r their base-precision rounding is below the pair's unit roundoff (float pairs:
+// NP = 4, NT = 8; double pairs: NP = 7, NT = 15).  Every x near 1, on either side, has e = 0 and
+// c = 1 (inv = 1, L = 0): r = x - 1 exactly, so a small logarithm keeps its relative accuracy.
 template <typename F, typename B = F>
 SPH2D_HD FFT<F> ff_log(FFT<F> x) {
+  constexpr bool DBL = sizeof(B) == sizeof(double);
+  constexpr int NP = DBL ? 7 : 4, NT = DBL ? 15 : 8;
   int e = 0;
-  const F m = frexp_f(x.hi, &e);
-  if (m < F(0.70710678f)) e -= 1;
-  const FFT<F> xm{ldexp_f(x.hi, -e), ldexp_f(x.lo, -e)};
-  const FFT<F> one{F(1), F(0)};
-  const FFT<F> z = (xm - one) / (xm + one);
-  const FFT<F> z2 = z * z;
-  constexpr int top = LogTerms<B>::top;
-  FFT<F> sum = ffk<F, B>(1.0, double(top));
+  const F m0 = frexp_f(x.hi, &e);                        // [1/2, 1)
+  if (raw_f(m0) < 0.70710678118654752) e -= 1;           // m = x.hi 2^-e in [1/sqrt2, sqrt2)
+  const FFT<F> xm{ldexp_f(x.hi, -e), ldexp_f(x.lo, -e)}; // exact scaling
+  const int i = int(raw_f(xm.hi) * 128 + 0.5) - 64;      // nearest table point (either one at a tie)
+  const auto ent = log_entry<DBL>(i);
+  const F inv = F(ent.inv);
+  const FFT<F> p = ff_two_prod(xm.hi, inv), q = ff_two_prod(xm.lo, inv);   // exact
+  const FFT<F> r = ff_fast_two_sum(p.hi - F(1), p.lo) + q; // p.hi - 1 exact (Sterbenz), |p.hi - 1| >= |p.lo|
+  const F rh = r.hi;
+  F tail = F(((NT & 1) ? 1.0 : -1.0) / double(NT));
 #pragma unroll
-  for (int k = top - 2; k >= 1; k -= 2) sum = sum * z2 + ffk<F, B>(1.0, double(k));
-  const FFT<F> lz = (z * sum) * F(2);
-  return lz + ffln2<F, B>() * F(double(e));
+  for (int k = NT - 1; k > NP; --k) tail = fma_f(tail, rh, F(((k & 1) ? 1.0 : -1.0) / double(k)));
+  F rp = rh;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) rp = rp * rh;             // r^(NP+1)
+  tail = tail * rp;
+  FFT<F> S = ffk<F, B>(((NP & 1) ? 1.0 : -1.0), double(NP));
+#pragma unroll
+  for (int k = NP - 1; k >= 1; --k) S = S * r + ffk<F, B>(((k & 1) ? 1.0 : -1.0), double(k));
+  const FFT<F> l1p = r * S + FFT<F>{tail, F(0)};
+  return (l1p + FFT<F>{F(ent.hi), F(ent.lo)}) + ffln2<F, B>() * F(double(e));
 }
+
 // asinh(t2/d) - asinh(t1/d) in FF (see asinh_diff)
 template <typename F, typename B = F>
 SPH2D_HD FFT<F> asinh_diff_ff(F t1, F t2, FFT<F> r1, FFT<F> r2, F d) {
@@ -367,12 +431,15 @@ SPH2D_HD FFT<F> asinh_diff_ff(F t1, F t2, FFT<F> r1, FFT<F> r2, F d) {
 //   M02, M12         += dJ  b_{q-2}/(q+2) | b_{q-2}/(q+3)   and  dJ d^2 (-b_q/(q+4) | -b_q/(q+5))
 //   M01, M11, M21    += dP  b_{q-2}/((q+1+m-1) q)   (m = 1, 2, 3)
 //   M03              += dP  b_{q-4}/((q+1) q)        and  dP d^2 (-b_{q-2}/((q+3) q))
-// The rows live in constant memory (the step index is uniform across a warp) so the
-// recurrence loop needs no unrolling.
+// The d^2 parts of M02, M12 and M03 are -d^2 times the M20, M30 and M21 sums (same rows), so
+// they are not accumulated: the three sums are S02A - d^2 S20, S12A - d^2 S30 and S03A - d^2 S21,
+// formed once per fan in the accumulation precision.
+// With SPH2D_Q_UNROLL=0 the rows live in constant memory (the step index is uniform across a
+// warp) so the recurrence loop needs no unrolling.
 // ---------------------------------------------------------------------------------------
 enum : int {
-  SL_G = 0, SL_N, SL_T, SL_10, SL_20, SL_30, SL_02A, SL_02B, SL_12A, SL_12B,
-  SL_01, SL_11, SL_21, SL_03A, SL_03B, NSL
+  SL_G = 0, SL_N, SL_T, SL_10, SL_20, SL_30, SL_02A, SL_12A,
+  SL_01, SL_11, SL_21, SL_03A, NSL
 };
 struct NumDen {
   double num, den;
@@ -390,14 +457,11 @@ SPH2D_HD constexpr NumDen edge_coef(int q, int s) {
     case SL_20: return {bk<P>(q), Q + 4};
     case SL_30: return {bk<P>(q), Q + 5};
     case SL_02A: return {bk<P>(q - 2), Q + 2};
-    case SL_02B: return {-bk<P>(q), Q + 4};
     case SL_12A: return {bk<P>(q - 2), Q + 3};
-    case SL_12B: return {-bk<P>(q), Q + 5};
     case SL_01: return q >= 1 ? NumDen{bk<P>(q - 2), (Q + 1) * Q} : NumDen{0.0, 1.0};
     case SL_11: return q >= 1 ? NumDen{bk<P>(q - 2), (Q + 2) * Q} : NumDen{0.0, 1.0};
     case SL_21: return q >= 1 ? NumDen{bk<P>(q - 2), (Q + 3) * Q} : NumDen{0.0, 1.0};
     case SL_03A: return q >= 1 ? NumDen{bk<P>(q - 4), (Q + 1) * Q} : NumDen{0.0, 1.0};
-    case SL_03B: return q >= 1 ? NumDen{-bk<P>(q - 2), (Q + 3) * Q} : NumDen{0.0, 1.0};
   }
   return {0.0, 1.0};
 }
@@ -487,10 +551,12 @@ struct AccPlain {
     return k == F(0) ? acc : fma_f(x, k, acc);      // zero test is uniform across the warp
   }
   SPH2D_HD static F recip1(int, F iq) { return iq; }
+  SPH2D_HD static F divq(F x, int, F iq) { return x * iq; }   // x / (q + 1), iq = 1/(q + 1)
   SPH2D_HD static F maddc(F acc, F x, double num, double den) {
     return num == 0.0 ? acc : fma_f(x, F(num / den), acc);
   }
   SPH2D_HD static F result(F acc) { return acc; }
+  SPH2D_HD static F resultA(F acc) { return acc; }     // the sum as an accumulation-type value
   SPH2D_HD static F jm1(F t1, F t2, F r1, F r2, F d, F ra, F rb) {
     (void)ra; (void)rb;
     return asinh_diff(t1, t2, r1, r2, d);
@@ -538,7 +604,18 @@ struct AccFF {
     const F r = fma_f(-iq, F(float(q + 1)), F(1));
     return FFT<F>{iq, r * iq};
   }
+  // x / (q + 1) for a small integer q + 1: quotient digit, its residual by fma, second digit
+  SPH2D_HD static FFT<F> divq(FFT<F> x, int q, F iq) {
+#if SPH2D_DIVQ
+    const F q1 = x.hi * iq;
+    const F r = fma_f(-q1, F(float(q + 1)), x.hi) + x.lo;
+    return ff_fast_two_sum(q1, r * iq);
+#else
+    return x * recip1(q, iq);
+#endif
+  }
   SPH2D_HD static F result(CSum<F> a) { return a.s + a.c; }
+  SPH2D_HD static FFT<F> resultA(CSum<F> a) { return ff_two_sum(a.s, a.c); }
 };
 template <> struct Acc<float> : AccFF<float> {};
 
@@ -585,7 +662,17 @@ struct AccDD {
     const D r = fma_f(-iq, D(double(q + 1)), D(1));
     return FFT<D>{iq, r * iq};
   }
+  SPH2D_HD static FFT<D> divq(FFT<D> x, int q, D iq) {
+#if SPH2D_DIVQ
+    const D q1 = x.hi * iq;
+    const D r = fma_f(-q1, D(double(q + 1)), x.hi) + x.lo;
+    return ff_fast_two_sum(q1, r * iq);
+#else
+    return x * recip1(q, iq);
+#endif
+  }
   SPH2D_HD static D result(CSum<D> a) { return a.s + a.c; }
+  SPH2D_HD static FFT<D> resultA(CSum<D> a) { return ff_two_sum(a.s, a.c); }
 };
 
 // accumulation type per precision and kernel polynomial (PLAIN: the uncompensated form of
@@ -686,14 +773,13 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
         S01 = AC::template madd<P>(S01, dP, row, SL_01);
       }
       if (MD >= 3) {
-        const A e1 = dJ * d2a, e2 = dP * d2a;
         S20 = AC::template madd<P>(S20, dJ, row, SL_20);
         S30 = AC::template madd<P>(S30, dJ, row, SL_30);
-        S02 = AC::template madd<P>(AC::template madd<P>(S02, dJ, row, SL_02A), e1, row, SL_02B);
-        S12 = AC::template madd<P>(AC::template madd<P>(S12, dJ, row, SL_12A), e1, row, SL_12B);
+        S02 = AC::template madd<P>(S02, dJ, row, SL_02A);
+        S12 = AC::template madd<P>(S12, dJ, row, SL_12A);
         S11 = AC::template madd<P>(S11, dP, row, SL_11);
         S21 = AC::template madd<P>(S21, dP, row, SL_21);
-        S03 = AC::template madd<P>(AC::template madd<P>(S03, dP, row, SL_03A), e2, row, SL_03B);
+        S03 = AC::template madd<P>(S03, dP, row, SL_03A);
       }
     };
     const A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);      // Delta J_{-1}
@@ -715,7 +801,7 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
       const A dP = p2 - p1;                                 // Delta rho^q
       const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);     // Delta (t rho^q)
       const R qf = R(q), iq = R(1) / R(q + 1);
-      const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);   // Delta J_q
+      const A dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);   // Delta J_q
       step(q + 1, dJ, dP);
       dJq2 = dJq1;
       dJq1 = dJ;
@@ -729,13 +815,14 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     }
     if (MD >= 3) {
       const R d3 = d2 * d, d4 = d2 * d2;
-      E[3] += d3 * AC::result(S20);
+      const A s20 = AC::resultA(S20), s30 = AC::resultA(S30), s21 = AC::resultA(S21);
+      E[3] += d3 * AC::out(s20);
       E[4] += d2 * AC::result(S11);
-      E[5] += d * AC::result(S02);
-      E[6] += d4 * AC::result(S30);
-      E[7] += d3 * AC::result(S21);
-      E[8] += d2 * AC::result(S12);
-      E[9] += d * AC::result(S03);
+      E[5] += d * AC::out(AC::resultA(S02) - s20 * d2a);
+      E[6] += d4 * AC::out(s30);
+      E[7] += d3 * AC::out(s21);
+      E[8] += d2 * AC::out(AC::resultA(S12) - s30 * d2a);
+      E[9] += d * AC::out(AC::resultA(S03) - s21 * d2a);
     }
   }
   // rotate the gradient back from the edge frame (Sec. 2, Eq. improper)
@@ -795,14 +882,24 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   }
 }
 
+// Whether the three fans of a single-polynomial kernel run as a loop (one copy of the fan code)
+// or inlined.  Measured on GB300 (the 1024^2 box with obstacle): in FP32 the loop ran 20-23%
+// faster for gamma and grad gamma alone (Wendland C2 and C4) and 6% faster for Wendland C2 with
+// ten moments, and 13% slower for Wendland C4 with ten moments; in FP64 it ran 7% faster for C2
+// with moments and the same for C4.  The cubic spline's pieces loop over their fans as well.
+template <typename R, class P, int MD>
+struct FanLoop {
+  static constexpr bool value = !(MD >= 3 && P::K >= 8);
+};
+
 // raw integrals of kernel KID over the local-frame triangle, in input orientation
 // (multiply by the orientation sign for the unsigned integral)
 template <typename R, int KID, int MD, bool PLAIN = false>
 SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   clear(o);
-  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, true, PLAIN>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, true, PLAIN>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, true, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, !FanLoop<R, PolyWC2, MD>::value, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, !FanLoop<R, PolyWC4, MD>::value, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, !FanLoop<R, PolyWC6, MD>::value, PLAIN>(ax, ay, bx, by, cx, cy, o);
   else {
     // k(q) = 2 k1(q) - k1(2q), k1 = (1-q)^3_+.  With p' = 2p:
     //   int f(p) k1(2|p|) dA = 1/4 int f(p'/2) k1(|p'|) dA',  f = p^m -> 2^-m
@@ -875,7 +972,7 @@ SPH2D_HD void edge_line_integrals(R d, R t1, R t2, R& Jo, R& To) {
     if (q <= P::K) {
       const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);
       const R qf = R(q), iq = R(1) / R(q + 1);
-      const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);
+      const A dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);
       sJ = AC::maddc(sJ, dJ, bk<P>(q), 1.0);
       dJq2 = dJq1;
       dJq1 = dJ;
@@ -966,7 +1063,7 @@ SPH2D_HD void edge_grad_integrals(R d, R t1, R t2, R& Jo, R& S0, R& S2, R& Dk) {
     p2 = p2 * r2a;
     const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);
     const R qf = R(q), iq = R(1) / R(q + 1);
-    const A dJ = (dT + AC::mulr(dJq2 * d2a, qf)) * AC::recip1(q, iq);
+    const A dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);
     sJ = AC::maddc(sJ, dJ, bk<P>(q), 1.0);
     s0 = AC::maddc(s0, dJ, double(q + 2) * bk<P>(q + 2), 1.0);
     s2 = AC::maddc(s2, dJ, double(q) * bk<P>(q), 1.0);

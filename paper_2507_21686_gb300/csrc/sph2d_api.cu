@@ -230,6 +230,13 @@ sph2d_status sph2d_last_stats(const sph2d_ctx* h, sph2d_stats* out) {
     cudaError_t e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return SPH2D_ERR_CUDA;
     out->n_fallback = c.pinned[10];
+    out->n_audit = c.pinned[11];
+    out->n_audit_over = c.pinned[12];
+    uint32_t bits = uint32_t(uint64_t(c.pinned[13]) & 0xffffffffu);
+    float emax;
+    std::memcpy(&emax, &bits, sizeof(emax));
+    out->audit_max_err = emax;
+    out->n_redo = out->n_audit_over > 0 ? out->n_pairs : 0;
   }
   return SPH2D_OK;
 }
@@ -539,6 +546,17 @@ sph2d_status sph2d_surrogate_get_params(sph2d_ctx* h, float* host, int64_t cap) 
   if (!host) return set_err(c, SPH2D_ERR_INVALID_ARG, "null pointer");
   if (cap < SPH2D_SURROGATE_PARAMS) return set_err(c, SPH2D_ERR_CAPACITY, "buffer smaller than SPH2D_SURROGATE_PARAMS");
   return surrogate_get_params(c, host);
+}
+
+sph2d_status sph2d_surrogate_set_audit(sph2d_ctx* h, int period, double tol) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (period < 0 || period > 65536 || (period & (period - 1)) != 0)
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "audit period must be 0 or a power of two up to 65536");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return set_err(c, SPH2D_ERR_INVALID_ARG, "audit bound must be > 0");
+  c->sur_audit_period = period;
+  c->sur_audit_tol = tol;
+  return SPH2D_OK;
 }
 
 sph2d_status sph2d_surrogate_set_params(sph2d_ctx* h, const float* host, int64_t n) {

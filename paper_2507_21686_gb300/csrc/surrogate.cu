@@ -451,9 +451,26 @@ struct SurArgs {
   double C, H, invH;
   float* vals;                    // per-pair (gamma, dgamma/dx, dgamma/dy), world units [P][3]
   int32_t* accepted;              // optional per-pair guard result [P]
-  int64_t* fb_list;               // fallback pair indices (capacity P)
-  unsigned long long* fb_count;   // number of entries in fb_list
+  int64_t* fb_list;               // fallback pair indices from the front, audited ones from the back (capacity P)
+  unsigned long long* fb_count;   // number of fallback entries in fb_list
+  // serving-time audit: one accepted pair in audit_period (0: none) is also evaluated
+  // analytically; au_* are zeroed device counters
+  int audit_period;
+  unsigned audit_shift;           // 64 - log2(audit_period)
+  float audit_tol;                // error bound in units of the output scales
+  float grad_scale;               // scale of the gradient outputs, 2 C int_0^1 k(q) dq / H
+  unsigned long long* au_count;   // audited pairs (entries at the back of fb_list)
+  unsigned long long* au_over;    // audited pairs with an error above audit_tol
+  unsigned* au_max;               // largest audited error (float bits; errors are >= 0)
 };
+
+// whether accepted pair q is audited: a multiplicative hash of its index falls in the first
+// of audit_period buckets (audit_period a power of two)
+__device__ __forceinline__ bool audited(const SurArgs& sa, int64_t q) {
+  if (sa.audit_period <= 0) return false;
+  if (sa.audit_period == 1) return true;
+  return ((unsigned long long)q * 0x9E3779B97F4A7C15ull) >> sa.audit_shift == 0ull;
+}
 
 // per-pair FP32 local frame for the two pair sources: independent pairs (double [P][8]) or
 // the culled pair list (FP32 particles and triangles, same arithmetic as the analytic kernel)
@@ -510,29 +527,84 @@ __global__ void __launch_bounds__(128, 6) surrogate_values_kernel(IntArgs a, con
       base = __shfl_sync(0xffffffffu, base, leader);
       if ((q < a.P) && !use) sa.fb_list[base + __popc(rej & ((1u << lane) - 1u))] = q;
     }
+    // and the audited ones to the back of the same list (a pair is in at most one part, so
+    // the two parts never meet)
+    const bool aud = use && audited(sa, q);
+    const unsigned am = __ballot_sync(0xffffffffu, aud);
+    if (am) {
+      unsigned long long base = 0;
+      const int leader = __ffs(am) - 1;
+      if (lane == leader) base = atomicAdd(sa.au_count, (unsigned long long)__popc(am));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (aud) sa.fb_list[a.P - 1 - int64_t(base + __popc(am & ((1u << lane) - 1u)))] = q;
+    }
     __syncwarp();
   }
 }
 
-// analytic FP32 path (with the FP64 fix-up for far or non-finite geometry) over the list
+// the analytic FP32 path (with the FP64 fix-up for far or non-finite geometry) for pair q
+template <int KID, bool LIST>
+__device__ __forceinline__ void analytic_pair(const IntArgs& a, const double* pairs, int64_t q, float* v) {
+  if (LIST) {
+    eval_pair<float, KID, 0>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
+  } else {
+    double ld[6];
+    float lf[6];
+    pair_local(pairs + 8 * q, a.invH, ld, lf);
+    eval_mode<float, KID, 0>(ld, a.C, a.invH, v);
+  }
+}
+
+// the analytic path over the fallback list, then over the audited pairs: each audited pair's
+// network value is judged against its analytic value, which replaces it
 template <int KID, bool LIST>
 __global__ void __launch_bounds__(128) surrogate_fallback_kernel(IntArgs a, const double* __restrict__ pairs,
                                                                  SurArgs sa) {
   const int64_t n = int64_t(*sa.fb_count);
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t q = sa.fb_list[i];
+  const int64_t na = sa.audit_period > 0 ? int64_t(*sa.au_count) : 0;
+  float emax = 0.0f;
+  unsigned over = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n + na; i += int64_t(gridDim.x) * blockDim.x) {
+    const bool aud = i >= n;
+    const int64_t q = aud ? sa.fb_list[a.P - 1 - (i - n)] : sa.fb_list[i];
     float v[3];
-    if (LIST) {
-      eval_pair<float, KID, 0>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), v);
-    } else {
-      double ld[6];
-      float lf[6];
-      pair_local(pairs + 8 * q, a.invH, ld, lf);
-      eval_mode<float, KID, 0>(ld, a.C, a.invH, v);
+    analytic_pair<KID, LIST>(a, pairs, q, v);
+    if (aud) {
+      const float s[3] = {1.0f, sa.grad_scale, sa.grad_scale};
+      float e = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) e = fmaxf(e, fabsf(sa.vals[3 * q + k] - v[k]) / fmaxf(fabsf(v[k]), s[k]));
+      if (!(e <= sa.audit_tol)) ++over;           // NaN counts as over
+      emax = fmaxf(emax, isfinite(e) ? e : 3.0e38f);
     }
     sa.vals[3 * q] = v[0];
     sa.vals[3 * q + 1] = v[1];
     sa.vals[3 * q + 2] = v[2];
+  }
+  if (sa.audit_period > 0) {
+    const unsigned wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(emax));
+    const unsigned wover = __reduce_add_sync(0xffffffffu, over);
+    if ((threadIdx.x & 31) == 0) {
+      if (wmax) atomicMax(sa.au_max, wmax);
+      if (wover) atomicAdd(sa.au_over, (unsigned long long)wover);
+    }
+  }
+}
+
+// the audit's verdict: if an audited pair was off by more than the bound, the network is not
+// trusted for this call and every pair is evaluated analytically (and reported as not
+// accepted); otherwise the kernel returns at once
+template <int KID, bool LIST>
+__global__ void __launch_bounds__(128) surrogate_redo_kernel(IntArgs a, const double* __restrict__ pairs,
+                                                             SurArgs sa) {
+  if (*sa.au_over == 0ull) return;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < a.P; q += int64_t(gridDim.x) * blockDim.x) {
+    float v[3];
+    analytic_pair<KID, LIST>(a, pairs, q, v);
+    sa.vals[3 * q] = v[0];
+    sa.vals[3 * q + 1] = v[1];
+    sa.vals[3 * q + 2] = v[2];
+    if (sa.accepted) sa.accepted[q] = 0;
   }
 }
 
@@ -817,6 +889,10 @@ static void launch_serving(Ctx* c, const IntArgs& a, const double* pairs, const 
   // the list length is only known on the device: a persistent grid strides over it
   const unsigned g2 = persistent_grid(c, surrogate_fallback_kernel<KID, LIST>, (a.P + 127) / 128);
   SPH2D_LAUNCH(c, (surrogate_fallback_kernel<KID, LIST>), g2, 128, a, pairs, sa);
+  if (sa.audit_period > 0) {
+    const unsigned g3 = persistent_grid(c, surrogate_redo_kernel<KID, LIST>, (a.P + 127) / 128);
+    SPH2D_LAUNCH(c, (surrogate_redo_kernel<KID, LIST>), g3, 128, a, pairs, sa);
+  }
 }
 
 template <bool LIST>
@@ -829,21 +905,33 @@ static void dispatch_serving(Ctx* c, const IntArgs& a, const double* pairs, cons
   }
 }
 
-static sph2d_status serving_setup(Ctx* c, int64_t P, SurArgs& sa) {
+// counters in host_flags_dev: [2] fallback count, [3] audited pairs, [4] audited pairs over the
+// bound, [5] largest audited error (float bits); copied to pinned[10..13] after the call
+static sph2d_status serving_setup(Ctx* c, int64_t P, double H, SurArgs& sa) {
   sph2d_status s = ensure(c, c->sur_fb, size_t(P > 0 ? P : 1) * sizeof(int64_t));
   if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
   if (s != SPH2D_OK) return s;
+  auto* flags = static_cast<unsigned long long*>(c->host_flags_dev.ptr);
   sa.prm = static_cast<const float*>(c->sur_prm.ptr);
   sa.fb_list = static_cast<int64_t*>(c->sur_fb.ptr);
-  sa.fb_count = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 2;
-  cudaError_t e = cudaMemsetAsync(sa.fb_count, 0, sizeof(unsigned long long), c->stream);
+  sa.fb_count = flags + 2;
+  sa.au_count = flags + 3;
+  sa.au_over = flags + 4;
+  sa.au_max = reinterpret_cast<unsigned*>(flags + 5);
+  sa.audit_period = c->sur_audit_period;
+  int lg = 0;
+  while ((1 << lg) < sa.audit_period) ++lg;
+  sa.audit_shift = unsigned(64 - lg);
+  sa.audit_tol = float(c->sur_audit_tol);
+  sa.grad_scale = float(2.0 * kernel_C(c->sur_kernel) * kernel_int0(c->sur_kernel) / H);
+  cudaError_t e = cudaMemsetAsync(sa.fb_count, 0, 4 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   return SPH2D_OK;
 }
 
 static sph2d_status serving_finish(Ctx* c, const SurArgs& sa, int64_t P) {
-  cudaError_t e = cudaMemcpyAsync(c->pinned + 10, sa.fb_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                  c->stream);
+  cudaError_t e = cudaMemcpyAsync(c->pinned + 10, sa.fb_count, 4 * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "fallback count copy");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "surrogate launch");
@@ -856,7 +944,7 @@ static sph2d_status serving_finish(Ctx* c, const SurArgs& sa, int64_t P) {
 
 sph2d_status surrogate_pairs(Ctx* c, const double* pairs, int64_t P, double H, float* out, int32_t* accepted) {
   SurArgs sa{};
-  sph2d_status s = serving_setup(c, P, sa);
+  sph2d_status s = serving_setup(c, P, H, sa);
   if (s != SPH2D_OK) return s;
   sa.C = kernel_C(c->sur_kernel);
   sa.H = H;
@@ -892,7 +980,7 @@ sph2d_status surrogate_integrals(Ctx* c, void* gamma, void* grad) {
   a.mom = nullptr;
   a.nm = 0;
   SurArgs sa{};
-  sph2d_status s = serving_setup(c, a.P, sa);
+  sph2d_status s = serving_setup(c, a.P, cl.H, sa);
   if (s == SPH2D_OK) s = ensure(c, c->sur_vals, size_t(a.P > 0 ? a.P : 1) * 3 * sizeof(float));
   if (s == SPH2D_OK) s = ensure(c, c->slots, size_t(((a.P + 31) >> 5) * 2 * 3 + 1) * sizeof(float));
   if (s != SPH2D_OK) return s;

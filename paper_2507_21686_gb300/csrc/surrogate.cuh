@@ -44,7 +44,7 @@ constexpr int kOffW4 = kOffB3 + kSurHid, kOffB4 = kOffW4 + kSurOut * kSurHid;
 constexpr int kSurParams = kOffB4 + kSurOut;   // 8963
 
 constexpr float kSurMinSize = 0.1f, kSurMaxSize = 0.45f;
-constexpr float kSurMinCentroid = 0.2f, kSurMaxRadius = 1.5f;
+constexpr float kSurMinCentroid = 0.3f, kSurMaxRadius = 1.5f;
 constexpr float kSurSinMinAngle = 0.25881904510252074f;   // sin 15 deg
 
 struct Canon {

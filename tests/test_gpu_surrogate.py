@@ -15,7 +15,7 @@ import pytest
 import oracle
 from oracle import surrogate as S
 from paper_2507_21686_gb300 import workloads as W
-from tests.helpers import TOL_FP32, rel_err, scales
+from tests.helpers import TOL_FP32, TOL_SURROGATE, rel_err, scales
 
 pytestmark = pytest.mark.gpu
 
@@ -98,8 +98,12 @@ def test_grad_matches_reference(ctx, B):
     for name, shape in S.SHAPES:
         n = int(np.prod(shape))
         a, b = g[o:o + n], gref[o:o + n]
-        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert rel < 2e-2, (name, rel)
+        # element by element, in units of the tensor's largest gradient: the reference rounds
+        # every backward operand to BF16 as the GPU does, what remains is FP32 accumulation
+        # order and the hardware tanh of the forward activations
+        err = np.abs(a - b) / np.abs(b).max()
+        assert err.max() < 2e-2, (name, err.max())
+        assert np.median(err) < 2e-3, (name, np.median(err))
         o += n
 
 
@@ -120,6 +124,7 @@ def _local(pairs, H):
 def test_guard_and_fallback(ctx):
     prm = glorot(41)
     ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
+    ctx.set_surrogate_audit(0)                           # an untrained network: audit off
     pairs, H = _world_pairs(20000, 42)
     out, acc = ctx.surrogate_pairs(_t(pairs), H)
     out, acc = out.cpu().numpy().astype(np.float64), acc.cpu().numpy().astype(bool)
@@ -139,6 +144,7 @@ def test_guard_and_fallback(ctx):
 def test_network_values_and_frame(ctx):
     prm = glorot(51)
     ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
+    ctx.set_surrogate_audit(0)                           # compare the raw (untrained) network
     pairs, H = _world_pairs(20000, 52)
     out, acc = ctx.surrogate_pairs(_t(pairs), H)
     out, acc = out.cpu().numpy().astype(np.float64), acc.cpu().numpy().astype(bool)
@@ -153,6 +159,35 @@ def test_network_values_and_frame(ctx):
     err = np.abs(got - want) / scale
     assert np.median(err) < 5e-4, np.median(err)
     assert err.max() < 1e-2, err.max()
+
+
+def test_audit_catches_an_untrained_network(ctx):
+    """The serving audit re-evaluates a sample of accepted pairs analytically; with an untrained
+    network it finds errors far above the bound, and the whole call is evaluated analytically
+    (same values as the analytic FP32 per-pair entry, bit for bit)."""
+    prm = glorot(45)
+    ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
+    ctx.set_surrogate_audit(8, 1e-3)
+    pairs, H = _world_pairs(20000, 46)
+    out, acc = ctx.surrogate_pairs(_t(pairs), H)
+    st = ctx.stats()
+    ana = ctx.pair_integrals(_t(pairs), KERNEL, H, -1, "fp32_fixup").cpu().numpy()
+    cn = S.canonicalize(_local(pairs, H))
+    assert st["n_audit"] > 0.5 * cn["accept"].sum() / 8
+    assert st["n_audit_over"] > 0 and st["audit_max_err"] > 1e-3
+    assert st["n_redo"] == len(pairs)
+    assert not acc.cpu().numpy().any()
+    assert np.array_equal(out.cpu().numpy(), ana)
+    ctx.set_surrogate_audit(64, 1e-3)
+
+
+def test_audit_statuses(ctx):
+    from paper_2507_21686_gb300._lib import Sph2dError
+    for period, tol in ((3, 1e-3), (-1, 1e-3), (131072, 1e-3), (8, 0.0), (8, float("nan"))):
+        with pytest.raises(Sph2dError, match="INVALID_ARG"):
+            ctx.set_surrogate_audit(period, tol)
+    ctx.set_surrogate_audit(0, 1e-3)
+    ctx.set_surrogate_audit(64, 1e-3)
 
 
 def test_training_is_deterministic_and_learns(ctx):
@@ -235,18 +270,23 @@ def test_error_statuses(ctx):
 # ---------------------------------------------------------------------------------------
 @pytest.fixture(scope="module")
 def trained(ctx):
+    """the benchmark's training run: 8 M generated pairs (those inside the guard are used),
+    60 epochs, batch 16,384, learning rate 5e-3"""
     rng = np.random.default_rng(81)
-    pairs = W.surrogate_training_pairs(4_000_000, rng)
+    pairs = W.surrogate_training_pairs(8_000_000, rng)
     ctx.surrogate_init(KERNEL, 5)
-    loss, used = ctx.surrogate_train(_t(pairs), 1.0, epochs=40, batch=16384, lr=5e-3, seed=5)
+    loss, used = ctx.surrogate_train(_t(pairs), 1.0, epochs=60, batch=16384, lr=5e-3, seed=5)
     return ctx.surrogate_params().numpy().copy(), loss, used
 
 
 def test_trained_accuracy_on_held_out_pairs(ctx, trained):
+    """every held-out pair the network serves is within 1e-3 of the quadrature oracle (in units
+    of the output scales), the audit finds the same, and the rejected pairs are analytic"""
     prm, loss, used = trained
     ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
+    ctx.set_surrogate_audit(0)
     rng = np.random.default_rng(82)
-    pairs = W.surrogate_training_pairs(6000, rng)
+    pairs = W.surrogate_training_pairs(20000, rng)
     out, acc = ctx.surrogate_pairs(_t(pairs), 1.0)
     out, acc = out.cpu().numpy().astype(np.float64), acc.cpu().numpy().astype(bool)
     ref = oracle.pairs(KERNEL, 1.0, pairs)[:, :3]
@@ -256,8 +296,19 @@ def test_trained_accuracy_on_held_out_pairs(ctx, trained):
           f"accepted {acc.mean():.3f}; err p50 {np.median(ea):.2e} p99 {np.percentile(ea, 99):.2e} "
           f"max {ea.max():.2e}; fallback max {err[~acc].max():.2e}")
     assert err[~acc].max() <= TOL_FP32
-    assert np.percentile(ea, 99) < 1e-3
-    assert ea.max() < 5e-3
+    assert ea.max() <= TOL_SURROGATE
+    # with the audit on, the audited pairs come back analytic and none is over the bound
+    ctx.set_surrogate_audit(16, TOL_SURROGATE)
+    out2, acc2 = ctx.surrogate_pairs(_t(pairs), 1.0)
+    st = ctx.stats()
+    assert st["n_audit"] > 0 and st["n_audit_over"] == 0 and st["n_redo"] == 0
+    assert 0 < st["audit_max_err"] <= TOL_SURROGATE
+    assert np.array_equal(acc2.cpu().numpy().astype(bool), acc)
+    changed = np.flatnonzero(np.any(out2.cpu().numpy() != out.astype(np.float32), axis=1))
+    assert 0 < len(changed) <= st["n_audit"]
+    e2 = rel_err(out2.cpu().numpy()[changed], ref[changed], scales(KERNEL, 1.0, 0))
+    assert e2.max() <= TOL_FP32                          # audited pairs carry the analytic value
+    ctx.set_surrogate_audit(64, TOL_SURROGATE)
 
 
 def test_serving_over_pair_list(ctx, trained):
@@ -282,7 +333,40 @@ def test_serving_over_pair_list(ctx, trained):
     err = rel_err(got, ref, scales(KERNEL, H, 0)).max(axis=1)
     npairs = np.diff(off)
     print(f"\nsurrogate serving box_obstacle(256, 80): pairs {st['n_pairs']}, fallback "
-          f"{st['n_fallback'] / max(st['n_pairs'], 1):.3f}; particle err p50 {np.median(err):.2e} "
-          f"max {err.max():.2e} (mean pairs/particle {npairs.mean():.1f})")
-    # per-pair errors add up over the ~50-100 pairs of a particle
-    assert err.max() < 5e-2
+          f"{st['n_fallback'] / max(st['n_pairs'], 1):.3f}; audit {st['n_audit']} pairs, max "
+          f"{st['audit_max_err']:.2e}; particle err p50 {np.median(err):.2e} max {err.max():.2e} "
+          f"(mean pairs/particle {npairs.mean():.1f})")
+    assert st["n_redo"] == 0
+    assert err.max() <= TOL_SURROGATE
+
+
+def test_surrogate_gain_over_the_analytic_path(ctx, trained):
+    """what the trained network gains: gamma and grad gamma of one pair list (the 1024^2 box with
+    a 330-cell obstacle, Wendland C2) by the surrogate with its fallback and audit, against the
+    analytic FP32 path on the same list, timed with CUDA events"""
+    import torch
+    ctx.surrogate_init(KERNEL, 0).set_surrogate_params(trained[0])
+    ctx.set_surrogate_audit(64, TOL_SURROGATE)
+    w = W.box_obstacle(2, 1024, 330)
+    ctx.build_cells(_t(w.particles), _t(w.triangles), w.H)
+    P = ctx.pair_count()
+    st = torch.cuda.current_stream()
+    ms = {}
+    for mode in ("surrogate", "fp32_fixup"):
+        for _ in range(3):
+            ctx.integrals_from_pairs(KERNEL, -1, mode)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        for a, b in ev:
+            a.record(st)
+            ctx.integrals_from_pairs(KERNEL, -1, mode)
+            b.record(st)
+        torch.cuda.synchronize()
+        ms[mode] = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        if mode == "surrogate":
+            sst = ctx.stats()
+    gain = ms["fp32_fixup"] / ms["surrogate"]
+    print(f"\nsurrogate gain on {P} pairs: surrogate {ms['surrogate']:.3f} ms (fallback "
+          f"{sst['n_fallback'] / P:.3f}, audit {sst['n_audit']} pairs, max err {sst['audit_max_err']:.2e}), "
+          f"analytic FP32 {ms['fp32_fixup']:.3f} ms: {gain:.2f}x")
+    assert sst["n_redo"] == 0 and sst["n_audit_over"] == 0
+    assert gain > 1.3
