@@ -539,12 +539,17 @@ static unsigned resident_blocks(Ctx* c, K kern, int64_t wanted) {
 // (particle, region) with the segmented sums and crossing slots of integrals_kernel, and the
 // finalize adds a particle's region sums in region order.  Every order is fixed, so results
 // are deterministic run to run.
+// A particle's sum over the last region, when held in one chunk, goes straight to the outputs
+// (the last region holds most pairs: the cubic spline's far pairs, the hybrid mode's quadrature
+// pairs); the finalize reads it back only for a particle that also has pairs in another region
+// or whose last-region pairs cross chunks.  The other regions' in-chunk sums go to a
+// [K-1][N][NV] buffer.
 // ---------------------------------------------------------------------------------------
 struct PairSplit {
   const uint32_t* mask;    // [K][nchunks] bit l of word (r, ch): pair 32 ch + l is of region r
   const int64_t* off;      // [K nchunks + 1] region-major exclusive scan of the mask counts
-  const int64_t* order;    // [P] pair at each position of the partition
-  void* part;              // [K][N][NV] sums of a particle's region held in one chunk
+  const int32_t* order;    // [P] pair at each position of the partition (P < 2^31)
+  void* part;              // [K-1][N][NV] sums of a particle's region r < K-1 held in one chunk
   int64_t nchunks;
   int nreg;
 };
@@ -578,7 +583,7 @@ __device__ __forceinline__ void store_region_masks(uint32_t* __restrict__ mask, 
 }
 
 // the partition: each pair at its rank within its region
-static __global__ void __launch_bounds__(128) partition_kernel(PairSplit s, int64_t P, int64_t* __restrict__ order) {
+static __global__ void __launch_bounds__(128) partition_kernel(PairSplit s, int64_t P, int32_t* __restrict__ order) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < s.nchunks; ch += nw) {
@@ -587,7 +592,7 @@ static __global__ void __launch_bounds__(128) partition_kernel(PairSplit s, int6
     for (int r = 0; r < s.nreg; ++r) {
       const unsigned m = s.mask[r * s.nchunks + ch];
       if ((m >> lane) & 1u) {
-        order[s.off[r * s.nchunks + ch] + __popc(m & ((1u << lane) - 1u))] = q;
+        order[s.off[r * s.nchunks + ch] + __popc(m & ((1u << lane) - 1u))] = int32_t(q);
         break;
       }
     }
@@ -595,8 +600,8 @@ static __global__ void __launch_bounds__(128) partition_kernel(PairSplit s, int6
 }
 
 // segmented sums of one chunk of positions keyed by K pid + region (K regions), written
-// like integrals_kernel's: a key held within the chunk to part[region][pid], the chunk's first
-// and last keys to its two slots
+// like integrals_kernel's: a key held within the chunk to part[region][pid] (the last region:
+// to the particle's outputs), the chunk's first and last keys to its two slots
 // (KT: the key type, 32-bit where K N stays below 2^32)
 template <typename OT, int NV, int K, typename KT>
 __device__ __forceinline__ void keyed_chunk_sums(const IntArgs& a, const PairSplit& sp, int64_t ch, bool valid,
@@ -623,9 +628,13 @@ __device__ __forceinline__ void keyed_chunk_sums(const IntArgs& a, const PairSpl
     int64_t s0, s1;
     part_range(a, sp, pid, r, s0, s1);
     if (s0 >= cs && s1 <= cs + 32) {
-      OT* w = static_cast<OT*>(sp.part) + (int64_t(r) * a.N + pid) * NV;
+      if (r == K - 1) {
+        write_particle<OT, NV == 3 ? 0 : (NV == 6 ? 1 : 3)>(a, pid, v);
+      } else {
+        OT* w = static_cast<OT*>(sp.part) + (int64_t(r) * a.N + pid) * NV;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) w[k] = v[k];
+        for (int k = 0; k < NV; ++k) w[k] = v[k];
+      }
     }
     OT* slots = static_cast<OT*>(a.slots);
     if (lane == 0) {
@@ -639,7 +648,32 @@ __device__ __forceinline__ void keyed_chunk_sums(const IntArgs& a, const PairSpl
   }
 }
 
-// per particle: the region sums in region order, each from its chunk or its crossing slots
+// a particle's outputs as write_particle stored them (the components it does not store are 0)
+template <typename OT, int MD>
+__device__ __forceinline__ void read_particle(const IntArgs& a, int64_t pid, OT* v) {
+  constexpr int NV = nv_of(MD);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = OT(0);
+  v[0] = static_cast<const OT*>(a.gamma)[pid];
+  if (a.grad) {
+    v[1] = static_cast<const OT*>(a.grad)[2 * pid];
+    v[2] = static_cast<const OT*>(a.grad)[2 * pid + 1];
+  }
+  if (MD >= 1) {
+    if (a.nm == 1) {
+      v[3] = v[0];                                 // M00 = gamma
+    } else {
+      const OT* m = static_cast<const OT*>(a.mom) + pid * a.nm;
+#pragma unroll
+      for (int k = 0; k < nmom_of(MD); ++k)
+        if (k < a.nm) v[3 + k] = m[k];
+    }
+  }
+}
+
+// per particle: the region sums in region order, each from its chunk (the last region's from
+// the outputs) or its crossing slots.  A particle whose pairs are all in the last region and
+// within one chunk already has its sum in the outputs.
 template <typename OT, int MD>
 __global__ void split_finalize_kernel(IntArgs a, PairSplit sp) {
   constexpr int NV = nv_of(MD);
@@ -649,6 +683,10 @@ __global__ void split_finalize_kernel(IntArgs a, PairSplit sp) {
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = OT(0);
   if (a.pair_off[i + 1] > a.pair_off[i]) {
+    const int last = sp.nreg - 1;
+    int64_t l0, l1;
+    part_range(a, sp, i, last, l0, l1);
+    if (l1 - l0 == a.pair_off[i + 1] - a.pair_off[i] && (l0 >> 5) == ((l1 - 1) >> 5)) return;
     const OT* slots = static_cast<const OT*>(a.slots);
     bool first = true;
 #pragma unroll 1
@@ -659,9 +697,13 @@ __global__ void split_finalize_kernel(IntArgs a, PairSplit sp) {
       OT w[NV];
       const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
       if (c0 == c1) {
-        const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
+        if (r == last) {
+          read_particle<OT, MD>(a, i, w);
+        } else {
+          const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
 #pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] = src[k];
+          for (int k = 0; k < NV; ++k) w[k] = src[k];
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < NV; ++k) w[k] = slots[(c0 * 2 + 1) * NV + k];
@@ -680,25 +722,29 @@ __global__ void split_finalize_kernel(IntArgs a, PairSplit sp) {
   write_particle<OT, MD>(a, i, v);
 }
 
-// scratch of a K-region partition in pair_list2: header (chunk counter at [4]) | order [P] |
-// counts [K nchunks + 1] | offsets [K nchunks + 1] | masks [K nchunks] | extra bytes; region
-// sums [K][N][NV] in pair_vals
+// scratch of a K-region partition in pair_list2: header (chunk counter at [4]) | counts
+// [K nchunks + 1] | offsets [K nchunks + 1] | order int32 [P] (padded to 8 bytes) | masks
+// [K nchunks] | extra bytes; region sums [K-1][N][NV] in pair_vals
 inline size_t split_list_bytes(int64_t P, int64_t nchunks, int K, size_t extra) {
-  return 64 + size_t(P + 2 * (K * nchunks + 1)) * sizeof(int64_t) + size_t(K * nchunks + 1) * 4 + extra;
+  return 64 + size_t(2 * (K * nchunks + 1)) * sizeof(int64_t) + size_t((P + 1) / 2) * 8 +
+         size_t(K * nchunks + 1) * 4 + extra;
 }
 template <typename OT>
 static sph2d_status split_scratch(Ctx* c, const IntArgs& a, int K, int NV, size_t extra, PairSplit& sp,
                                   int64_t*& cnt, unsigned long long*& hdr, unsigned char*& extra_ptr) {
+  if (a.P >= (int64_t(1) << 31))
+    return set_err(c, SPH2D_ERR_CAPACITY, "a partitioned pair list (cubic spline, hybrid mode) holds < 2^31 pairs");
   const int64_t nchunks = (a.P + 31) >> 5;
   sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
-  if (s == SPH2D_OK) s = ensure(c, c->pair_vals, size_t(K) * size_t(a.N > 0 ? a.N : 1) * NV * sizeof(OT));
+  if (s == SPH2D_OK)
+    s = ensure(c, c->pair_vals, size_t(K - 1 > 0 ? K - 1 : 1) * size_t(a.N > 0 ? a.N : 1) * NV * sizeof(OT));
   if (s == SPH2D_OK) s = ensure(c, c->pair_list2, split_list_bytes(a.P, nchunks, K, extra));
   if (s != SPH2D_OK) return s;
   hdr = static_cast<unsigned long long*>(c->pair_list2.ptr);
-  int64_t* order = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
-  cnt = order + a.P;
+  cnt = reinterpret_cast<int64_t*>(static_cast<char*>(c->pair_list2.ptr) + 64);
   int64_t* off = cnt + (K * nchunks + 1);
-  uint32_t* mask = reinterpret_cast<uint32_t*>(off + (K * nchunks + 1));
+  int32_t* order = reinterpret_cast<int32_t*>(off + (K * nchunks + 1));
+  uint32_t* mask = reinterpret_cast<uint32_t*>(order + 2 * ((a.P + 1) / 2));
   extra_ptr = reinterpret_cast<unsigned char*>(mask + (K * nchunks + 1));
   sp = PairSplit{mask, off, order, c->pair_vals.ptr, nchunks, K};
   return SPH2D_OK;
@@ -709,7 +755,7 @@ static sph2d_status split_order(Ctx* c, const IntArgs& a, PairSplit& sp, const i
   sph2d_status s = exclusive_scan_i64(c, cnt, const_cast<int64_t*>(sp.off), int64_t(sp.nreg) * sp.nchunks);
   if (s != SPH2D_OK) return s;
   SPH2D_LAUNCH(c, (partition_kernel), resident_blocks(c, partition_kernel, (sp.nchunks + 3) / 4), 128, sp, a.P,
-               const_cast<int64_t*>(sp.order));
+               const_cast<int32_t*>(sp.order));
   return SPH2D_OK;
 }
 

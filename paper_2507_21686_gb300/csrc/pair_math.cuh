@@ -384,9 +384,12 @@ SPH2D_HD FFT<F> ff_log(FFT<F> x) {
   constexpr int NP = DBL ? 7 : 4, NT = DBL ? 15 : 8;
   int e = 0;
   const F m0 = frexp_f(x.hi, &e);                        // [1/2, 1)
-  if (raw_f(m0) < 0.70710678118654752) e -= 1;           // m = x.hi 2^-e in [1/sqrt2, sqrt2)
+  // (all of this in the working precision: a double literal here would put FP64 instructions
+  // into the FP32 kernels)
+  using MF = decltype(raw_f(m0));
+  if (raw_f(m0) < MF(0.70710678118654752)) e -= 1;       // m = x.hi 2^-e in [1/sqrt2, sqrt2)
   const FFT<F> xm{ldexp_f(x.hi, -e), ldexp_f(x.lo, -e)}; // exact scaling
-  const int i = int(raw_f(xm.hi) * 128 + 0.5) - 64;      // nearest table point (either one at a tie)
+  const int i = int(raw_f(xm.hi) * MF(128) + MF(0.5)) - 64;   // nearest table point (either one at a tie)
   const auto ent = log_entry<DBL>(i);
   const F inv = F(ent.inv);
   const FFT<F> p = ff_two_prod(xm.hi, inv), q = ff_two_prod(xm.lo, inv);   // exact
@@ -403,7 +406,7 @@ SPH2D_HD FFT<F> ff_log(FFT<F> x) {
 #pragma unroll
   for (int k = NP - 1; k >= 1; --k) S = S * r + ffk<F, B>(((k & 1) ? 1.0 : -1.0), double(k));
   const FFT<F> l1p = r * S + FFT<F>{tail, F(0)};
-  return (l1p + FFT<F>{F(ent.hi), F(ent.lo)}) + ffln2<F, B>() * F(double(e));
+  return (l1p + FFT<F>{F(ent.hi), F(ent.lo)}) + ffln2<F, B>() * F(MF(e));
 }
 
 // asinh(t2/d) - asinh(t1/d) in FF (see asinh_diff)

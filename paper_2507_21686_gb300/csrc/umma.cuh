@@ -1,0 +1,122 @@
+// Fifth-generation tensor-core (tcgen05) building blocks for sm_100a / sm_103a: the shared-memory
+// matrix descriptor and the kind::f16 instruction descriptor (constexpr, host and device, unit-
+// tested on the CPU against the PTX ISA field tables), and thin inline-PTX wrappers for TMEM
+// allocation, the MMA, its commit to an mbarrier, bounded mbarrier waits and TMEM loads.
+//
+// Operand layout used here: K-major, no swizzle.  A matrix of R rows and K 16-bit elements is
+// stored as "core matrices" of 8 rows x 8 elements (8 rows of 16 contiguous bytes = 128 bytes);
+// the core matrix of row group g and column group j starts at g * SBO + j * LBO bytes.  With
+// LBO = 128 and SBO = 128 * K / 8, row r, column c sits at byte
+//   (r / 8) * SBO + (c / 8) * 128 + (r % 8) * 16 + (c % 8) * 2.
+#pragma once
+
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define UMMA_HD __host__ __device__
+#else
+#define UMMA_HD
+#endif
+
+namespace sph2d {
+namespace umma {
+
+// byte offset of element (r, c) of a K-major no-swizzle operand with K columns (16-bit elements)
+UMMA_HD constexpr uint32_t kmajor_offset(uint32_t r, uint32_t c, uint32_t K) {
+  return (r / 8u) * (128u * (K / 8u)) + (c / 8u) * 128u + (r % 8u) * 16u + (c % 8u) * 2u;
+}
+
+// Shared-memory matrix descriptor (64 bits):
+//   bits  0-13  start address >> 4        bits 16-29  leading-dimension byte offset >> 4
+//   bits 32-45  stride-dimension byte offset >> 4
+//   bits 46-47  descriptor version (1 on sm_100-class GPUs)
+//   bits 49-51  base offset (0: no swizzle)   bit 52  LBO mode (0)
+//   bits 61-63  layout / swizzle mode (0: no swizzle)
+UMMA_HD constexpr uint64_t smem_desc(uint32_t smem_addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  return uint64_t((smem_addr >> 4) & 0x3FFFu) | (uint64_t((lbo_bytes >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo_bytes >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16 (32 bits):
+//   bits 0-1 sparsity selector, 2 sparsity, 3 saturate, 4-5 D format (1: F32), 7-9 A format
+//   (0: F16, 1: BF16), 10-12 B format, 13 negate A, 14 negate B, 15 A major (0: K), 16 B major
+//   (0: K), 17-22 N >> 3, 24-28 M >> 4, 30-31 max shift (0)
+UMMA_HD constexpr uint32_t idesc_f16(uint32_t M, uint32_t N, bool bf16) {
+  return (1u << 4) | (uint32_t(bf16) << 7) | (uint32_t(bf16) << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+#if defined(__CUDACC__)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// TMEM allocation by one whole warp: the allocated column base is written to *dst (shared)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst)), "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(uint32_t(accumulate)));
+}
+// arrive once on the mbarrier when every MMA this thread issued so far has completed
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// wait for the mbarrier phase with the given parity, at most `limit` polls; false if it ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
+  const uint32_t addr = smem_u32(mbar);
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// make this thread's generic-proxy shared-memory writes visible to the tensor core's reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane (warp w reads lanes 32w .. 32w+31).
+// The wait for the load is in the same asm statement, so no instruction the compiler schedules
+// can read the destination registers before the data has arrived.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+#endif
+
+}  // namespace umma
+}  // namespace sph2d
