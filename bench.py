@@ -797,8 +797,25 @@ def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3
                                   "max_err": st["audit_max_err"], "redo_pairs": st["n_redo"],
                                   "note": "audited pairs are re-evaluated by the analytic FP32 path and return "
                                           "its value; an audited error above tol re-evaluates the whole call"}
+    # the same serving on the fifth-generation tensor cores (tcgen05 engine), for the A/B
+    ctx.set_surrogate_engine("tcgen05")
+    outs["surrogate_tcgen05"] = ctx.integrals_from_pairs(k, -1, "surrogate")
+    st = ctx.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a_, b_ in ev:
+        flush.zero_()
+        a_.record(stream)
+        ctx.integrals_from_pairs(k, -1, "surrogate")
+        b_.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_surrogate_engine("mma_sync")
+    ms = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+    res["surrogate_tcgen05"] = {"ms": ms, "pairs_per_s": P / (ms / 1e3), "fallback_rate": st["n_fallback"] / max(P, 1),
+                                "mma_timeouts": st["n_mma_timeouts"],
+                                "note": "serving network on tcgen05 (TMEM accumulators, activations staged in "
+                                        "shared memory); the surrogate line above is the mma.sync engine"}
     ref = torch.cat([outs["fp64"][0][:, None], outs["fp64"][1]], 1).cpu().numpy()
-    for mode in ("surrogate", "fp32_fixup"):
+    for mode in ("surrogate", "surrogate_tcgen05", "fp32_fixup"):
         got = torch.cat([outs[mode][0][:, None], outs[mode][1]], 1).double().cpu().numpy()
         e = rel_err(got, ref, scales(k, w.H, 0)).max(axis=1)
         res[mode]["particle_err_vs_fp64_path"] = {"p50": float(np.median(e)), "p99": float(np.percentile(e, 99)),

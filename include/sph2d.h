@@ -118,6 +118,7 @@ typedef struct {
   int64_t n_audit_over;     /* audited pairs whose network error exceeded the bound */
   double audit_max_err;     /* largest audited network error, in units of the output scales */
   int64_t n_redo;           /* pairs re-evaluated analytically because the audit failed (0 or all) */
+  int64_t n_mma_timeouts;   /* tcgen05 serving: MMA completion waits that ran out (their pairs fell back) */
 } sph2d_stats;
 
 /* Create a context on CUDA device `device`; `stream` is a cudaStream_t (NULL = legacy
@@ -435,6 +436,18 @@ sph2d_status sph2d_surrogate_grad(sph2d_ctx* ctx, const float* x, const float* t
  * Errors: INVALID_ARG.
  */
 sph2d_status sph2d_surrogate_set_audit(sph2d_ctx* ctx, int period, double tol);
+
+/*
+ * Tensor-core engine of the serving network (sph2d_surrogate_pairs, SPH2D_SURROGATE mode):
+ * 0 (default) mma.sync m16n8k16, one warp per 32 pairs with the activations chained in
+ * registers; 1 tcgen05 (fifth-generation tensor cores), one CTA per 128 pairs with the
+ * accumulators in tensor memory and the activations staged in shared memory between layers.
+ * Both evaluate the same FP16-operand network with FP32 accumulation; results agree to FP32
+ * accumulation order.  A tcgen05 MMA whose completion wait runs out of its poll budget sends the
+ * CTA's remaining pairs to the analytic fallback (n_mma_timeouts in sph2d_last_stats).
+ * Errors: INVALID_ARG.
+ */
+sph2d_status sph2d_surrogate_set_engine(sph2d_ctx* ctx, int engine);
 
 /* Copy the FP32 parameters to / from host memory (n = SPH2D_SURROGATE_PARAMS).  get returns
  * CAPACITY if cap is smaller.  Synchronise.  Errors: NOT_BUILT, INVALID_ARG, CAPACITY, CUDA. */

@@ -39,7 +39,8 @@ class Stats(ctypes.Structure):
                 ("n_candidates", ctypes.c_int64),
                 ("n_launches", ctypes.c_int64),
                 ("n_audit", ctypes.c_int64), ("n_audit_over", ctypes.c_int64),
-                ("audit_max_err", ctypes.c_double), ("n_redo", ctypes.c_int64)]
+                ("audit_max_err", ctypes.c_double), ("n_redo", ctypes.c_int64),
+                ("n_mma_timeouts", ctypes.c_int64)]
 
 
 SIGNATURES = {
@@ -70,6 +71,7 @@ SIGNATURES = {
     "sph2d_surrogate_get_params": (_ST, [_P, _P, _I64]),
     "sph2d_surrogate_set_params": (_ST, [_P, _P, _I64]),
     "sph2d_surrogate_set_audit": (_ST, [_P, _I, _D]),
+    "sph2d_surrogate_set_engine": (_ST, [_P, _I]),
     "sph2d_measure_fma_peak": (_ST, [_I, _I, _D, ctypes.POINTER(ctypes.c_double)]),
     "sph2d_surrogate_save": (_ST, [_P, ctypes.c_char_p]),
     "sph2d_surrogate_load": (_ST, [_P, ctypes.c_char_p]),

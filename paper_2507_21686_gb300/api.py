@@ -299,6 +299,11 @@ class Context:
         check(self.lib, self.h, self.lib.sph2d_surrogate_set_audit(self.h, int(period), float(tol)))
         return self
 
+    def set_surrogate_engine(self, engine: str = "mma_sync"):
+        """Serving tensor-core engine: "mma_sync" (register-chained mma.sync) or "tcgen05"."""
+        check(self.lib, self.h, self.lib.sph2d_surrogate_set_engine(self.h, {"mma_sync": 0, "tcgen05": 1}[engine]))
+        return self
+
     def set_surrogate_params(self, p):
         q = torch.as_tensor(p, dtype=torch.float32).contiguous().cpu()
         self._bind_stream()

@@ -237,6 +237,7 @@ sph2d_status sph2d_last_stats(const sph2d_ctx* h, sph2d_stats* out) {
     std::memcpy(&emax, &bits, sizeof(emax));
     out->audit_max_err = emax;
     out->n_redo = out->n_audit_over > 0 ? out->n_pairs : 0;
+    out->n_mma_timeouts = c.pinned[14];
   }
   return SPH2D_OK;
 }
@@ -556,6 +557,13 @@ sph2d_status sph2d_surrogate_set_audit(sph2d_ctx* h, int period, double tol) {
   if (!(tol > 0.0) || !std::isfinite(tol)) return set_err(c, SPH2D_ERR_INVALID_ARG, "audit bound must be > 0");
   c->sur_audit_period = period;
   c->sur_audit_tol = tol;
+  return SPH2D_OK;
+}
+
+sph2d_status sph2d_surrogate_set_engine(sph2d_ctx* h, int engine) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  if (engine != 0 && engine != 1) return set_err(&h->c, SPH2D_ERR_INVALID_ARG, "engine must be 0 (mma.sync) or 1 (tcgen05)");
+  h->c.sur_engine = engine;
   return SPH2D_OK;
 }
 

@@ -50,7 +50,7 @@ struct Ctx {
   DevBuf cand_off, cand_kept;
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
   bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
-  bool fallback_pending = false;  // pinned[10..13]: fallback count and audit of the last surrogate call
+  bool fallback_pending = false;  // pinned[10..14]: fallback count, audit and MMA timeouts of the last surrogate call
   int64_t launches = 0;        // kernels launched by this context (cumulative)
   bool sur_ready = false;      // surrogate parameters initialised
   int sur_kernel = -1;         // kernel the surrogate is trained for
@@ -58,6 +58,7 @@ struct Ctx {
   float sur_w[3] = {1.0f, 1.0f, 1.0f};   // per-output loss weights
   int sur_audit_period = 64;   // serving audit: one accepted pair in this many (0: off)
   double sur_audit_tol = 1e-3; // audit bound in units of the output scales
+  int sur_engine = 0;          // serving MMAs: 0 mma.sync (register-chained), 1 tcgen05 (TMEM)
 };
 
 // error helpers ------------------------------------------------------------------------

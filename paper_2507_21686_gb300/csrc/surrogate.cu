@@ -35,6 +35,7 @@
 
 #include "integrals_impl.cuh"
 #include "surrogate.cuh"
+#include "umma.cuh"
 
 namespace sph2d {
 
@@ -462,6 +463,7 @@ struct SurArgs {
   unsigned long long* au_count;   // audited pairs (entries at the back of fb_list)
   unsigned long long* au_over;    // audited pairs with an error above audit_tol
   unsigned* au_max;               // largest audited error (float bits; errors are >= 0)
+  unsigned long long* tc_timeouts; // tensor-core serving: MMA waits that ran out (pairs then fall back)
 };
 
 // whether accepted pair q is audited: a multiplicative hash of its index falls in the first
@@ -540,6 +542,193 @@ __global__ void __launch_bounds__(128, 6) surrogate_values_kernel(IntArgs a, con
     }
     __syncwarp();
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Serving on the fifth-generation tensor cores (tcgen05), the alternative to the mma.sync
+// values kernel above.  A CTA of four warps takes 128 pairs at a time.  Each layer is a
+// 128 x N x 16 sequence of kind::f16 MMAs (FP16 operands from shared memory, FP32 accumulators
+// in tensor memory) issued by one thread; every thread then reads its row's accumulators with
+// tcgen05.ld, adds the bias, applies the same packed-FP16 2 GELU as the mma.sync kernel and
+// writes the row back to shared memory as the next layer's A operand (K-major core matrices,
+// umma.cuh).  An MMA whose completion wait runs out of its poll budget sends the CTA's pairs to
+// the analytic fallback from then on (results stay correct) and is counted.
+// ---------------------------------------------------------------------------------------
+struct SurTcSmem {
+  __half w1[kSurHid * 16];      // layer-1 B operand: N = 64 rows, K = 16 (6 inputs, zero padded)
+  __half w2[kSurHid * kSurHid];
+  __half w3[kSurHid * kSurHid];
+  __half w4[16 * kSurHid];      // output layer: N = 16 (3 outputs, zero padded)
+  __half a0[128 * 16];          // the tile's canonical inputs
+  __half act[128 * kSurHid];    // the tile's activations (2 GELU) between layers
+  float b1[kSurHid], b2[kSurHid], b3[kSurHid], b4[16];
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+// the same FP16 values as load_sur_weights (W2, W3, W4 halved for the 2 GELU activations), in
+// the tensor core's K-major layout
+__device__ void load_tc_weights(SurTcSmem& s, const float* __restrict__ prm) {
+  using umma::kmajor_offset;
+  for (int i = threadIdx.x; i < kSurHid * 16; i += blockDim.x) {
+    const int n = i / 16, k = i % 16;
+    s.w1[kmajor_offset(n, k, 16) / 2] = __float2half_rn(k < kSurIn ? prm[kOffW1 + n * kSurIn + k] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < kSurHid * kSurHid; i += blockDim.x) {
+    const int n = i / kSurHid, k = i % kSurHid;
+    s.w2[kmajor_offset(n, k, kSurHid) / 2] = __hmul(__float2half_rn(prm[kOffW2 + n * kSurHid + k]), __float2half(0.5f));
+    s.w3[kmajor_offset(n, k, kSurHid) / 2] = __hmul(__float2half_rn(prm[kOffW3 + n * kSurHid + k]), __float2half(0.5f));
+  }
+  for (int i = threadIdx.x; i < 16 * kSurHid; i += blockDim.x) {
+    const int n = i / kSurHid, k = i % kSurHid;
+    s.w4[kmajor_offset(n, k, kSurHid) / 2] =
+        __hmul(__float2half_rn(n < kSurOut ? prm[kOffW4 + n * kSurHid + k] : 0.0f), __float2half(0.5f));
+  }
+  for (int i = threadIdx.x; i < kSurHid; i += blockDim.x) {
+    s.b1[i] = prm[kOffB1 + i];
+    s.b2[i] = prm[kOffB2 + i];
+    s.b3[i] = prm[kOffB3 + i];
+  }
+  for (int i = threadIdx.x; i < 16; i += blockDim.x) s.b4[i] = i < kSurOut ? prm[kOffB4 + i] : 0.0f;
+}
+
+constexpr uint32_t kTcSpin = 1u << 22;          // polls of an MMA completion wait before giving up
+
+// wait for the next MMA completion on the CTA's mbarrier; the CTA agrees on the outcome
+__device__ __forceinline__ bool tc_wait(SurTcSmem& s, uint32_t& phase) {
+  const bool ok = __syncthreads_and(umma::mbar_wait(&s.mbar, phase, kTcSpin) ? 1 : 0) != 0;
+  if (ok) phase ^= 1u;
+  umma::fence_after_sync();
+  return ok;
+}
+
+// this thread's row of a hidden layer: accumulators + bias -> FP16 -> 2 GELU -> the next A operand
+__device__ __forceinline__ void tc_hidden_row(const SurTcSmem& s, uint32_t trow, const float* bias, __half* act, int row) {
+  float acc[kSurHid];
+  umma::tmem_ld64(trow, acc);
+#pragma unroll
+  for (int c16 = 0; c16 < kSurHid / 16; ++c16) {
+    const float* v = acc + 16 * c16;
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      w[j] = h2_bits(gelu2x_h2(__floats2half2_rn(v[2 * j] + bias[16 * c16 + 2 * j], v[2 * j + 1] + bias[16 * c16 + 2 * j + 1])));
+    *reinterpret_cast<uint4*>(act + umma::kmajor_offset(row, 16 * c16, kSurHid) / 2) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(act + umma::kmajor_offset(row, 16 * c16 + 8, kSurHid) / 2) = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+}
+
+// one thread issues a layer: D[tm] = A (K = 16 kblocks) x B^T, then commits to the mbarrier
+__device__ __forceinline__ void tc_issue(SurTcSmem& s, uint32_t tm, uint32_t a_addr, uint32_t b_addr, int kblocks,
+                                         uint32_t a_sbo, uint32_t b_sbo, uint32_t idesc) {
+  umma::fence_after_sync();
+  for (int kb = 0; kb < kblocks; ++kb)
+    umma::mma_f16(tm, umma::smem_desc(a_addr + 256 * kb, 128, a_sbo), umma::smem_desc(b_addr + 256 * kb, 128, b_sbo),
+                  idesc, kb > 0);
+  umma::mma_commit(&s.mbar);
+}
+
+template <int KID, bool LIST>
+__global__ void __launch_bounds__(128) surrogate_values_tc_kernel(IntArgs a, const double* __restrict__ pairs,
+                                                                  SurArgs sa) {
+  __shared__ __align__(128) SurTcSmem s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_tc_weights(s, sa.prm);
+  if (warp == 0) {
+    umma::tmem_alloc(&s.tmem, 64);
+    umma::tmem_relinquish();
+  }
+  if (tid == 0) {
+    umma::mbar_init(&s.mbar, 1);
+    umma::mbar_init_fence();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tm = s.tmem, trow = tm + (uint32_t(32 * warp) << 16);
+  const uint32_t sa0 = umma::smem_u32(s.a0), sact = umma::smem_u32(s.act);
+  const uint32_t sw1 = umma::smem_u32(s.w1), sw2 = umma::smem_u32(s.w2), sw3 = umma::smem_u32(s.w3),
+                 sw4 = umma::smem_u32(s.w4);
+  constexpr uint32_t ID64 = umma::idesc_f16(128, 64, false), ID16 = umma::idesc_f16(128, 16, false);
+  uint32_t phase = 0;
+  bool healthy = true;
+  unsigned long long timeouts = 0;
+  const float ih = float(a.invH);
+  const int64_t ntiles = (a.P + 127) / 128;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t q = tile * 128 + tid;
+    float lf[6] = {0, 0, 0, 0, 0, 0};
+    if (q < a.P) load_local<LIST>(a, pairs, q, ih, lf);
+    const Canon c = canonicalize(lf);
+    bool use = (q < a.P) && c.accept;
+    float y[16];
+    bool tile_ok = healthy;
+    if (healthy) {
+      {   // the input row: 6 canonical coordinates, zero padded to K = 16
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          w[j] = pack_f16(2 * j < kSurIn && use ? c.x[2 * j] : 0.0f, 2 * j + 1 < kSurIn && use ? c.x[2 * j + 1] : 0.0f);
+        *reinterpret_cast<uint4*>(s.a0 + umma::kmajor_offset(tid, 0, 16) / 2) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(s.a0 + umma::kmajor_offset(tid, 8, 16) / 2) = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+      umma::fence_proxy_async();
+      umma::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) tc_issue(s, tm, sa0, sw1, 1, 256, 256, ID64);
+      tile_ok = tc_wait(s, phase);
+      const float* bias[3] = {s.b1, s.b2, s.b3};
+      const uint32_t wl[3] = {sw2, sw3, sw4};
+#pragma unroll 1
+      for (int l = 0; l < 3 && tile_ok; ++l) {
+        tc_hidden_row(s, trow, bias[l], s.act, tid);
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) tc_issue(s, tm, sact, wl[l], 4, 1024, 1024, l < 2 ? ID64 : ID16);
+        tile_ok = tc_wait(s, phase);
+      }
+      if (tile_ok) {
+        umma::tmem_ld16(trow, y);
+#pragma unroll
+        for (int j = 0; j < kSurOut; ++j) y[j] += s.b4[j];
+      } else {
+        healthy = false;
+        ++timeouts;
+      }
+    }
+    use = use && tile_ok;
+    if (use) {
+      float lx, ly;
+      uncanonicalize_grad(c, c.area * y[1], c.area * y[2], lx, ly);
+      sa.vals[3 * q] = c.area * y[0];
+      sa.vals[3 * q + 1] = lx * ih;
+      sa.vals[3 * q + 2] = ly * ih;
+    }
+    if (sa.accepted && q < a.P) sa.accepted[q] = use ? 1 : 0;
+    const unsigned rej = __ballot_sync(0xffffffffu, (q < a.P) && !use);
+    if (rej) {
+      unsigned long long base = 0;
+      const int leader = __ffs(rej) - 1;
+      if (lane == leader) base = atomicAdd(sa.fb_count, (unsigned long long)__popc(rej));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if ((q < a.P) && !use) sa.fb_list[base + __popc(rej & ((1u << lane) - 1u))] = q;
+    }
+    const bool aud = use && audited(sa, q);
+    const unsigned am = __ballot_sync(0xffffffffu, aud);
+    if (am) {
+      unsigned long long base = 0;
+      const int leader = __ffs(am) - 1;
+      if (lane == leader) base = atomicAdd(sa.au_count, (unsigned long long)__popc(am));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (aud) sa.fb_list[a.P - 1 - int64_t(base + __popc(am & ((1u << lane) - 1u)))] = q;
+    }
+  }
+  if (!healthy) umma::mbar_wait(&s.mbar, phase, kTcSpin);   // let an overdue MMA drain
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tm, 64);
+  if (tid == 0 && timeouts) atomicAdd(sa.tc_timeouts, timeouts);
 }
 
 // the analytic FP32 path (with the FP64 fix-up for far or non-finite geometry) for pair q
@@ -883,9 +1072,14 @@ sph2d_status surrogate_train(Ctx* c, const double* pairs, int64_t P, double H, i
 // the values and fallback kernels for one pair source (fb_count already cleared)
 template <int KID, bool LIST>
 static void launch_serving(Ctx* c, const IntArgs& a, const double* pairs, const SurArgs& sa) {
-  const int64_t nch = (a.P + 31) / 32;
-  const unsigned g1 = persistent_grid(c, surrogate_values_kernel<KID, LIST>, (nch + 3) / 4);
-  SPH2D_LAUNCH(c, (surrogate_values_kernel<KID, LIST>), g1, 128, a, pairs, sa);
+  if (c->sur_engine == 1) {
+    const unsigned g1 = persistent_grid(c, surrogate_values_tc_kernel<KID, LIST>, (a.P + 127) / 128);
+    SPH2D_LAUNCH(c, (surrogate_values_tc_kernel<KID, LIST>), g1, 128, a, pairs, sa);
+  } else {
+    const int64_t nch = (a.P + 31) / 32;
+    const unsigned g1 = persistent_grid(c, surrogate_values_kernel<KID, LIST>, (nch + 3) / 4);
+    SPH2D_LAUNCH(c, (surrogate_values_kernel<KID, LIST>), g1, 128, a, pairs, sa);
+  }
   // the list length is only known on the device: a persistent grid strides over it
   const unsigned g2 = persistent_grid(c, surrogate_fallback_kernel<KID, LIST>, (a.P + 127) / 128);
   SPH2D_LAUNCH(c, (surrogate_fallback_kernel<KID, LIST>), g2, 128, a, pairs, sa);
@@ -906,7 +1100,8 @@ static void dispatch_serving(Ctx* c, const IntArgs& a, const double* pairs, cons
 }
 
 // counters in host_flags_dev: [2] fallback count, [3] audited pairs, [4] audited pairs over the
-// bound, [5] largest audited error (float bits); copied to pinned[10..13] after the call
+// bound, [5] largest audited error (float bits), [6] tensor-core MMA waits that ran out; copied
+// to pinned[10..14] after the call
 static sph2d_status serving_setup(Ctx* c, int64_t P, double H, SurArgs& sa) {
   sph2d_status s = ensure(c, c->sur_fb, size_t(P > 0 ? P : 1) * sizeof(int64_t));
   if (s == SPH2D_OK) s = ensure(c, c->host_flags_dev, 64);
@@ -918,19 +1113,20 @@ static sph2d_status serving_setup(Ctx* c, int64_t P, double H, SurArgs& sa) {
   sa.au_count = flags + 3;
   sa.au_over = flags + 4;
   sa.au_max = reinterpret_cast<unsigned*>(flags + 5);
+  sa.tc_timeouts = flags + 6;
   sa.audit_period = c->sur_audit_period;
   int lg = 0;
   while ((1 << lg) < sa.audit_period) ++lg;
   sa.audit_shift = unsigned(64 - lg);
   sa.audit_tol = float(c->sur_audit_tol);
   sa.grad_scale = float(2.0 * kernel_C(c->sur_kernel) * kernel_int0(c->sur_kernel) / H);
-  cudaError_t e = cudaMemsetAsync(sa.fb_count, 0, 4 * sizeof(unsigned long long), c->stream);
+  cudaError_t e = cudaMemsetAsync(sa.fb_count, 0, 5 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   return SPH2D_OK;
 }
 
 static sph2d_status serving_finish(Ctx* c, const SurArgs& sa, int64_t P) {
-  cudaError_t e = cudaMemcpyAsync(c->pinned + 10, sa.fb_count, 4 * sizeof(unsigned long long),
+  cudaError_t e = cudaMemcpyAsync(c->pinned + 10, sa.fb_count, 5 * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "fallback count copy");
   e = cudaGetLastError();

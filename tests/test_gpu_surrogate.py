@@ -255,6 +255,7 @@ def test_error_statuses(ctx):
         c.surrogate_train(torch.zeros((10, 8), dtype=torch.float64, device="cuda"), 1.0, 1, batch=4096)
     with pytest.raises(Sph2dError, match="INVALID_ARG"):
         c.set_surrogate_params(np.zeros(10, dtype=np.float32))
+    assert c.lib.sph2d_surrogate_set_engine(c.h, 2) == 1         # INVALID_ARG
     # surrogate mode: kernel must match, moments are not provided
     parts = np.zeros((4, 4), dtype=np.float32)
     tris = np.array([[0.0, 0.0, 0.1, 0.0, 0.0, 0.1]], dtype=np.float32)
@@ -338,6 +339,54 @@ def test_serving_over_pair_list(ctx, trained):
           f"(mean pairs/particle {npairs.mean():.1f})")
     assert st["n_redo"] == 0
     assert err.max() <= TOL_SURROGATE
+
+
+def test_tcgen05_engine_matches_mma_sync(ctx, trained):
+    """the fifth-generation tensor-core serving kernel (tcgen05, accumulators in tensor memory)
+    against the mma.sync kernel on held-out pairs: the same guard decisions, both within 1e-3 of
+    the quadrature oracle, and agreement to FP32 accumulation order (an FP16 rounding of an
+    activation may land on the neighbouring value)"""
+    prm = trained[0]
+    ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
+    ctx.set_surrogate_audit(0)
+    rng = np.random.default_rng(86)
+    pairs = W.surrogate_training_pairs(20000, rng)
+    outs = {}
+    for eng in ("mma_sync", "tcgen05"):
+        ctx.set_surrogate_engine(eng)
+        o, acc = ctx.surrogate_pairs(_t(pairs), 1.0)
+        outs[eng] = (o.cpu().numpy().astype(np.float64), acc.cpu().numpy().astype(bool))
+        assert ctx.stats()["n_mma_timeouts"] == 0
+    ctx.set_surrogate_engine("mma_sync")
+    ctx.set_surrogate_audit(64, TOL_SURROGATE)
+    (om, am), (ot, at) = outs["mma_sync"], outs["tcgen05"]
+    assert np.array_equal(am, at)
+    ref = oracle.pairs(KERNEL, 1.0, pairs)[:, :3]
+    sc = scales(KERNEL, 1.0, 0)
+    assert rel_err(ot[at], ref[at], sc).max() <= TOL_SURROGATE
+    d = rel_err(ot[at], om[at], sc)
+    print(f"\ntcgen05 vs mma.sync on {at.sum()} accepted pairs: median {np.median(d):.1e}, max {d.max():.1e}")
+    assert np.median(d) < 1e-5 and d.max() < 3e-4
+
+
+def test_tcgen05_serving_over_pair_list(ctx, trained):
+    """per-particle sums with the tcgen05 engine within 1e-3 of the oracle, deterministic"""
+    ctx.surrogate_init(KERNEL, 0).set_surrogate_params(trained[0])
+    ctx.set_surrogate_audit(64, TOL_SURROGATE)
+    ctx.set_surrogate_engine("tcgen05")
+    w = W.box_obstacle(2, 256, 80)
+    g, gr, _ = ctx.boundary_integrals(_t(w.particles), _t(w.triangles), KERNEL, w.H, -1, "surrogate")
+    st = ctx.stats()
+    g2, gr2, _ = ctx.integrals_from_pairs(KERNEL, -1, "surrogate")
+    ctx.set_surrogate_engine("mma_sync")
+    assert st["n_mma_timeouts"] == 0 and st["n_redo"] == 0
+    assert np.array_equal(g.cpu().numpy(), g2.cpu().numpy()) and np.array_equal(gr.cpu().numpy(), gr2.cpu().numpy())
+    idx = np.random.default_rng(87).choice(len(w.particles), 300, replace=False)
+    off, pt = oracle.cull(w.particles[idx], w.triangles, w.H)
+    og, ogr, _, _ = oracle.particle_sums(KERNEL, w.H, w.particles[idx], w.triangles, off, pt, -1)
+    got = np.concatenate([g.cpu().numpy()[idx, None], gr.cpu().numpy()[idx]], axis=1).astype(np.float64)
+    ref = np.concatenate([og[:, None], ogr], axis=1)
+    assert rel_err(got, ref, scales(KERNEL, w.H, 0)).max() <= TOL_SURROGATE
 
 
 def test_surrogate_gain_over_the_analytic_path(ctx, trained):
