@@ -851,12 +851,12 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
   }
 }
 
-// With all ten moments the cubic spline's pair code spills at 128 registers (~100 B per thread:
-// both pieces and the keyed sums); 3 resident blocks per SM (<= 168 registers, 12 warps) measured
-// 6% faster for it, while the Wendland kernels lose ~30% at that cap.
-template <typename OT, int MD> constexpr int cubic_split_minb() {
-  return sizeof(OT) == sizeof(float) && MD >= 3 ? 3 : int_minb<OT>();
-}
+// The cubic spline's partition kernel runs at the Wendland kernels' cap (4 blocks of 128 threads
+// per SM, <= 128 registers).  With its pieces' fans inlined it ran best at 3 blocks (168
+// registers).  With the fans looped, 4 blocks measured 6.5% faster than 3 with ten moments
+// (3.41 -> 3.19 ms on the 1024^2 box), although the ten-moment instance spills 92 bytes per
+// thread there.
+template <typename OT, int MD> constexpr int cubic_split_minb() { return int_minb<OT>(); }
 
 // chunks of 32 positions of the near/far partition
 template <typename OT, int MD>

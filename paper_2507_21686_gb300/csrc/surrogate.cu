@@ -1070,10 +1070,31 @@ sph2d_status surrogate_train(Ctx* c, const double* pairs, int64_t P, double H, i
 }
 
 // the values and fallback kernels for one pair source (fb_count already cleared)
+// Resident CTAs of the tcgen05 serving kernel per SM, from its three limits: shared memory
+// (static size plus the per-block reservation), registers, and tensor memory (64 of the SM's
+// 512 columns per CTA).  The runtime's occupancy query reports one block per SM for this kernel,
+// yet five run: measured 17.7 ms with one CTA per SM and 8.6 ms with five on the same pair list.
+template <typename K>
+static unsigned tc_grid(Ctx* c, K kern, int64_t wanted) {
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, kern);
+  int smem_sm = 0, res = 0, regs_sm = 0, sms = 0;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+  cudaDeviceGetAttribute(&res, cudaDevAttrReservedSharedMemoryPerBlock, c->device);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, c->device);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int64_t by_smem = int64_t(smem_sm) / std::max<int64_t>(1, int64_t(fa.sharedSizeBytes) + res);
+  const int64_t by_regs = int64_t(regs_sm) / std::max<int64_t>(1, int64_t(fa.numRegs) * 128);
+  const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(std::min(by_smem, by_regs), std::min<int64_t>(512 / 64, 16)));
+  const int64_t cap = per_sm * std::max(1, sms);
+  const int64_t want = wanted > 0 ? wanted : 1;
+  return unsigned(want < cap ? want : cap);
+}
+
 template <int KID, bool LIST>
 static void launch_serving(Ctx* c, const IntArgs& a, const double* pairs, const SurArgs& sa) {
   if (c->sur_engine == 1) {
-    const unsigned g1 = persistent_grid(c, surrogate_values_tc_kernel<KID, LIST>, (a.P + 127) / 128);
+    const unsigned g1 = tc_grid(c, surrogate_values_tc_kernel<KID, LIST>, (a.P + 127) / 128);
     SPH2D_LAUNCH(c, (surrogate_values_tc_kernel<KID, LIST>), g1, 128, a, pairs, sa);
   } else {
     const int64_t nch = (a.P + 31) / 32;

@@ -148,3 +148,20 @@ def test_mls_after_builds_without_triangles(ctx):
     ref = OP.mls_pressure("wendland_c2", 0.1, xy.astype(np.float32).astype(np.float64), vol.astype(np.float64),
                           p.astype(np.float64), pts.astype(np.float64))
     assert np.max(np.abs(got - ref)) < 1e-10 * np.abs(ref).max()
+
+
+def test_fma_peak_measurement():
+    """the FMA microbenchmark the bench reports against: plausible GB300 figures (derived FP32
+    FMA peak 80.5 TFLOP/s; NVIDIA's FP64 figure 1.25 TFLOP/s) and argument checks"""
+    import ctypes
+    from paper_2507_21686_gb300 import _lib
+    from paper_2507_21686_gb300.api import measure_fma_peak
+    fp32 = measure_fma_peak(0, "fp32", 0.05)
+    fp64 = measure_fma_peak(0, "fp64", 0.05)
+    assert 40.0 < fp32 < 90.0, fp32
+    assert 0.5 < fp64 < 2.0, fp64
+    lib = _lib.load()
+    out = ctypes.c_double()
+    assert lib.sph2d_measure_fma_peak(0, 2, 0.05, ctypes.byref(out)) == 1
+    assert lib.sph2d_measure_fma_peak(0, 0, 0.0, ctypes.byref(out)) == 1
+    assert lib.sph2d_measure_fma_peak(0, 0, 0.05, None) == 1
