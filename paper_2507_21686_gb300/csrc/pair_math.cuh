@@ -258,15 +258,32 @@ template <typename F>
 SPH2D_HD FFT<F> operator-(FFT<F> a) { return FFT<F>{-a.hi, -a.lo}; }
 template <typename F>
 SPH2D_HD FFT<F> operator-(FFT<F> a, FFT<F> b) { return a + (-b); }
+// Products return their two words without the final renormalisation unless
+// SPH2D_FF_NORM_PRODUCTS is set: every product here feeds an addition, which renormalises, or
+// another product, and the low word then stays within a few units of the high word's last
+// place, so the dropped lo x lo term stays far below the pair's unit roundoff.  Measured on the
+// 1024^2 box: FP32 passes 5-14% faster (C2 with ten moments 2.77 -> 2.39 ms), results within
+// 2.4e-7 of the FP64 form as before.
+#ifndef SPH2D_FF_NORM_PRODUCTS
+#define SPH2D_FF_NORM_PRODUCTS 0
+#endif
 template <typename F>
 SPH2D_HD FFT<F> operator*(FFT<F> a, FFT<F> b) {
   const FFT<F> p = ff_two_prod(a.hi, b.hi);
+#if SPH2D_FF_NORM_PRODUCTS
   return ff_fast_two_sum(p.hi, fma_f(a.hi, b.lo, fma_f(a.lo, b.hi, p.lo)));
+#else
+  return FFT<F>{p.hi, fma_f(a.hi, b.lo, fma_f(a.lo, b.hi, p.lo))};
+#endif
 }
 template <typename F>
 SPH2D_HD FFT<F> operator*(FFT<F> a, F b) {
   const FFT<F> p = ff_two_prod(a.hi, b);
+#if SPH2D_FF_NORM_PRODUCTS
   return ff_fast_two_sum(p.hi, fma_f(a.lo, b, p.lo));
+#else
+  return FFT<F>{p.hi, fma_f(a.lo, b, p.lo)};
+#endif
 }
 template <typename F>
 SPH2D_HD FFT<F> ff_sqrt(FFT<F> x) {               // one Newton step on sqrt(hi)

@@ -655,49 +655,23 @@ __global__ void __launch_bounds__(128) surrogate_values_tc_kernel(IntArgs a, con
   unsigned long long timeouts = 0;
   const float ih = float(a.invH);
   const int64_t ntiles = (a.P + 127) / 128;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t q = tile * 128 + tid;
-    float lf[6] = {0, 0, 0, 0, 0, 0};
-    if (q < a.P) load_local<LIST>(a, pairs, q, ih, lf);
-    const Canon c = canonicalize(lf);
-    bool use = (q < a.P) && c.accept;
-    float y[16];
-    bool tile_ok = healthy;
-    if (healthy) {
-      {   // the input row: 6 canonical coordinates, zero padded to K = 16
-        uint32_t w[8];
+  // Software pipeline over the CTA's tiles (t, t + grid, ...), so that work that does not depend
+  // on the tensor core overlaps its MMAs: tile t+2's local frame is loaded while tile t runs;
+  // tile t+1's canonical frame is computed and its input row staged while tile t's output
+  // layer runs (the input operand is free once tile t's first layer has completed); tile t's
+  // epilogue (values, guard flags, fallback and audit lists) runs while tile t+1's first
+  // layer runs.
+  auto stage_input = [&](const Canon& c, bool use) {
+    uint32_t w[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          w[j] = pack_f16(2 * j < kSurIn && use ? c.x[2 * j] : 0.0f, 2 * j + 1 < kSurIn && use ? c.x[2 * j + 1] : 0.0f);
-        *reinterpret_cast<uint4*>(s.a0 + umma::kmajor_offset(tid, 0, 16) / 2) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(s.a0 + umma::kmajor_offset(tid, 8, 16) / 2) = make_uint4(w[4], w[5], w[6], w[7]);
-      }
-      umma::fence_proxy_async();
-      umma::fence_before_sync();
-      __syncthreads();
-      if (tid == 0) tc_issue(s, tm, sa0, sw1, 1, 256, 256, ID64);
-      tile_ok = tc_wait(s, phase);
-      const float* bias[3] = {s.b1, s.b2, s.b3};
-      const uint32_t wl[3] = {sw2, sw3, sw4};
-#pragma unroll 1
-      for (int l = 0; l < 3 && tile_ok; ++l) {
-        tc_hidden_row(s, trow, bias[l], s.act, tid);
-        umma::fence_proxy_async();
-        umma::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) tc_issue(s, tm, sact, wl[l], 4, 1024, 1024, l < 2 ? ID64 : ID16);
-        tile_ok = tc_wait(s, phase);
-      }
-      if (tile_ok) {
-        umma::tmem_ld16(trow, y);
-#pragma unroll
-        for (int j = 0; j < kSurOut; ++j) y[j] += s.b4[j];
-      } else {
-        healthy = false;
-        ++timeouts;
-      }
-    }
-    use = use && tile_ok;
+    for (int j = 0; j < 8; ++j)
+      w[j] = pack_f16(2 * j < kSurIn && use ? c.x[2 * j] : 0.0f, 2 * j + 1 < kSurIn && use ? c.x[2 * j + 1] : 0.0f);
+    *reinterpret_cast<uint4*>(s.a0 + umma::kmajor_offset(tid, 0, 16) / 2) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(s.a0 + umma::kmajor_offset(tid, 8, 16) / 2) = make_uint4(w[4], w[5], w[6], w[7]);
+  };
+  // one tile's results: values of the accepted pairs, guard flags, fallback and audit entries
+  // (every thread of the CTA calls it: the list appends are warp-wide)
+  auto epilogue = [&](int64_t q, const Canon& c, bool use, const float* y) {
     if (use) {
       float lx, ly;
       uncanonicalize_grad(c, c.area * y[1], c.area * y[2], lx, ly);
@@ -723,7 +697,62 @@ __global__ void __launch_bounds__(128) surrogate_values_tc_kernel(IntArgs a, con
       base = __shfl_sync(0xffffffffu, base, leader);
       if (aud) sa.fb_list[a.P - 1 - int64_t(base + __popc(am & ((1u << lane) - 1u)))] = q;
     }
+  };
+  int64_t tile = blockIdx.x;
+  float lf[6] = {0, 0, 0, 0, 0, 0}, lnext[6] = {0, 0, 0, 0, 0, 0};
+  if (tile * 128 + tid < a.P) load_local<LIST>(a, pairs, tile * 128 + tid, ih, lf);
+  if ((tile + gridDim.x) * 128 + tid < a.P) load_local<LIST>(a, pairs, (tile + gridDim.x) * 128 + tid, ih, lnext);
+  Canon c_cur = canonicalize(lf);
+  bool use_cur = tile * 128 + tid < a.P && c_cur.accept;
+  stage_input(c_cur, use_cur);
+  Canon c_prev = c_cur;
+  bool use_prev = false, have_prev = false;
+  int64_t q_prev = 0;
+  float y_prev[3] = {0, 0, 0};
+  const float* bias[3] = {s.b1, s.b2, s.b3};
+  const uint32_t wl[3] = {sw2, sw3, sw4};
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t q = tile * 128 + tid;
+    bool tile_ok = healthy;
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (healthy && tid == 0) tc_issue(s, tm, sa0, sw1, 1, 256, 256, ID64);
+    if (have_prev) epilogue(q_prev, c_prev, use_prev, y_prev);
+    if (healthy) tile_ok = tc_wait(s, phase);
+#pragma unroll 1
+    for (int l = 0; l < 3 && tile_ok; ++l) {
+      tc_hidden_row(s, trow, bias[l], s.act, tid);
+      umma::fence_proxy_async();
+      umma::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) tc_issue(s, tm, sact, wl[l], 4, 1024, 1024, l < 2 ? ID64 : ID16);
+      if (l < 2) tile_ok = tc_wait(s, phase);
+    }
+    // the output layer's MMA is in flight (if the tile is healthy): the next tile's inputs
+    const int64_t qn = q + int64_t(gridDim.x) * 128;
+    const Canon c_next = canonicalize(lnext);
+    const bool use_next = qn < a.P && c_next.accept;
+    stage_input(c_next, use_next);
+    if (qn + int64_t(gridDim.x) * 128 < a.P) load_local<LIST>(a, pairs, qn + int64_t(gridDim.x) * 128, ih, lnext);
+    if (tile_ok) tile_ok = tc_wait(s, phase);
+    float y[16];
+    if (tile_ok) {
+      umma::tmem_ld16(trow, y);
+#pragma unroll
+      for (int j = 0; j < kSurOut; ++j) y_prev[j] = y[j] + s.b4[j];
+    } else if (healthy) {
+      healthy = false;
+      ++timeouts;
+    }
+    c_prev = c_cur;
+    use_prev = use_cur && tile_ok;
+    q_prev = q;
+    have_prev = true;
+    c_cur = c_next;
+    use_cur = use_next;
   }
+  if (have_prev) epilogue(q_prev, c_prev, use_prev, y_prev);
   if (!healthy) umma::mbar_wait(&s.mbar, phase, kTcSpin);   // let an overdue MMA drain
   umma::fence_before_sync();
   __syncthreads();

@@ -85,8 +85,9 @@ def test_compensated_log_accuracy(tmp_path):
     subprocess.run([cxx, "-std=c++17", "-O2", "-ffp-contract=off", "-I", CSRC, str(src), "-o", str(exe)], check=True)
     ef, efn, ed = map(float, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split())
     # float pairs: relative 2^-44 near and around 1 (where the result is small), absolute
-    # 1e-12 over 60 decades (|ln x| up to 70 times the pair's relative precision);
+    # 2e-12 over 60 decades (|ln x| up to 70 times the pair's relative precision: the e ln 2
+    # term carries the ln 2 pair's rounding times e);
     # double pairs: long double's own precision (2^-64) bounds what this check can see
     assert ef < 6e-14, ef
-    assert efn < 1e-12, efn
+    assert efn < 2e-12, efn
     assert ed < 3e-19, ed
