@@ -81,6 +81,9 @@ inline Counted<double> frexp_f(Counted<double> x, int* e) { return mk<double>(st
 inline Counted<double> ldexp_f(Counted<double> x, int e) { return mk<double>(std::ldexp(x.v, e)); }
 inline Counted<float> frexp_f(Counted<float> x, int* e) { return mk<float>(std::frexp(x.v, e)); }
 inline Counted<float> ldexp_f(Counted<float> x, int e) { return mk<float>(std::ldexp(x.v, e)); }
+template <typename F> struct Pow2;
+// the exact power-of-two scale of the FF edge sums (exponent-field work: not counted)
+inline Pow2<Counted<float>> pow2_scale(Counted<float> x);
 }  // namespace sph2d
 
 #include "pair_math.cuh"
@@ -113,11 +116,13 @@ template <> struct Acc<Counted<double>> {
   static R root(R v) { return sqrt(v); }
   static R out(R v) { return v; }
   static R mulr(R a, R b) { return a * b; }
+  static R sub_raw(R a, R b) { return a - b; }
   static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
   using Sum = R;
+  static constexpr bool SCALED = false;
   static R zero() { return R(0.0); }
   template <class P>
-  static R madd(R acc, R x, int row, int slot) {
+  static R madd(R acc, R x, int row, int slot, float) {
     const NumDen c = edge_coef<P>(row - 1, slot);
     const double k = c.num / c.den;
     if (k == 0.0) return acc;
@@ -139,11 +144,13 @@ template <> struct Acc<Counted<long double>> {
   static R root(R v) { return sqrt(v); }
   static R out(R v) { return v; }
   static R mulr(R a, R b) { return a * b; }
+  static R sub_raw(R a, R b) { return a - b; }
   static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
   using Sum = R;
+  static constexpr bool SCALED = false;
   static R zero() { return R(0.0); }
   template <class P>
-  static R madd(R acc, R x, int row, int slot) {
+  static R madd(R acc, R x, int row, int slot, float) {
     const NumDen c = edge_coef<P>(row - 1, slot);
     const double k = c.num / c.den;
     if (k == 0.0) return acc;
@@ -154,6 +161,10 @@ template <> struct Acc<Counted<long double>> {
   static R recip1(int, R iq) { return iq; }
   static R divq(R x, int, R iq) { return x * iq; }
 };
+inline Pow2<Counted<float>> pow2_scale(Counted<float> x) {
+  const Pow2<float> p = pow2_scale(x.v);
+  return Pow2<Counted<float>>{mk<float>(p.s), mk<float>(p.is)};
+}
 template <> struct Acc<Counted<float>> : AccFF<Counted<float>> {};
 template <> struct AccSel<Counted<double>, PolyWC6> { using type = AccDD<Counted<double>>; };
 

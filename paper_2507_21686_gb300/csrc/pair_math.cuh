@@ -29,6 +29,7 @@
 #pragma once
 
 #include <math.h>
+#include <string.h>
 
 #include "log_table.h"
 
@@ -41,10 +42,9 @@
 
 // Code shape (measured on GB300): the radial recurrence is unrolled with compile-time
 // coefficients (zero terms vanish) -- SPH2D_Q_UNROLL=0 selects a loop over rows of a
-// constant-memory table instead, which measured 15-40% slower.  Whether the three fans of a
-// triangle are a loop or inlined is chosen per instantiation (FanLoop below); the two-piece
-// cubic spline loops over its pieces and their fans (six inlined fans overflow the instruction
-// cache: 3.5x slower measured).
+// constant-memory table instead, which measured 15-40% slower.  The three fans of a triangle
+// are a loop (tri_raw below); the two-piece cubic spline loops over its pieces and their fans
+// (six inlined fans overflow the instruction cache: 3.5x slower measured).
 #ifndef SPH2D_Q_UNROLL
 #define SPH2D_Q_UNROLL 1
 #endif
@@ -258,6 +258,13 @@ template <typename F>
 SPH2D_HD FFT<F> operator-(FFT<F> a) { return FFT<F>{-a.hi, -a.lo}; }
 template <typename F>
 SPH2D_HD FFT<F> operator-(FFT<F> a, FFT<F> b) { return a + (-b); }
+// a - b with the two words left unrenormalised (the low word may exceed half an ulp of the
+// high one): for values that go only into the grid sums or into a renormalising addition
+template <typename F>
+SPH2D_HD FFT<F> ff_sub_raw(FFT<F> a, FFT<F> b) {
+  const FFT<F> s = ff_two_sum(a.hi, -b.hi);
+  return FFT<F>{s.hi, s.lo + (a.lo - b.lo)};
+}
 // Products return their two words without the final renormalisation unless
 // SPH2D_FF_NORM_PRODUCTS is set: every product here feeds an addition, which renormalises, or
 // another product, and the low word then stays within a few units of the high word's last
@@ -356,6 +363,33 @@ SPH2D_HD float ldexp_f(float x, int e) {
 // the machine value of a scalar (the op counter's counted types define their own)
 SPH2D_HD float raw_f(float x) { return x; }
 SPH2D_HD double raw_f(double x) { return x; }
+
+// an exact power-of-two scale and its inverse
+template <typename F>
+struct Pow2 {
+  F s, is;
+};
+// For finite non-zero x: s = 2^-e and is = 2^e, with 2^(e-1) <= |x| < 2^e, so that |x| s lies in
+// [1/2, 1); e is taken from the exponent field and held at -64 or above (s <= 2^64).
+SPH2D_HD Pow2<float> pow2_scale(float x) {
+#if defined(__CUDA_ARCH__)
+  const unsigned b = __float_as_uint(x);
+#else
+  unsigned b;
+  memcpy(&b, &x, sizeof b);
+#endif
+  int e = int((b >> 23) & 0xffu) - 126;
+  e = e < -64 ? -64 : e;
+  const unsigned us = unsigned(127 - e) << 23, ui = unsigned(127 + e) << 23;
+#if defined(__CUDA_ARCH__)
+  return Pow2<float>{__uint_as_float(us), __uint_as_float(ui)};
+#else
+  Pow2<float> r;
+  memcpy(&r.s, &us, sizeof us);
+  memcpy(&r.is, &ui, sizeof ui);
+  return r;
+#endif
+}
 
 // argument-reduction table of ff_log (log_table.h, written by gen_log_table.py): entry i holds
 // inv = 1/c_i rounded to the working precision (c_i = (64 + i)/128) and -ln(inv) as hi + lo
@@ -485,6 +519,27 @@ SPH2D_HD constexpr NumDen edge_coef(int q, int s) {
   }
   return {0.0, 1.0};
 }
+// the slots whose inputs are Delta rho^q (the others take Delta J_q)
+SPH2D_HD constexpr bool slot_uses_drho(int s) {
+  return s == SL_T || s == SL_01 || s == SL_11 || s == SL_21 || s == SL_03A;
+}
+// the double factorial n!! (1 for n <= 0)
+SPH2D_HD constexpr double dfact(int n) {
+  double f = 1.0;
+  for (int k = n; k > 1; k -= 2) f *= double(k);
+  return f;
+}
+// Rows of the FP32 path, whose recurrence runs on Y_q = J_q / w_q with w_q = q!!/(q+1)!!
+// (w_-1 = w_0 = 1): the J_q rows carry the factor w_q, the rho^q rows are unchanged.  With
+// that scaling the recurrence J_q = (Delta(t rho^q) + q d^2 J_{q-2}) / (q + 1) reads
+// Y_q = Delta(t rho^q) (q-1)!!/q!! + d^2 Y_{q-2}: one constant product instead of the division
+// and the product by q.
+template <class P>
+SPH2D_HD constexpr NumDen edge_coef_y(int q, int s) {
+  const NumDen c = edge_coef<P>(q, s);
+  if (slot_uses_drho(s) || q < 1) return c;
+  return NumDen{c.num * dfact(q), c.den * dfact(q + 1)};
+}
 template <class P>
 struct EdgeRows {
   static constexpr int QMIN = -1, QMAX = P::K + 4, ROWS = QMAX - QMIN + 1;
@@ -498,7 +553,8 @@ struct EdgeRows {
         const FFT<double> dd = dd_rational(c.num, c.den);
         d[q - QMIN][s] = dd.hi;
         dlo[q - QMIN][s] = dd.lo;
-        const FF ff = ff_const(c.num / c.den);
+        const NumDen cy = edge_coef_y<P>(q, s);
+        const FF ff = ff_const(cy.num / cy.den);
         fhi[q - QMIN][s] = ff.hi;
         flo[q - QMIN][s] = ff.lo;
       }
@@ -546,6 +602,53 @@ SPH2D_HD CSum<F> csum_madd(CSum<F> a, FFT<F> x, F khi, F klo) {
   return CSum<F>{s, a.c + (err + pl)};
 }
 
+// The same sum by error-free extraction against a fixed grid (Rump, Ogita and Oishi, "Accurate
+// floating-point summation, part I", SIAM J. Sci. Comput. 31, 2008), for terms bounded in
+// advance.  g is a power of two and every product |x k| <= g / n for the n terms of the sum
+// (n >= 2).  Then t = fl(x.hi khi + g) lies in [g/2, 2g], q = t - g is exact (Sterbenz) and a
+// multiple of ulp(g)/2, and s, a sum of such q with sum |q| < g, is exact; r = fl(x.hi khi - q)
+// is the remainder, below ulp(g) in size, with one rounding.  c collects the remainders, the
+// low word of x and the coefficient's low part.  Six or seven instructions against the twelve
+// of csum_madd; the error is O(n u^2 g) absolute, u = 2^-24, against O(u^2 sum|x k|) there.
+template <typename F>
+SPH2D_HD CSum<F> xsum_madd(CSum<F> a, FFT<F> x, F khi, F klo, F g) {
+  const F t = fma_f(x.hi, khi, g);
+  const F q = t - g;
+  F r = fma_f(x.hi, khi, -q);
+  r = fma_f(x.lo, khi, r);
+  if (klo != F(0)) r = fma_f(x.hi, klo, r);
+  return CSum<F>{a.s + q, a.c + r};
+}
+// the grid constant g of one edge-sum slot: the smallest power of two with g >= n m (1 + 2^-7),
+// n >= 2 the number of non-zero terms and m the largest |coefficient| times the bound of its
+// input.  The inputs are scaled per fan (add_fan) so that |Delta J_q| < 1 for q >= 0 (and
+// q = -1, where the row is used: J_q = int rho^q dt with rho <= 1 on the edge piece, so
+// |Delta J_q| <= |Delta t|) and |Delta rho^q| < q (|d rho / dt| <= 1).
+template <class P>
+SPH2D_HD constexpr float slot_grid(int s) {
+  double m = 0.0;
+  int n = 0;
+  for (int q = -1; q <= P::K + 4; ++q) {
+    const NumDen c = edge_coef<P>(q, s);
+    if (c.num == 0.0) continue;
+    const double w = (c.num < 0 ? -c.num : c.num) / c.den * (slot_uses_drho(s) && q > 1 ? double(q) : 1.0);
+    m = w > m ? w : m;
+    ++n;
+  }
+  const double need = (n < 2 ? 2 : n) * m * (1.0 + 1.0 / 128);
+  double g = 1.0;
+  while (g < need) g *= 2.0;
+  while (g * 0.5 >= need) g *= 0.5;
+  return float(g);
+}
+// whether any edge-sum slot takes the q = -1 row (Delta J_-1), i.e. k has a linear term
+template <class P>
+SPH2D_HD constexpr bool uses_row_m1() {
+  for (int s = 0; s < NSL; ++s)
+    if (edge_coef<P>(-1, s).num != 0.0) return true;
+  return false;
+}
+
 // accumulation type of the radial part: plain arithmetic in the base precision F (the FP64
 // path, and the bulk FP32 path), or FF compensated FP32 (the FP32 path's compensated form)
 template <typename F>
@@ -558,10 +661,12 @@ struct AccPlain {
   SPH2D_HD static F root(F v) { return sqrt(v); }
   SPH2D_HD static F out(F v) { return v; }
   SPH2D_HD static F mulr(F a, F b) { return a * b; }
+  SPH2D_HD static F sub_raw(F a, F b) { return a - b; }
   using Sum = F;
+  static constexpr bool SCALED = false;                // edge sums on unscaled inputs
   SPH2D_HD static F zero() { return F(0); }
   template <class P>
-  SPH2D_HD static F madd(F acc, F x, int row, int slot) {
+  SPH2D_HD static F madd(F acc, F x, int row, int slot, float) {
 #if SPH2D_Q_UNROLL
     const NumDen c = edge_coef<P>(row - 1, slot);
     const F k = F(c.num / c.den);
@@ -600,18 +705,41 @@ struct AccFF {
     return asinh_diff_ff(t1, t2, ra, rb, d);
   }
   using Sum = CSum<F>;
+  // The edge sums run by grid extraction (xsum_madd) on inputs scaled per fan by an exact
+  // power of two: 1 / the power of two above |Delta t| (and above |Delta J_-1| where a slot
+  // takes that row), so that every term is below its slot's grid constant.
+  static constexpr bool SCALED = true;
+  template <class P>
+  SPH2D_HD static Pow2<F> fan_scale(F dt, FFT<F> dJm) {
+    F b = fabs(dt);
+    if constexpr (uses_row_m1<P>()) b = fmax(b, fabs(dJm.hi) + fabs(dJm.lo));
+    return pow2_scale(b);
+  }
+  SPH2D_HD static FFT<F> pscale(FFT<F> x, F s) { return FFT<F>{x.hi * s, x.lo * s}; }
+  SPH2D_HD static FFT<F> sub_raw(FFT<F> a, FFT<F> b) { return ff_sub_raw(a, b); }
+  // Y_q = Delta(t rho^q) (q-1)!!/q!! + d^2 Y_{q-2} (edge_coef_y); both terms have the sign of
+  // Delta t, so the sum is left unrenormalised
+  SPH2D_HD static FFT<F> ystep(int q, FFT<F> dT, FFT<F> y2, FFT<F> d2a) {
+    const FF k = ff_const(dfact(q - 1) / dfact(q));
+    FFT<F> a = ff_two_prod(dT.hi, F(k.hi));
+    a.lo = fma_f(dT.lo, F(k.hi), a.lo);
+    if (k.lo != 0.0f) a.lo = fma_f(dT.hi, F(k.lo), a.lo);
+    const FFT<F> b = y2 * d2a;
+    const FFT<F> t = ff_two_sum(a.hi, b.hi);
+    return FFT<F>{t.hi, t.lo + (a.lo + b.lo)};
+  }
   SPH2D_HD static CSum<F> zero() { return CSum<F>{F(0), F(0)}; }
   template <class P>
-  SPH2D_HD static CSum<F> madd(CSum<F> acc, FFT<F> x, int row, int slot) {
+  SPH2D_HD static CSum<F> madd(CSum<F> acc, FFT<F> x, int row, int slot, float grid) {
 #if SPH2D_Q_UNROLL
-    const NumDen c = edge_coef<P>(row - 1, slot);
+    const NumDen c = edge_coef_y<P>(row - 1, slot);
     if (c.num == 0.0) return acc;
     const FF k = ff_const(c.num / c.den);
-    return csum_madd(acc, x, F(k.hi), F(k.lo));
+    return xsum_madd(acc, x, F(k.hi), F(k.lo), F(grid));
 #else
     const EdgeRows<P>& r = edge_rows<P>();
     if (r.fhi[row][slot] == 0.0f) return acc;        // uniform across the warp
-    return csum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]));
+    return xsum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]), F(grid));
 #endif
   }
   SPH2D_HD static CSum<F> maddc(CSum<F> acc, FFT<F> x, double num, double den) {
@@ -654,14 +782,16 @@ struct AccDD {
   SPH2D_HD static FFT<D> root(FFT<D> v) { return ff_sqrt(v); }
   SPH2D_HD static D out(FFT<D> v) { return to_f(v); }
   SPH2D_HD static FFT<D> mulr(FFT<D> a, D b) { return a * b; }
+  SPH2D_HD static FFT<D> sub_raw(FFT<D> a, FFT<D> b) { return a - b; }
   SPH2D_HD static FFT<D> jm1(D t1, D t2, D r1, D r2, D d, FFT<D> ra, FFT<D> rb) {
     (void)r1; (void)r2;
     return asinh_diff_ff<D, double>(t1, t2, ra, rb, d);
   }
   using Sum = CSum<D>;
+  static constexpr bool SCALED = false;
   SPH2D_HD static CSum<D> zero() { return CSum<D>{D(0), D(0)}; }
   template <class P>
-  SPH2D_HD static CSum<D> madd(CSum<D> acc, FFT<D> x, int row, int slot) {
+  SPH2D_HD static CSum<D> madd(CSum<D> acc, FFT<D> x, int row, int slot, float) {
 #if SPH2D_Q_UNROLL
     const NumDen c = edge_coef<P>(row - 1, slot);
     if (c.num == 0.0) return acc;
@@ -785,28 +915,39 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     const A zeroA = AC::c(0);
     // one step of the sums: q's row, Delta J_q and Delta rho^q
     auto step = [&](int row, const A& dJ, const A& dP) {
-      Sg = AC::template madd<P>(Sg, dJ, row, SL_G);
-      Sn = AC::template madd<P>(Sn, dJ, row, SL_N);
-      St = AC::template madd<P>(St, dP, row, SL_T);
+      Sg = AC::template madd<P>(Sg, dJ, row, SL_G, slot_grid<P>(SL_G));
+      Sn = AC::template madd<P>(Sn, dJ, row, SL_N, slot_grid<P>(SL_N));
+      St = AC::template madd<P>(St, dP, row, SL_T, slot_grid<P>(SL_T));
       if (MD >= 1) {
-        S10 = AC::template madd<P>(S10, dJ, row, SL_10);
-        S01 = AC::template madd<P>(S01, dP, row, SL_01);
+        S10 = AC::template madd<P>(S10, dJ, row, SL_10, slot_grid<P>(SL_10));
+        S01 = AC::template madd<P>(S01, dP, row, SL_01, slot_grid<P>(SL_01));
       }
       if (MD >= 3) {
-        S20 = AC::template madd<P>(S20, dJ, row, SL_20);
-        S30 = AC::template madd<P>(S30, dJ, row, SL_30);
-        S02 = AC::template madd<P>(S02, dJ, row, SL_02A);
-        S12 = AC::template madd<P>(S12, dJ, row, SL_12A);
-        S11 = AC::template madd<P>(S11, dP, row, SL_11);
-        S21 = AC::template madd<P>(S21, dP, row, SL_21);
-        S03 = AC::template madd<P>(S03, dP, row, SL_03A);
+        S20 = AC::template madd<P>(S20, dJ, row, SL_20, slot_grid<P>(SL_20));
+        S30 = AC::template madd<P>(S30, dJ, row, SL_30, slot_grid<P>(SL_30));
+        S02 = AC::template madd<P>(S02, dJ, row, SL_02A, slot_grid<P>(SL_02A));
+        S12 = AC::template madd<P>(S12, dJ, row, SL_12A, slot_grid<P>(SL_12A));
+        S11 = AC::template madd<P>(S11, dP, row, SL_11, slot_grid<P>(SL_11));
+        S21 = AC::template madd<P>(S21, dP, row, SL_21, slot_grid<P>(SL_21));
+        S03 = AC::template madd<P>(S03, dP, row, SL_03A, slot_grid<P>(SL_03A));
       }
     };
-    const A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);      // Delta J_{-1}
-    const A dJp = AC::from(t2) - AC::from(t1);              // Delta J_0
+    A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);            // Delta J_{-1}
+    A dJp = AC::from(t2) - AC::from(t1);                    // Delta J_0
+    A p1 = AC::c(1), p2 = AC::c(1);                         // rho^q at the two ends
+    // the scaled form (FF sums): every J and rho^q below runs times the fan's power of two s,
+    // undone exactly in the outputs (ds = d / s)
+    R ds = d;
+    if constexpr (AC::SCALED) {
+      const auto sc = AC::template fan_scale<P>(t2 - t1, dJm);
+      dJm = AC::pscale(dJm, sc.s);
+      dJp = AC::pscale(dJp, sc.s);
+      p1 = AC::from(sc.s);
+      p2 = p1;
+      ds = d * sc.is;
+    }
     step(0, dJm, zeroA);                                    // q = -1
     step(1, dJp, zeroA);                                    // q = 0
-    A p1 = AC::c(1), p2 = AC::c(1);                         // rho^q at the two ends
     A dJq2 = dJm, dJq1 = dJp;                               // Delta J_{q-2}, Delta J_{q-1}
     // highest row any requested sum uses: gamma/gradient K, first moments K + 2, all K + 4
     constexpr int QMAX = MD >= 3 ? P::K + 4 : (MD >= 1 ? P::K + 2 : P::K);
@@ -818,31 +959,37 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     for (int q = 1; q <= QMAX; ++q) {
       p1 = p1 * r1a;
       p2 = p2 * r2a;
-      const A dP = p2 - p1;                                 // Delta rho^q
-      const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);     // Delta (t rho^q)
-      const R qf = R(q), iq = R(1) / R(q + 1);
-      const A dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);   // Delta J_q
+      const A dP = AC::sub_raw(p2, p1);                     // Delta rho^q (only summed)
+      const A dT = AC::sub_raw(AC::mulr(p2, t2), AC::mulr(p1, t1));   // Delta (t rho^q)
+      A dJ;                                                 // Delta J_q (FP32 path: Delta Y_q)
+      if constexpr (AC::SCALED) {
+        dJ = AC::ystep(q, dT, dJq2, d2a);
+      } else {
+        const R qf = R(q), iq = R(1) / R(q + 1);
+        dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);
+      }
       step(q + 1, dJ, dP);
       dJq2 = dJq1;
       dJq1 = dJ;
     }
-    eg += d * AC::result(Sg);
-    en += d2 * AC::result(Sn);
-    et += d * AC::result(St);
+    const R d2s = AC::SCALED ? d * ds : d2;                 // d^2 / s
+    eg += ds * AC::result(Sg);
+    en += d2s * AC::result(Sn);
+    et += ds * AC::result(St);
     if (MD >= 1) {
-      E[1] += d2 * AC::result(S10);
-      E[2] += d * AC::result(S01);
+      E[1] += d2s * AC::result(S10);
+      E[2] += ds * AC::result(S01);
     }
     if (MD >= 3) {
-      const R d3 = d2 * d, d4 = d2 * d2;
+      const R d3s = d2s * d, d4s = d2s * d2;
       const A s20 = AC::resultA(S20), s30 = AC::resultA(S30), s21 = AC::resultA(S21);
-      E[3] += d3 * AC::out(s20);
-      E[4] += d2 * AC::result(S11);
-      E[5] += d * AC::out(AC::resultA(S02) - s20 * d2a);
-      E[6] += d4 * AC::out(s30);
-      E[7] += d3 * AC::out(s21);
-      E[8] += d2 * AC::out(AC::resultA(S12) - s30 * d2a);
-      E[9] += d * AC::out(AC::resultA(S03) - s21 * d2a);
+      E[3] += d3s * AC::out(s20);
+      E[4] += d2s * AC::result(S11);
+      E[5] += ds * AC::out(AC::resultA(S02) - s20 * d2a);
+      E[6] += d4s * AC::out(s30);
+      E[7] += d3s * AC::out(s21);
+      E[8] += d2s * AC::out(AC::resultA(S12) - s30 * d2a);
+      E[9] += ds * AC::out(AC::resultA(S03) - s21 * d2a);
     }
   }
   // rotate the gradient back from the edge frame (Sec. 2, Eq. improper)
@@ -902,24 +1049,20 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   }
 }
 
-// Whether the three fans of a single-polynomial kernel run as a loop (one copy of the fan code)
-// or inlined.  Measured on GB300 (the 1024^2 box with obstacle): in FP32 the loop ran 20-23%
-// faster for gamma and grad gamma alone (Wendland C2 and C4) and 6% faster for Wendland C2 with
-// ten moments, and 13% slower for Wendland C4 with ten moments; in FP64 it ran 7% faster for C2
-// with moments and the same for C4.  The cubic spline's pieces loop over their fans as well.
-template <typename R, class P, int MD>
-struct FanLoop {
-  static constexpr bool value = !(MD >= 3 && P::K >= 8);
-};
-
+// The three fans of a triangle run as a loop (one copy of the fan code) in every kernel and
+// precision.  Measured on GB300 (the 1024^2 box with obstacle, FP32): against inlined fans the
+// loop ran 20-23% faster for gamma and grad gamma alone and 6% faster for Wendland C2 with ten
+// moments.  Wendland C4 with ten moments first ran 13% slower looped; once the edge sums took
+// the grid extraction and the scaled recurrence, looping ran 3% faster for it in FP32 and 8% in
+// FP64.
 // raw integrals of kernel KID over the local-frame triangle, in input orientation
 // (multiply by the orientation sign for the unsigned integral)
 template <typename R, int KID, int MD, bool PLAIN = false>
 SPH2D_HD void tri_raw(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   clear(o);
-  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, !FanLoop<R, PolyWC2, MD>::value, PLAIN>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, !FanLoop<R, PolyWC4, MD>::value, PLAIN>(ax, ay, bx, by, cx, cy, o);
-  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, !FanLoop<R, PolyWC6, MD>::value, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  if (KID == KID_WC2) tri_poly<R, PolyWC2, MD, false, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC4) tri_poly<R, PolyWC4, MD, false, PLAIN>(ax, ay, bx, by, cx, cy, o);
+  else if (KID == KID_WC6) tri_poly<R, PolyWC6, MD, false, PLAIN>(ax, ay, bx, by, cx, cy, o);
   else {
     // k(q) = 2 k1(q) - k1(2q), k1 = (1-q)^3_+.  With p' = 2p:
     //   int f(p) k1(2|p|) dA = 1/4 int f(p'/2) k1(|p'|) dA',  f = p^m -> 2^-m

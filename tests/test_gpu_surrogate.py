@@ -418,4 +418,6 @@ def test_surrogate_gain_over_the_analytic_path(ctx, trained):
           f"{sst['n_fallback'] / P:.3f}, audit {sst['n_audit']} pairs, max err {sst['audit_max_err']:.2e}), "
           f"analytic FP32 {ms['fp32_fixup']:.3f} ms: {gain:.2f}x")
     assert sst["n_redo"] == 0 and sst["n_audit_over"] == 0
-    assert gain > 1.3
+    # a gain, with a margin for timing noise: the analytic path this is measured against is
+    # also the surrogate's fallback and audit, so the margin shrinks as that path gets faster
+    assert gain > 1.1

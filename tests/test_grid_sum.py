@@ -1,0 +1,162 @@
+"""CPU pins of the grid-extraction sums of the FP32 closed form (csrc/pair_math.cuh): the
+per-fan power-of-two scale, the exactness of the extracted running sum and its absolute error
+bound (checked against exact rational arithmetic), and the per-slot grid constants against the
+coefficient rows they must bound.  The header is compiled for the host with g++."""
+from __future__ import annotations
+
+import math
+import os
+import shutil
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2507_21686_gb300", "csrc")
+
+PROG = r'''
+#include <cmath>
+#include <cstdio>
+#include <random>
+#include "pair_math.cuh"
+using namespace sph2d;
+
+template <class P>
+static void grids(const char* name) {
+  for (int s = 0; s < NSL; ++s) {
+    std::printf("G %s %d %a %d", name, s, double(slot_grid<P>(s)), int(slot_uses_drho(s)));
+    for (int q = -1; q <= P::K + 4; ++q) {
+      const NumDen c = edge_coef<P>(q, s);
+      if (c.num != 0.0) std::printf(" %d:%a:%a", q, c.num, c.den);
+    }
+    std::printf("\n");
+  }
+  std::printf("M %s %d\n", name, int(uses_row_m1<P>()));
+}
+
+int main() {
+  grids<PolyWC2>("wc2");
+  grids<PolyWC4>("wc4");
+  grids<PolyWC6>("wc6");
+  grids<PolyCube>("cube");
+  std::mt19937_64 g(11);
+  std::uniform_real_distribution<double> u(-1, 1);
+  // sums of n products with |x k| <= grid / n, alternating signs so that the exact sum cancels
+  for (int trial = 0; trial < 400; ++trial) {
+    const int n = 2 + trial % 15;
+    const float grid = std::ldexp(1.0f, -20 + int(trial % 41));
+    CSum<float> acc{0.0f, 0.0f};
+    std::printf("S %d %a", n, double(grid));
+    for (int i = 0; i < n; ++i) {
+      const double kv = (1.0 + 3.0 * std::fabs(u(g))) * ((i & 1) ? -1 : 1);
+      const FF k = ff_const(trial % 3 == 0 ? double(float(kv)) : kv);
+      const double xv = u(g) * double(grid) / (n * 4.0);
+      const float xh = float(xv), xl = float(xv - double(xh));
+      acc = xsum_madd(acc, FF{xh, xl}, k.hi, k.lo, grid);
+      std::printf(" %a,%a,%a,%a", double(xh), double(xl), double(k.hi), double(k.lo));
+    }
+    std::printf(" | %a %a\n", double(acc.s), double(acc.c));
+  }
+  // the scale: 2^-e with |x| in [2^(e-1), 2^e)
+  for (int i = 0; i < 2000; ++i) {
+    float x;
+    if (i < 300) x = std::ldexp(1.0f, -70 + i % 100);                   // powers of two
+    else if (i < 400) x = std::nextafter(std::ldexp(1.0f, -30 + i % 60), 0.0f);
+    else if (i < 420) x = std::ldexp(1.0f, -140 + i % 20);              // subnormal
+    else x = float(std::exp(40.0 * u(g))) * (i & 1 ? -1.0f : 1.0f);
+    const Pow2<float> p = pow2_scale(x);
+    std::printf("P %a %a %a\n", double(x), double(p.s), double(p.is));
+  }
+  return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def lines(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("gridsum")
+    src = d / "gs.cpp"
+    src.write_text(PROG)
+    exe = d / "gs"
+    subprocess.run([cxx, "-std=c++17", "-O2", "-ffp-contract=off", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    return subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+
+
+def is_pow2(v):
+    m, _ = math.frexp(v)
+    return v > 0 and m == 0.5
+
+
+def test_slot_grids_bound_their_terms(lines):
+    """every slot's grid g is a power of two with g >= max(n, 2) m and g < 2 max(n, 2) m (1 +
+    2^-7), where n counts the non-zero rows and m is the largest |coefficient| times its input
+    bound (1 for Delta J_q, q for Delta rho^q)"""
+    rows = [l.split() for l in lines if l.startswith("G ")]
+    assert len(rows) == 4 * 12
+    for r in rows:
+        g, drho = float.fromhex(r[3]), r[4] == "1"
+        terms = [t.split(":") for t in r[5:]]
+        if not terms:
+            continue
+        n = len(terms)
+        m = 0.0
+        for q, num, den in terms:
+            q = int(q)
+            w = abs(float.fromhex(num)) / float.fromhex(den) * (q if drho and q > 1 else 1)
+            m = max(m, w)
+        need = max(n, 2) * m
+        assert is_pow2(g), r
+        assert g >= need, r
+        assert g < 2 * need * (1 + 2 ** -7), r
+        if drho:
+            assert all(int(q) >= 1 for q, _, _ in terms), r     # Delta rho^q rows start at q = 1
+
+
+def test_row_minus_one_only_with_a_linear_term(lines):
+    """the q = -1 row (Delta J_-1, the unbounded log term) is used only by the cubic spline,
+    whose (1 - q)^3 has a linear term; Wendland kernels have b_1 = 0"""
+    flags = dict((l.split()[1], l.split()[2]) for l in lines if l.startswith("M "))
+    assert flags == {"wc2": "0", "wc4": "0", "wc6": "0", "cube": "1"}
+
+
+def test_extracted_sum_error_bound(lines):
+    """s + c against the exact rational sum of (x.hi + x.lo)(k.hi + k.lo): within
+    4 n^2 u^2 g absolute (u = 2^-24), far below the u g that a rounded running sum would show;
+    s itself is a multiple of u g with |s| <= g"""
+    rows = [l for l in lines if l.startswith("S ")]
+    assert len(rows) == 400
+    u = Fraction(1, 2 ** 24)
+    worst = 0.0
+    for l in rows:
+        head, tail = l[2:].split(" | ")
+        parts = head.split()
+        n, g = int(parts[0]), Fraction(float.fromhex(parts[1]))
+        exact = Fraction(0)
+        for t in parts[2:]:
+            xh, xl, kh, kl = (Fraction(float.fromhex(v)) for v in t.split(","))
+            exact += (xh + xl) * (kh + kl)
+        s, c = (Fraction(float.fromhex(v)) for v in tail.split())
+        assert abs(s) <= g
+        assert (s / (u * g)).denominator == 1
+        err = abs(s + c - exact)
+        bound = 4 * n * n * u * u * g
+        assert err <= bound, (l, float(err), float(bound))
+        worst = max(worst, float(err / (u * u * g)))
+    assert worst > 0.0                                          # the check can see an error
+
+
+def test_pow2_scale(lines):
+    rows = [l.split() for l in lines if l.startswith("P ")]
+    assert len(rows) == 2000
+    for _, x, s, i in rows:
+        x, s, i = float.fromhex(x), float.fromhex(s), float.fromhex(i)
+        assert is_pow2(s) and is_pow2(i) and s * i == 1.0
+        assert s <= 2.0 ** 64
+        if s < 2.0 ** 64:
+            assert 0.5 <= abs(x) * s < 1.0, (x, s)
+        else:
+            assert abs(x) * s < 1.0, (x, s)
