@@ -121,8 +121,11 @@ template <> struct Acc<Counted<double>> {
   using Sum = R;
   static constexpr bool SCALED = false;
   static R zero() { return R(0.0); }
+  static R zero_g(float) { return R(0.0); }
+  static R result_g(R a, float) { return a; }
+  static R resultA_g(R a, float) { return a; }
   template <class P>
-  static R madd(R acc, R x, int row, int slot, float) {
+  static R madd(R acc, R x, int row, int slot) {
     const NumDen c = edge_coef<P>(row - 1, slot);
     const double k = c.num / c.den;
     if (k == 0.0) return acc;
@@ -149,8 +152,11 @@ template <> struct Acc<Counted<long double>> {
   using Sum = R;
   static constexpr bool SCALED = false;
   static R zero() { return R(0.0); }
+  static R zero_g(float) { return R(0.0); }
+  static R result_g(R a, float) { return a; }
+  static R resultA_g(R a, float) { return a; }
   template <class P>
-  static R madd(R acc, R x, int row, int slot, float) {
+  static R madd(R acc, R x, int row, int slot) {
     const NumDen c = edge_coef<P>(row - 1, slot);
     const double k = c.num / c.den;
     if (k == 0.0) return acc;

@@ -603,25 +603,29 @@ SPH2D_HD CSum<F> csum_madd(CSum<F> a, FFT<F> x, F khi, F klo) {
 }
 
 // The same sum by error-free extraction against a fixed grid (Rump, Ogita and Oishi, "Accurate
-// floating-point summation, part I", SIAM J. Sci. Comput. 31, 2008), for terms bounded in
-// advance.  g is a power of two and every product |x k| <= g / n for the n terms of the sum
-// (n >= 2).  Then t = fl(x.hi khi + g) lies in [g/2, 2g], q = t - g is exact (Sterbenz) and a
-// multiple of ulp(g)/2, and s, a sum of such q with sum |q| < g, is exact; r = fl(x.hi khi - q)
-// is the remainder, below ulp(g) in size, with one rounding.  c collects the remainders, the
-// low word of x and the coefficient's low part.  Six or seven instructions against the twelve
-// of csum_madd; the error is O(n u^2 g) absolute, u = 2^-24, against O(u^2 sum|x k|) there.
+// floating-point summation, part I", SIAM J. Sci. Comput. 31, 2008; the running-sigma form of
+// their FastAccSum), for terms bounded in advance.  g is a power of two with |x k| <= g / (2n)
+// for all n terms of the sum, and s starts at 3g/2 (xsum_init).  Every t = fl(s + x.hi khi)
+// then stays in (g, 2g), on the grid ulp = 2^-23 g, so q = t - s is exact (Sterbenz) and s - 3g/2
+// is the exact sum of the q; r = fl(x.hi khi - q) is the remainder, |r| <= 2^-24 g, with one
+// rounding.  c collects the remainders, the low word of x and the coefficient's low part.  Five
+// or six instructions against the twelve of csum_madd; the error is O(n u^2 g) absolute,
+// u = 2^-24, against O(u^2 sum|x k|) there.
 template <typename F>
-SPH2D_HD CSum<F> xsum_madd(CSum<F> a, FFT<F> x, F khi, F klo, F g) {
-  const F t = fma_f(x.hi, khi, g);
-  const F q = t - g;
-  F r = fma_f(x.hi, khi, -q);
+SPH2D_HD CSum<F> xsum_init(float g) { return CSum<F>{F(1.5f * g), F(0)}; }
+template <typename F>
+SPH2D_HD CSum<F> xsum_madd(CSum<F> a, FFT<F> x, F khi, F klo) {
+  const F t = fma_f(x.hi, khi, a.s);
+  F r = fma_f(x.hi, khi, a.s - t);
   r = fma_f(x.lo, khi, r);
   if (klo != F(0)) r = fma_f(x.hi, klo, r);
-  return CSum<F>{a.s + q, a.c + r};
+  return CSum<F>{t, a.c + r};
 }
-// the grid constant g of one edge-sum slot: the smallest power of two with g >= n m (1 + 2^-7),
-// n >= 2 the number of non-zero terms and m the largest |coefficient| times the bound of its
-// input.  The inputs are scaled per fan (add_fan) so that |Delta J_q| < 1 for q >= 0 (and
+// the sum as s + c, with s exact
+template <typename F>
+SPH2D_HD FFT<F> xsum_result(CSum<F> a, float g) { return ff_two_sum(a.s - F(1.5f * g), a.c); }
+// the grid constant g of one edge-sum slot: the smallest power of two with g >= 2 n m (1 + 2^-7),
+// n the number of non-zero terms and m the largest |coefficient| times the bound of its input.  The inputs are scaled per fan (add_fan) so that |Delta J_q| < 1 for q >= 0 (and
 // q = -1, where the row is used: J_q = int rho^q dt with rho <= 1 on the edge piece, so
 // |Delta J_q| <= |Delta t|) and |Delta rho^q| < q (|d rho / dt| <= 1).
 template <class P>
@@ -635,7 +639,8 @@ SPH2D_HD constexpr float slot_grid(int s) {
     m = w > m ? w : m;
     ++n;
   }
-  const double need = (n < 2 ? 2 : n) * m * (1.0 + 1.0 / 128);
+  if (n == 0) return 1.0f;
+  const double need = 2.0 * n * m * (1.0 + 1.0 / 128);
   double g = 1.0;
   while (g < need) g *= 2.0;
   while (g * 0.5 >= need) g *= 0.5;
@@ -665,8 +670,11 @@ struct AccPlain {
   using Sum = F;
   static constexpr bool SCALED = false;                // edge sums on unscaled inputs
   SPH2D_HD static F zero() { return F(0); }
+  SPH2D_HD static F zero_g(float) { return F(0); }     // slot sums (g: the slot's grid)
+  SPH2D_HD static F result_g(F acc, float) { return acc; }
+  SPH2D_HD static F resultA_g(F acc, float) { return acc; }
   template <class P>
-  SPH2D_HD static F madd(F acc, F x, int row, int slot, float) {
+  SPH2D_HD static F madd(F acc, F x, int row, int slot) {
 #if SPH2D_Q_UNROLL
     const NumDen c = edge_coef<P>(row - 1, slot);
     const F k = F(c.num / c.den);
@@ -729,17 +737,20 @@ struct AccFF {
     return FFT<F>{t.hi, t.lo + (a.lo + b.lo)};
   }
   SPH2D_HD static CSum<F> zero() { return CSum<F>{F(0), F(0)}; }
+  SPH2D_HD static CSum<F> zero_g(float g) { return xsum_init<F>(g); }
+  SPH2D_HD static F result_g(CSum<F> a, float g) { return (a.s - F(1.5f * g)) + a.c; }
+  SPH2D_HD static FFT<F> resultA_g(CSum<F> a, float g) { return xsum_result(a, g); }
   template <class P>
-  SPH2D_HD static CSum<F> madd(CSum<F> acc, FFT<F> x, int row, int slot, float grid) {
+  SPH2D_HD static CSum<F> madd(CSum<F> acc, FFT<F> x, int row, int slot) {
 #if SPH2D_Q_UNROLL
     const NumDen c = edge_coef_y<P>(row - 1, slot);
     if (c.num == 0.0) return acc;
     const FF k = ff_const(c.num / c.den);
-    return xsum_madd(acc, x, F(k.hi), F(k.lo), F(grid));
+    return xsum_madd(acc, x, F(k.hi), F(k.lo));
 #else
     const EdgeRows<P>& r = edge_rows<P>();
     if (r.fhi[row][slot] == 0.0f) return acc;        // uniform across the warp
-    return xsum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]), F(grid));
+    return xsum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]));
 #endif
   }
   SPH2D_HD static CSum<F> maddc(CSum<F> acc, FFT<F> x, double num, double den) {
@@ -790,8 +801,11 @@ struct AccDD {
   using Sum = CSum<D>;
   static constexpr bool SCALED = false;
   SPH2D_HD static CSum<D> zero() { return CSum<D>{D(0), D(0)}; }
+  SPH2D_HD static CSum<D> zero_g(float) { return zero(); }
+  SPH2D_HD static D result_g(CSum<D> a, float) { return result(a); }
+  SPH2D_HD static FFT<D> resultA_g(CSum<D> a, float) { return resultA(a); }
   template <class P>
-  SPH2D_HD static CSum<D> madd(CSum<D> acc, FFT<D> x, int row, int slot, float) {
+  SPH2D_HD static CSum<D> madd(CSum<D> acc, FFT<D> x, int row, int slot) {
 #if SPH2D_Q_UNROLL
     const NumDen c = edge_coef<P>(row - 1, slot);
     if (c.num == 0.0) return acc;
@@ -909,27 +923,32 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
     // running sums without their d^(j+1) factors
     using SM = typename AC::Sum;
-    SM Sg = AC::zero(), Sn = AC::zero(), St = AC::zero();
-    SM S10 = AC::zero(), S01 = AC::zero(), S20 = AC::zero(), S11 = AC::zero(), S02 = AC::zero();
-    SM S30 = AC::zero(), S21 = AC::zero(), S12 = AC::zero(), S03 = AC::zero();
+    constexpr float gG = slot_grid<P>(SL_G), gN = slot_grid<P>(SL_N), gT = slot_grid<P>(SL_T);
+    constexpr float g10 = slot_grid<P>(SL_10), g01 = slot_grid<P>(SL_01), g20 = slot_grid<P>(SL_20);
+    constexpr float g11 = slot_grid<P>(SL_11), g02 = slot_grid<P>(SL_02A), g30 = slot_grid<P>(SL_30);
+    constexpr float g21 = slot_grid<P>(SL_21), g12 = slot_grid<P>(SL_12A), g03 = slot_grid<P>(SL_03A);
+    SM Sg = AC::zero_g(gG), Sn = AC::zero_g(gN), St = AC::zero_g(gT);
+    SM S10 = AC::zero_g(g10), S01 = AC::zero_g(g01), S20 = AC::zero_g(g20), S11 = AC::zero_g(g11);
+    SM S02 = AC::zero_g(g02), S30 = AC::zero_g(g30), S21 = AC::zero_g(g21), S12 = AC::zero_g(g12);
+    SM S03 = AC::zero_g(g03);
     const A zeroA = AC::c(0);
     // one step of the sums: q's row, Delta J_q and Delta rho^q
     auto step = [&](int row, const A& dJ, const A& dP) {
-      Sg = AC::template madd<P>(Sg, dJ, row, SL_G, slot_grid<P>(SL_G));
-      Sn = AC::template madd<P>(Sn, dJ, row, SL_N, slot_grid<P>(SL_N));
-      St = AC::template madd<P>(St, dP, row, SL_T, slot_grid<P>(SL_T));
+      Sg = AC::template madd<P>(Sg, dJ, row, SL_G);
+      Sn = AC::template madd<P>(Sn, dJ, row, SL_N);
+      St = AC::template madd<P>(St, dP, row, SL_T);
       if (MD >= 1) {
-        S10 = AC::template madd<P>(S10, dJ, row, SL_10, slot_grid<P>(SL_10));
-        S01 = AC::template madd<P>(S01, dP, row, SL_01, slot_grid<P>(SL_01));
+        S10 = AC::template madd<P>(S10, dJ, row, SL_10);
+        S01 = AC::template madd<P>(S01, dP, row, SL_01);
       }
       if (MD >= 3) {
-        S20 = AC::template madd<P>(S20, dJ, row, SL_20, slot_grid<P>(SL_20));
-        S30 = AC::template madd<P>(S30, dJ, row, SL_30, slot_grid<P>(SL_30));
-        S02 = AC::template madd<P>(S02, dJ, row, SL_02A, slot_grid<P>(SL_02A));
-        S12 = AC::template madd<P>(S12, dJ, row, SL_12A, slot_grid<P>(SL_12A));
-        S11 = AC::template madd<P>(S11, dP, row, SL_11, slot_grid<P>(SL_11));
-        S21 = AC::template madd<P>(S21, dP, row, SL_21, slot_grid<P>(SL_21));
-        S03 = AC::template madd<P>(S03, dP, row, SL_03A, slot_grid<P>(SL_03A));
+        S20 = AC::template madd<P>(S20, dJ, row, SL_20);
+        S30 = AC::template madd<P>(S30, dJ, row, SL_30);
+        S02 = AC::template madd<P>(S02, dJ, row, SL_02A);
+        S12 = AC::template madd<P>(S12, dJ, row, SL_12A);
+        S11 = AC::template madd<P>(S11, dP, row, SL_11);
+        S21 = AC::template madd<P>(S21, dP, row, SL_21);
+        S03 = AC::template madd<P>(S03, dP, row, SL_03A);
       }
     };
     A dJm = AC::jm1(t1, t2, r1, r2, d, r1a, r2a);            // Delta J_{-1}
@@ -973,23 +992,23 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
       dJq1 = dJ;
     }
     const R d2s = AC::SCALED ? d * ds : d2;                 // d^2 / s
-    eg += ds * AC::result(Sg);
-    en += d2s * AC::result(Sn);
-    et += ds * AC::result(St);
+    eg += ds * AC::result_g(Sg, gG);
+    en += d2s * AC::result_g(Sn, gN);
+    et += ds * AC::result_g(St, gT);
     if (MD >= 1) {
-      E[1] += d2s * AC::result(S10);
-      E[2] += ds * AC::result(S01);
+      E[1] += d2s * AC::result_g(S10, g10);
+      E[2] += ds * AC::result_g(S01, g01);
     }
     if (MD >= 3) {
       const R d3s = d2s * d, d4s = d2s * d2;
-      const A s20 = AC::resultA(S20), s30 = AC::resultA(S30), s21 = AC::resultA(S21);
+      const A s20 = AC::resultA_g(S20, g20), s30 = AC::resultA_g(S30, g30), s21 = AC::resultA_g(S21, g21);
       E[3] += d3s * AC::out(s20);
-      E[4] += d2s * AC::result(S11);
-      E[5] += ds * AC::out(AC::resultA(S02) - s20 * d2a);
+      E[4] += d2s * AC::result_g(S11, g11);
+      E[5] += ds * AC::out(AC::resultA_g(S02, g02) - s20 * d2a);
       E[6] += d4s * AC::out(s30);
       E[7] += d3s * AC::out(s21);
-      E[8] += d2s * AC::out(AC::resultA(S12) - s30 * d2a);
-      E[9] += ds * AC::out(AC::resultA(S03) - s21 * d2a);
+      E[8] += d2s * AC::out(AC::resultA_g(S12, g12) - s30 * d2a);
+      E[9] += ds * AC::out(AC::resultA_g(S03, g03) - s21 * d2a);
     }
   }
   // rotate the gradient back from the edge frame (Sec. 2, Eq. improper)

@@ -42,21 +42,22 @@ int main() {
   grids<PolyCube>("cube");
   std::mt19937_64 g(11);
   std::uniform_real_distribution<double> u(-1, 1);
-  // sums of n products with |x k| <= grid / n, alternating signs so that the exact sum cancels
+  // sums of n products with |x k| <= grid / (2n), alternating signs so that the exact sum cancels
   for (int trial = 0; trial < 400; ++trial) {
     const int n = 2 + trial % 15;
     const float grid = std::ldexp(1.0f, -20 + int(trial % 41));
-    CSum<float> acc{0.0f, 0.0f};
+    CSum<float> acc = xsum_init<float>(grid);
     std::printf("S %d %a", n, double(grid));
     for (int i = 0; i < n; ++i) {
       const double kv = (1.0 + 3.0 * std::fabs(u(g))) * ((i & 1) ? -1 : 1);
       const FF k = ff_const(trial % 3 == 0 ? double(float(kv)) : kv);
-      const double xv = u(g) * double(grid) / (n * 4.0);
+      const double xv = u(g) * double(grid) / (n * 8.0);
       const float xh = float(xv), xl = float(xv - double(xh));
-      acc = xsum_madd(acc, FF{xh, xl}, k.hi, k.lo, grid);
+      acc = xsum_madd(acc, FF{xh, xl}, k.hi, k.lo);
       std::printf(" %a,%a,%a,%a", double(xh), double(xl), double(k.hi), double(k.lo));
     }
-    std::printf(" | %a %a\n", double(acc.s), double(acc.c));
+    const FF r = xsum_result(acc, grid);
+    std::printf(" | %a %a %a %a\n", double(acc.s - 1.5f * grid), double(acc.c), double(r.hi), double(r.lo));
   }
   // the scale: 2^-e with |x| in [2^(e-1), 2^e)
   for (int i = 0; i < 2000; ++i) {
@@ -92,9 +93,9 @@ def is_pow2(v):
 
 
 def test_slot_grids_bound_their_terms(lines):
-    """every slot's grid g is a power of two with g >= max(n, 2) m and g < 2 max(n, 2) m (1 +
-    2^-7), where n counts the non-zero rows and m is the largest |coefficient| times its input
-    bound (1 for Delta J_q, q for Delta rho^q)"""
+    """every slot's grid g is a power of two with g >= 2 n m and g < 4 n m (1 + 2^-7), where n
+    counts the non-zero rows and m is the largest |coefficient| times its input bound (1 for
+    Delta J_q, q for Delta rho^q)"""
     rows = [l.split() for l in lines if l.startswith("G ")]
     assert len(rows) == 4 * 12
     for r in rows:
@@ -108,7 +109,7 @@ def test_slot_grids_bound_their_terms(lines):
             q = int(q)
             w = abs(float.fromhex(num)) / float.fromhex(den) * (q if drho and q > 1 else 1)
             m = max(m, w)
-        need = max(n, 2) * m
+        need = 2 * n * m
         assert is_pow2(g), r
         assert g >= need, r
         assert g < 2 * need * (1 + 2 ** -7), r
@@ -124,9 +125,10 @@ def test_row_minus_one_only_with_a_linear_term(lines):
 
 
 def test_extracted_sum_error_bound(lines):
-    """s + c against the exact rational sum of (x.hi + x.lo)(k.hi + k.lo): within
-    4 n^2 u^2 g absolute (u = 2^-24), far below the u g that a rounded running sum would show;
-    s itself is a multiple of u g with |s| <= g"""
+    """the running-sigma sum, started at 3g/2: s - 3g/2 (exact) plus c against the exact rational
+    sum of (x.hi + x.lo)(k.hi + k.lo), within 4 n^2 u^2 g absolute (u = 2^-24), far below the
+    u g that a rounded running sum would show; s - 3g/2 is a multiple of 2 u g with
+    |s - 3g/2| <= g/2, and the returned pair is s - 3g/2 + c to one rounding"""
     rows = [l for l in lines if l.startswith("S ")]
     assert len(rows) == 400
     u = Fraction(1, 2 ** 24)
@@ -139,9 +141,10 @@ def test_extracted_sum_error_bound(lines):
         for t in parts[2:]:
             xh, xl, kh, kl = (Fraction(float.fromhex(v)) for v in t.split(","))
             exact += (xh + xl) * (kh + kl)
-        s, c = (Fraction(float.fromhex(v)) for v in tail.split())
-        assert abs(s) <= g
-        assert (s / (u * g)).denominator == 1
+        s, c, rh, rl = (Fraction(float.fromhex(v)) for v in tail.split())
+        assert abs(s) <= g / 2
+        assert (s / (2 * u * g)).denominator == 1
+        assert rh + rl == s + c or abs(rh + rl - (s + c)) <= u * u * abs(s + c)
         err = abs(s + c - exact)
         bound = 4 * n * n * u * u * g
         assert err <= bound, (l, float(err), float(bound))
