@@ -116,7 +116,6 @@ template <> struct Acc<Counted<double>> {
   static R root(R v) { return sqrt(v); }
   static R out(R v) { return v; }
   static R mulr(R a, R b) { return a * b; }
-  static R sub_raw(R a, R b) { return a - b; }
   static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
   using Sum = R;
   static constexpr bool SCALED = false;
@@ -147,7 +146,6 @@ template <> struct Acc<Counted<long double>> {
   static R root(R v) { return sqrt(v); }
   static R out(R v) { return v; }
   static R mulr(R a, R b) { return a * b; }
-  static R sub_raw(R a, R b) { return a - b; }
   static R jm1(R t1, R t2, R r1, R r2, R d, R, R) { return asinh_diff(t1, t2, r1, r2, d); }
   using Sum = R;
   static constexpr bool SCALED = false;

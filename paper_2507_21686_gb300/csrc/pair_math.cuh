@@ -258,13 +258,6 @@ template <typename F>
 SPH2D_HD FFT<F> operator-(FFT<F> a) { return FFT<F>{-a.hi, -a.lo}; }
 template <typename F>
 SPH2D_HD FFT<F> operator-(FFT<F> a, FFT<F> b) { return a + (-b); }
-// a - b with the two words left unrenormalised (the low word may exceed half an ulp of the
-// high one): for values that go only into the grid sums or into a renormalising addition
-template <typename F>
-SPH2D_HD FFT<F> ff_sub_raw(FFT<F> a, FFT<F> b) {
-  const FFT<F> s = ff_two_sum(a.hi, -b.hi);
-  return FFT<F>{s.hi, s.lo + (a.lo - b.lo)};
-}
 // Products return their two words without the final renormalisation unless
 // SPH2D_FF_NORM_PRODUCTS is set: every product here feeds an addition, which renormalises, or
 // another product, and the low word then stays within a few units of the high word's last
@@ -302,6 +295,28 @@ SPH2D_HD FFT<F> ff_sqrt(FFT<F> x) {               // one Newton step on sqrt(hi)
 }
 template <typename F>
 SPH2D_HD F to_f(FFT<F> a) { return a.hi + a.lo; }
+
+// Two values of the same operation side by side.  For float on sm_100-family GPUs each
+// operation is one packed instruction (fma/mul .rn.f32x2: the same FP32 lanes, half the issue
+// slots); elsewhere it is two scalar operations.
+template <typename F>
+struct V2 {
+  F x, y;
+};
+template <typename F>
+SPH2D_HD V2<F> v2_fma(V2<F> a, V2<F> b, V2<F> c) { return V2<F>{fma_f(a.x, b.x, c.x), fma_f(a.y, b.y, c.y)}; }
+template <typename F>
+SPH2D_HD V2<F> v2_mul(V2<F> a, V2<F> b) { return V2<F>{a.x * b.x, a.y * b.y}; }
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+SPH2D_HD V2<float> v2_fma(V2<float> a, V2<float> b, V2<float> c) {
+  const float2 r = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y));
+  return V2<float>{r.x, r.y};
+}
+SPH2D_HD V2<float> v2_mul(V2<float> a, V2<float> b) {
+  const float2 r = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  return V2<float>{r.x, r.y};
+}
+#endif
 template <typename F>
 SPH2D_HD FFT<F> operator/(FFT<F> a, FFT<F> b) {   // long division, two quotient digits
   const F q1 = a.hi / b.hi;
@@ -666,7 +681,6 @@ struct AccPlain {
   SPH2D_HD static F root(F v) { return sqrt(v); }
   SPH2D_HD static F out(F v) { return v; }
   SPH2D_HD static F mulr(F a, F b) { return a * b; }
-  SPH2D_HD static F sub_raw(F a, F b) { return a - b; }
   using Sum = F;
   static constexpr bool SCALED = false;                // edge sums on unscaled inputs
   SPH2D_HD static F zero() { return F(0); }
@@ -724,7 +738,6 @@ struct AccFF {
     return pow2_scale(b);
   }
   SPH2D_HD static FFT<F> pscale(FFT<F> x, F s) { return FFT<F>{x.hi * s, x.lo * s}; }
-  SPH2D_HD static FFT<F> sub_raw(FFT<F> a, FFT<F> b) { return ff_sub_raw(a, b); }
   // Y_q = Delta(t rho^q) (q-1)!!/q!! + d^2 Y_{q-2} (edge_coef_y); both terms have the sign of
   // Delta t, so the sum is left unrenormalised
   SPH2D_HD static FFT<F> ystep(int q, FFT<F> dT, FFT<F> y2, FFT<F> d2a) {
@@ -793,7 +806,6 @@ struct AccDD {
   SPH2D_HD static FFT<D> root(FFT<D> v) { return ff_sqrt(v); }
   SPH2D_HD static D out(FFT<D> v) { return to_f(v); }
   SPH2D_HD static FFT<D> mulr(FFT<D> a, D b) { return a * b; }
-  SPH2D_HD static FFT<D> sub_raw(FFT<D> a, FFT<D> b) { return a - b; }
   SPH2D_HD static FFT<D> jm1(D t1, D t2, D r1, D r2, D d, FFT<D> ra, FFT<D> rb) {
     (void)r1; (void)r2;
     return asinh_diff_ff<D, double>(t1, t2, ra, rb, d);
@@ -970,26 +982,50 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
     A dJq2 = dJm, dJq1 = dJp;                               // Delta J_{q-2}, Delta J_{q-1}
     // highest row any requested sum uses: gamma/gradient K, first moments K + 2, all K + 4
     constexpr int QMAX = MD >= 3 ? P::K + 4 : (MD >= 1 ? P::K + 2 : P::K);
+    if constexpr (AC::SCALED) {
+      // both ends' rho^q (times s) as packed pairs with negated low words: P_q = P_{q-1} R and
+      // P_q t in float-pair arithmetic, one packed instruction per step for both ends
+      using V = V2<R>;
+      V phi{p1.hi, p2.hi}, pnl{R(0), R(0)};
+      const V rhi{r1a.hi, r2a.hi}, nrhi{-r1a.hi, -r2a.hi}, nrlo{-r1a.lo, -r2a.lo};
+      const V tt{t1, t2}, nt{-t1, -t2};
 #if SPH2D_Q_UNROLL
 #pragma unroll
 #else
 #pragma unroll 1
 #endif
-    for (int q = 1; q <= QMAX; ++q) {
-      p1 = p1 * r1a;
-      p2 = p2 * r2a;
-      const A dP = AC::sub_raw(p2, p1);                     // Delta rho^q (only summed)
-      const A dT = AC::sub_raw(AC::mulr(p2, t2), AC::mulr(p1, t1));   // Delta (t rho^q)
-      A dJ;                                                 // Delta J_q (FP32 path: Delta Y_q)
-      if constexpr (AC::SCALED) {
-        dJ = AC::ystep(q, dT, dJq2, d2a);
-      } else {
-        const R qf = R(q), iq = R(1) / R(q + 1);
-        dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);
+      for (int q = 1; q <= QMAX; ++q) {
+        const V ph = v2_mul(phi, rhi);
+        pnl = v2_fma(pnl, rhi, v2_fma(phi, nrlo, v2_fma(phi, nrhi, ph)));   // -(lo of P R)
+        phi = ph;
+        const V th = v2_mul(phi, tt);
+        const V tnl = v2_fma(pnl, tt, v2_fma(phi, nt, th));                 // -(lo of P t)
+        // differences end 2 - end 1, left unrenormalised (they feed only sums and ystep)
+        const FFT<R> sp = ff_two_sum(phi.y, -phi.x), st = ff_two_sum(th.y, -th.x);
+        const A dP{sp.hi, sp.lo + (pnl.x - pnl.y)};                        // Delta rho^q
+        const A dT{st.hi, st.lo + (tnl.x - tnl.y)};                        // Delta (t rho^q)
+        const A dJ = AC::ystep(q, dT, dJq2, d2a);                           // Delta Y_q
+        step(q + 1, dJ, dP);
+        dJq2 = dJq1;
+        dJq1 = dJ;
       }
-      step(q + 1, dJ, dP);
-      dJq2 = dJq1;
-      dJq1 = dJ;
+    } else {
+#if SPH2D_Q_UNROLL
+#pragma unroll
+#else
+#pragma unroll 1
+#endif
+      for (int q = 1; q <= QMAX; ++q) {
+        p1 = p1 * r1a;
+        p2 = p2 * r2a;
+        const A dP = p2 - p1;                               // Delta rho^q
+        const A dT = AC::mulr(p2, t2) - AC::mulr(p1, t1);   // Delta (t rho^q)
+        const R qf = R(q), iq = R(1) / R(q + 1);
+        const A dJ = AC::divq(dT + AC::mulr(dJq2 * d2a, qf), q, iq);   // Delta J_q
+        step(q + 1, dJ, dP);
+        dJq2 = dJq1;
+        dJq1 = dJ;
+      }
     }
     const R d2s = AC::SCALED ? d * ds : d2;                 // d^2 / s
     eg += ds * AC::result_g(Sg, gG);
