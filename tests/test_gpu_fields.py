@@ -112,7 +112,9 @@ def test_field_options_and_errors(ctx):
         v, g = ctx.field_integrals(_t(np.ascontiguousarray(vv[:, :, :nf])), "cubic_spline", "fp32_fixup")
         assert torch.equal(v, v4[:, :nf]) and torch.equal(g, g4[:, :nf])
     v0, g0 = ctx.field_integrals(_t(vv), "cubic_spline", "fp32_fixup", want_grad=False)
-    assert g0 is None and torch.equal(v0, v4)
+    # the same values from the kernel instantiation without the gradient, to a few ulps: the
+    # two instantiations are compiled separately and may contract different multiply-adds
+    assert g0 is None and float((v0 - v4).abs().max()) <= 1e-6 * float(v4.abs().max())
     v2, g2 = ctx.field_integrals(_t(vv), "cubic_spline", "fp32_fixup")
     assert torch.equal(v2, v4) and torch.equal(g2, g4)          # deterministic
     bad = np.zeros((len(tris), 3, 5), dtype=np.float32)
