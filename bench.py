@@ -772,6 +772,25 @@ def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3
     torch.cuda.synchronize()
     train_s = time.time() - t0
     del tpd
+    # A/B of the training step's GEMM engine: one forward + backward (11 GEMMs and the
+    # elementwise kernels) at the training batch, CUDA events, with the trained parameters
+    gab = {"batch": batch}
+    xb = torch.rand(batch, 6, device=dev) * 2 - 1
+    tb = torch.rand(batch, 3, device=dev)
+    for eng in ("mma_sync", "tcgen05"):
+        ctx.set_surrogate_train_engine(eng)
+        for _ in range(5):
+            ctx.surrogate_grad(xb, tb)
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(50):
+            ctx.surrogate_grad(xb, tb)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        gab[f"{eng}_ms_per_step"] = a_.elapsed_time(b_) / 50
+    ctx.set_surrogate_train_engine("mma_sync")
+    gab["note"] = ("training GEMMs on mma.sync (64 x 64 tiles) against tcgen05 (128 x 64 tiles, TMEM "
+                   "accumulators); training runs on mma.sync")
     w = W.surrogate_box(n=n, obstacle_cells=(660 * n) // 2048)
     parts = torch.from_numpy(w.particles).to(dev)
     tris = torch.from_numpy(w.triangles).to(dev)
@@ -825,6 +844,7 @@ def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3
             "train": {"pairs": len(tp), "in_domain": used, "epochs": epochs, "batch": batch, "lr": lr,
                       "steps": epochs * (used // batch), "seconds": train_s, "final_batch_loss": loss,
                       "data_generation_s_host": gen_s},
+            "train_step_gemm_engines": gab,
             "speedup_vs_fp32_fixup": res["fp32_fixup"]["ms"] / res["surrogate"]["ms"],
             "speedup_vs_fp64": res["fp64"]["ms"] / res["surrogate"]["ms"], **res}
 

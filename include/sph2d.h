@@ -449,6 +449,16 @@ sph2d_status sph2d_surrogate_set_audit(sph2d_ctx* ctx, int period, double tol);
  */
 sph2d_status sph2d_surrogate_set_engine(sph2d_ctx* ctx, int engine);
 
+/*
+ * Tensor-core engine of the training GEMMs (sph2d_surrogate_train, sph2d_surrogate_grad):
+ * 0 (default) mma.sync m16n8k16 in 64 x 64 block tiles; 1 tcgen05 in 128 x 64 tiles with the
+ * FP32 accumulators in tensor memory.  Both round the same FP32 operands to FP16 (forward) or
+ * BF16 (backward) and accumulate in FP32, with the same split of long K sums; results agree to
+ * FP32 accumulation order.  With engine 1, sph2d_surrogate_train returns CUDA if an MMA
+ * completion wait ran out of its poll budget.  Errors: INVALID_ARG.
+ */
+sph2d_status sph2d_surrogate_set_train_engine(sph2d_ctx* ctx, int engine);
+
 /* Copy the FP32 parameters to / from host memory (n = SPH2D_SURROGATE_PARAMS).  get returns
  * CAPACITY if cap is smaller.  Synchronise.  Errors: NOT_BUILT, INVALID_ARG, CAPACITY, CUDA. */
 sph2d_status sph2d_surrogate_get_params(sph2d_ctx* ctx, float* host, int64_t cap);

@@ -72,6 +72,7 @@ SIGNATURES = {
     "sph2d_surrogate_set_params": (_ST, [_P, _P, _I64]),
     "sph2d_surrogate_set_audit": (_ST, [_P, _I, _D]),
     "sph2d_surrogate_set_engine": (_ST, [_P, _I]),
+    "sph2d_surrogate_set_train_engine": (_ST, [_P, _I]),
     "sph2d_measure_fma_peak": (_ST, [_I, _I, _D, ctypes.POINTER(ctypes.c_double)]),
     "sph2d_surrogate_save": (_ST, [_P, ctypes.c_char_p]),
     "sph2d_surrogate_load": (_ST, [_P, ctypes.c_char_p]),

@@ -304,6 +304,12 @@ class Context:
         check(self.lib, self.h, self.lib.sph2d_surrogate_set_engine(self.h, {"mma_sync": 0, "tcgen05": 1}[engine]))
         return self
 
+    def set_surrogate_train_engine(self, engine: str = "mma_sync"):
+        """Tensor-core engine of the training GEMMs: "mma_sync" or "tcgen05"."""
+        check(self.lib, self.h,
+              self.lib.sph2d_surrogate_set_train_engine(self.h, {"mma_sync": 0, "tcgen05": 1}[engine]))
+        return self
+
     def set_surrogate_params(self, p):
         q = torch.as_tensor(p, dtype=torch.float32).contiguous().cpu()
         self._bind_stream()

@@ -1167,9 +1167,95 @@ SPH2D_HD int tri_orientation(R ax, R ay, R bx, R by, R cx, R cy) {
 //   Jo = int k(rho) dt = sum_k b_k Delta J_k,   To = int k(rho) t dt = sum_k b_k Delta rho^{k+2}/(k+2)
 // over t clipped to the support are the same square-root integrals as the forward edge piece.
 // ---------------------------------------------------------------------------------------
+// the grid constant of an extraction sum of n terms each at most m (see slot_grid)
+SPH2D_HD constexpr float grid_for(int n, double m) {
+  if (n == 0) return 1.0f;
+  const double need = 2.0 * n * m * (1.0 + 1.0 / 128);
+  double g = 1.0;
+  while (g < need) g *= 2.0;
+  while (g * 0.5 >= need) g *= 0.5;
+  return float(g);
+}
+// the grid of a sum of c_q x_q, c_q = f * b_{q+sh} * (q + a)^e over q in [q0, q1] with |x_q| < 1
+template <class P>
+SPH2D_HD constexpr float poly_grid(int q0, int q1, int sh = 0, int a = 0, int e = 0) {
+  double m = 0.0;
+  int n = 0;
+  for (int q = q0; q <= q1; ++q) {
+    const int k = q + sh;
+    double b = (k < 0 || k > P::K) ? 0.0 : P::b(k);
+    for (int i = 0; i < e; ++i) b *= double(q + a);
+    b = b < 0 ? -b : b;
+    if (b == 0.0) continue;
+    m = b > m ? b : m;
+    ++n;
+  }
+  return grid_for(n, m);
+}
+
+// The FP32 path's form of edge_line_integrals, built as the forward edge piece: inputs scaled by
+// the power of two s that brings |Delta t| into [1/2, 1), the recurrence on Y_q = J_q / w_q with
+// both ends in packed instructions, and both sums by grid extraction.  The terms are bounded as
+// in the forward sums: |b_q Delta J_q| <= |b_q| |Delta t| and |(b_{q-2} / q) Delta rho^q| <=
+// |b_{q-2}| |Delta t| on an interval inside the support.
+template <typename R, class P>
+SPH2D_HD void edge_line_integrals_ff(R d, R t1, R t2, R& Jo, R& To) {
+  using AC = typename AccSel<R, P>::type;
+  using A = typename AC::T;
+  using V = V2<R>;
+  constexpr float g = poly_grid<P>(0, P::K);             // b_q and (b_{q-2} / q) q alike
+  const A d2a = AC::sq(d);
+  const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
+  const R r1 = sqrt(d * d + t1 * t1), r2 = sqrt(d * d + t2 * t2);
+  const Pow2<R> sc = pow2_scale(t2 - t1);
+  // Delta J_{-1} enters only as d^2 J_{-1}; at d = 0 that product vanishes
+  const A dJm = AC::pscale(d > Tiny<R>::v() ? AC::jm1(t1, t2, r1, r2, d, r1a, r2a) : AC::c(0), sc.s);
+  const A dJp = AC::pscale(AC::from(t2) - AC::from(t1), sc.s);
+  CSum<R> sJ = xsum_init<R>(g), sT = xsum_init<R>(g);
+  {
+    const FF k = ff_const(P::b(0));
+    sJ = xsum_madd(sJ, dJp, R(k.hi), R(k.lo));
+  }
+  V phi{sc.s, sc.s}, pnl{R(0), R(0)};
+  const V rhi{r1a.hi, r2a.hi}, nrhi{-r1a.hi, -r2a.hi}, nrlo{-r1a.lo, -r2a.lo};
+  const V tt{t1, t2}, nt{-t1, -t2};
+  A y2 = dJm, y1 = dJp;                                   // Delta Y_{q-2}, Delta Y_{q-1}
+#pragma unroll
+  for (int q = 1; q <= P::K + 2; ++q) {
+    const V ph = v2_mul(phi, rhi);
+    pnl = v2_fma(pnl, rhi, v2_fma(phi, nrlo, v2_fma(phi, nrhi, ph)));
+    phi = ph;
+    if (q <= P::K) {
+      const V th = v2_mul(phi, tt);
+      const V tnl = v2_fma(pnl, tt, v2_fma(phi, nt, th));
+      const FFT<R> st = ff_two_sum(th.y, -th.x);
+      const A dT{st.hi, st.lo + (tnl.x - tnl.y)};
+      const A y = AC::ystep(q, dT, y2, d2a);
+      if (P::b(q) != 0.0) {
+        const FF k = ff_const(P::b(q) * dfact(q) / dfact(q + 1));    // b_q w_q
+        sJ = xsum_madd(sJ, y, R(k.hi), R(k.lo));
+      }
+      y2 = y1;
+      y1 = y;
+    }
+    if (q >= 2 && P::b(q - 2) != 0.0) {
+      const FFT<R> sp = ff_two_sum(phi.y, -phi.x);
+      const A dP{sp.hi, sp.lo + (pnl.x - pnl.y)};
+      const FF k = ff_const(P::b(q - 2) / double(q));
+      sT = xsum_madd(sT, dP, R(k.hi), R(k.lo));
+    }
+  }
+  Jo = ((sJ.s - R(1.5f * g)) + sJ.c) * sc.is;
+  To = ((sT.s - R(1.5f * g)) + sT.c) * sc.is;
+}
+
 template <typename R, class P>
 SPH2D_HD void edge_line_integrals(R d, R t1, R t2, R& Jo, R& To) {
   using AC = typename AccSel<R, P>::type;
+  if constexpr (AC::SCALED) {
+    edge_line_integrals_ff<R, P>(d, t1, t2, Jo, To);
+    return;
+  }
   using A = typename AC::T;
   using SM = typename AC::Sum;
   SM sJ = AC::zero(), sT = AC::zero();
@@ -1251,9 +1337,78 @@ SPH2D_HD void tri_vertex_grad_poly(const R* v, R* g) {
 // d grad gamma / d nu_j = -(C/H^2) sum_{e ni j} dF_e/dv_j and d grad gamma / d x_i = -sum_j
 // of those (translation invariance); the last equals (C/H^2) oint k'(rho) n (x) p/rho ds.
 // ---------------------------------------------------------------------------------------
+// The FP32 path's form of edge_grad_integrals (scaled inputs, packed ends, Y recurrence, grid
+// extraction).  Inputs scale by the power of two above |Delta t|, or above |Delta J_-1| too when
+// k'(q)/q has a 1/q term (the q = -1 row of S0); bounds as in edge_line_integrals_ff, with
+// |Delta rho^q| <= q |Delta t|.
+template <typename R, class P>
+SPH2D_HD void edge_grad_integrals_ff(R d, R t1, R t2, R& Jo, R& S0, R& S2, R& Dk) {
+  using AC = typename AccSel<R, P>::type;
+  using A = typename AC::T;
+  using V = V2<R>;
+  constexpr bool need_m1 = P::K >= 1 && P::b(1) != 0.0;
+  constexpr float gJ = poly_grid<P>(0, P::K);
+  constexpr float g0 = poly_grid<P>(-1, P::K, 2, 2, 1);   // (q + 2) b_{q+2}; q = -1 gives b_1
+  constexpr float g2 = poly_grid<P>(1, P::K, 0, 0, 1);
+  constexpr float gk = poly_grid<P>(1, P::K, 0, 0, 1);   // b_q Delta rho^q <= |b_q| q |Delta t|
+  const A d2a = AC::sq(d);
+  const A r1a = AC::root(d2a + AC::sq(t1)), r2a = AC::root(d2a + AC::sq(t2));
+  const R r1 = sqrt(d * d + t1 * t1), r2 = sqrt(d * d + t2 * t2);
+  const A dJm0 = (d > Tiny<R>::v() || (need_m1 && t1 * t2 > R(0))) ? AC::jm1(t1, t2, r1, r2, d, r1a, r2a) : AC::c(0);
+  R bnd = fabs(t2 - t1);
+  if constexpr (need_m1) bnd = fmax(bnd, fabs(dJm0.hi) + fabs(dJm0.lo));
+  const Pow2<R> sc = pow2_scale(bnd);
+  const A dJm = AC::pscale(dJm0, sc.s);
+  const A dJp = AC::pscale(AC::from(t2) - AC::from(t1), sc.s);
+  CSum<R> sJ = xsum_init<R>(gJ), s0 = xsum_init<R>(g0), s2 = xsum_init<R>(g2), sk = xsum_init<R>(gk);
+  auto add = [](CSum<R>& acc, const A& x, double c) {
+    if (c == 0.0) return;
+    const FF k = ff_const(c);
+    acc = xsum_madd(acc, x, R(k.hi), R(k.lo));
+  };
+  if (need_m1) add(s0, dJm, P::b(1));
+  add(sJ, dJp, P::b(0));
+  add(s0, dJp, 2.0 * bk<P>(2));
+  V phi{sc.s, sc.s}, pnl{R(0), R(0)};
+  const V rhi{r1a.hi, r2a.hi}, nrhi{-r1a.hi, -r2a.hi}, nrlo{-r1a.lo, -r2a.lo};
+  const V tt{t1, t2}, nt{-t1, -t2};
+  A y2 = dJm, y1 = dJp;
+#pragma unroll
+  for (int q = 1; q <= P::K; ++q) {
+    const V ph = v2_mul(phi, rhi);
+    pnl = v2_fma(pnl, rhi, v2_fma(phi, nrlo, v2_fma(phi, nrhi, ph)));
+    phi = ph;
+    const V th = v2_mul(phi, tt);
+    const V tnl = v2_fma(pnl, tt, v2_fma(phi, nt, th));
+    const FFT<R> st = ff_two_sum(th.y, -th.x), sp = ff_two_sum(phi.y, -phi.x);
+    const A dT{st.hi, st.lo + (tnl.x - tnl.y)};
+    const A dP{sp.hi, sp.lo + (pnl.x - pnl.y)};
+    const A y = AC::ystep(q, dT, y2, d2a);               // Delta Y_q, Delta J_q = w_q Delta Y_q
+    const double w = dfact(q) / dfact(q + 1);
+    add(sJ, y, bk<P>(q) * w);
+    add(s0, y, double(q + 2) * bk<P>(q + 2) * w);
+    add(s2, y, double(q) * bk<P>(q) * w);
+    add(sk, dP, bk<P>(q));
+    y2 = y1;
+    y1 = y;
+  }
+  Jo = ((sJ.s - R(1.5f * gJ)) + sJ.c) * sc.is;
+  S0 = ((s0.s - R(1.5f * g0)) + s0.c) * sc.is;
+  S2 = ((s2.s - R(1.5f * g2)) + s2.c) * sc.is;
+  Dk = ((sk.s - R(1.5f * gk)) + sk.c) * sc.is;
+}
+
 template <typename R, class P>
 SPH2D_HD void edge_grad_integrals(R d, R t1, R t2, R& Jo, R& S0, R& S2, R& Dk) {
   using AC = typename AccSel<R, P>::type;
+  if constexpr (AC::SCALED) {
+    if (!(t2 > t1)) {
+      Jo = S0 = S2 = Dk = R(0);
+      return;
+    }
+    edge_grad_integrals_ff<R, P>(d, t1, t2, Jo, S0, S2, Dk);
+    return;
+  }
   using A = typename AC::T;
   using SM = typename AC::Sum;
   SM sJ = AC::zero(), s0 = AC::zero(), s2 = AC::zero(), sk = AC::zero();

@@ -567,6 +567,13 @@ sph2d_status sph2d_surrogate_set_engine(sph2d_ctx* h, int engine) {
   return SPH2D_OK;
 }
 
+sph2d_status sph2d_surrogate_set_train_engine(sph2d_ctx* h, int engine) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  if (engine != 0 && engine != 1) return set_err(&h->c, SPH2D_ERR_INVALID_ARG, "engine must be 0 (mma.sync) or 1 (tcgen05)");
+  h->c.sur_train_engine = engine;
+  return SPH2D_OK;
+}
+
 sph2d_status sph2d_surrogate_set_params(sph2d_ctx* h, const float* host, int64_t n) {
   Ctx* c;
   sph2d_status s = sur_ctx(h, &c, true);

@@ -59,6 +59,7 @@ struct Ctx {
   int sur_audit_period = 64;   // serving audit: one accepted pair in this many (0: off)
   double sur_audit_tol = 1e-3; // audit bound in units of the output scales
   int sur_engine = 0;          // serving MMAs: 0 mma.sync (register-chained), 1 tcgen05 (TMEM)
+  int sur_train_engine = 0;    // training GEMMs: 0 mma.sync, 1 tcgen05 (TMEM accumulators)
 };
 
 // error helpers ------------------------------------------------------------------------

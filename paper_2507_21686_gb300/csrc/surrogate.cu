@@ -31,6 +31,7 @@
 #include <cstring>
 #include <random>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "integrals_impl.cuh"
@@ -144,6 +145,115 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits,
   float s = 0.0f;
   for (int z = 0; z < splits; ++z) s += part[size_t(z) * M * N + i];
   C[size_t(i / N) * ldc + (i % N)] = alpha * s;
+}
+
+// ---------------------------------------------------------------------------------------
+// the same GEMM on the fifth-generation tensor cores (training engine 1): CTA tile 128 x 64,
+// K blocks of 32 staged (FP32 -> FP16/BF16, round to nearest even, zero padded) into shared
+// memory in the K-major no-swizzle core-matrix layout of umma.cuh; one thread issues two
+// tcgen05.mma kind::f16 (M = 128, N = 64, K = 16) per block into FP32 accumulators in tensor
+// memory (64 columns) and commits them to an mbarrier that every thread waits on (bounded);
+// the epilogue reads each row's 64 accumulators with one tcgen05.ld.  Same split-K contract as
+// gemm_tc_kernel.  A wait that runs out of its poll budget adds 1 to *timeouts, lets the MMA
+// drain (bounded) and leaves the tile's outputs unwritten.
+// ---------------------------------------------------------------------------------------
+constexpr int UBM = 128, UBN = 64, UBK = 32;
+constexpr uint32_t kGemmSpin = 1u << 22;
+
+template <typename T>
+struct GemmTcSmem {
+  T a[UBM * UBK];               // 8 KB: row r, column c at kmajor_offset(r, c, 32) bytes
+  T b[UBN * UBK];               // 4 KB
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) gemm_umma_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                        int lda, int ta, const float* __restrict__ B, int ldb,
+                                                        int tb, float* __restrict__ C, int ldc, float alpha,
+                                                        int ksplit, unsigned long long* timeouts) {
+  using umma::kmajor_offset;
+  __shared__ __align__(128) GemmTcSmem<T> s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    umma::tmem_alloc(&s.tmem, 64);
+    umma::tmem_relinquish();
+  }
+  if (tid == 0) {
+    umma::mbar_init(&s.mbar, 1);
+    umma::mbar_init_fence();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tm = s.tmem, sa = umma::smem_u32(s.a), sb = umma::smem_u32(s.b);
+  constexpr uint32_t ID = umma::idesc_f16(UBM, UBN, std::is_same<T, __nv_bfloat16>::value);
+  const int m0 = blockIdx.x * UBM, n0 = blockIdx.y * UBN;
+  const int kper = (K + ksplit - 1) / ksplit;
+  const int kbeg = blockIdx.z * kper, kend = min(K, kbeg + kper);
+  uint32_t phase = 0;
+  bool ok = true, any = false;
+  for (int k0 = kbeg; k0 < kend; k0 += UBK) {
+#pragma unroll 4
+    for (int i = 0; i < (UBM * UBK) / 128; ++i) {
+      const int e = tid + 128 * i;
+      int m, k;
+      if (!ta) { m = e / UBK; k = e % UBK; } else { k = e / UBM; m = e % UBM; }
+      const int gm = m0 + m, gk = k0 + k;
+      float v = 0.0f;
+      if (gm < M && gk < kend) v = ta ? A[size_t(gk) * lda + gm] : A[size_t(gm) * lda + gk];
+      s.a[kmajor_offset(m, k, UBK) / 2] = to_op(v, T());
+    }
+#pragma unroll 4
+    for (int i = 0; i < (UBN * UBK) / 128; ++i) {
+      const int e = tid + 128 * i;
+      int n, k;
+      if (!tb) { n = e / UBK; k = e % UBK; } else { k = e / UBN; n = e % UBN; }
+      const int gn = n0 + n, gk = k0 + k;
+      float v = 0.0f;
+      if (gn < N && gk < kend) v = tb ? B[size_t(gk) * ldb + gn] : B[size_t(gn) * ldb + gk];
+      s.b[kmajor_offset(n, k, UBK) / 2] = to_op(v, T());
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      umma::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < UBK / 16; ++kk)
+        umma::mma_f16(tm, umma::smem_desc(sa + 256 * kk, 128, 128 * UBK / 8),
+                      umma::smem_desc(sb + 256 * kk, 128, 128 * UBK / 8), ID, any || kk > 0);
+      umma::mma_commit(&s.mbar);
+    }
+    any = true;
+    ok = __syncthreads_and(umma::mbar_wait(&s.mbar, phase, kGemmSpin) ? 1 : 0) != 0;
+    umma::fence_after_sync();
+    if (!ok) break;
+    phase ^= 1u;
+  }
+  float* Cz = ksplit > 1 ? C + size_t(blockIdx.z) * M * N : C;
+  const int ld = ksplit > 1 ? N : ldc;
+  const float sc = ksplit > 1 ? 1.0f : alpha;
+  const int gm = m0 + 32 * warp + (tid & 31);
+  if (ok && any) {
+    float acc[UBN];
+    umma::tmem_ld64(tm + (uint32_t(32 * warp) << 16), acc);
+    if (gm < M)
+#pragma unroll
+      for (int j = 0; j < UBN; ++j)
+        if (n0 + j < N) Cz[size_t(gm) * ld + n0 + j] = sc * acc[j];
+  } else if (ok) {                                   // an empty K split: its partial is zero
+    if (gm < M)
+      for (int j = 0; j < UBN; ++j)
+        if (n0 + j < N) Cz[size_t(gm) * ld + n0 + j] = 0.0f;
+  } else {
+    if (tid == 0) atomicAdd(timeouts, 1ull);
+    umma::mbar_wait(&s.mbar, phase, kGemmSpin);      // let the overdue MMA drain
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tm, 64);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -892,19 +1002,32 @@ static unsigned persistent_grid(Ctx* c, K kern, int64_t blocks_wanted) {
 template <typename T>
 static sph2d_status gemm(Ctx* c, int M, int N, int K, const float* A, int lda, int ta, const float* B,
                          int ldb, int tb, float* C, int ldc) {
+  const bool tc = c->sur_train_engine == 1;
+  const int bm = tc ? UBM : GBM, bn = tc ? UBN : GBN;
   // split K when the output tile grid is small and K is long (weight gradients over the batch)
-  const int tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+  const int tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+  // (the tcgen05 engine waits on each K block's MMA, so it takes shorter splits: K / 256)
   int splits = 1;
-  if (K >= 4096 && tiles < 64) splits = std::min(64, K / 1024);
-  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, splits);
-  if (splits == 1) {
-    SPH2D_LAUNCH(c, (gemm_tc_kernel<T>), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0f, 1);
-    return SPH2D_OK;
+  if (K >= 4096 && tiles < 64) splits = tc ? std::min(128, K / 256) : std::min(64, K / 1024);
+  dim3 grid((M + bm - 1) / bm, (N + bn - 1) / bn, splits);
+  float* out = C;
+  int ldo = ldc;
+  if (splits > 1) {
+    sph2d_status s = ensure(c, c->sur_split, size_t(splits) * M * N * sizeof(float));
+    if (s != SPH2D_OK) return s;
+    out = static_cast<float*>(c->sur_split.ptr);
+    ldo = N;
   }
-  sph2d_status s = ensure(c, c->sur_split, size_t(splits) * M * N * sizeof(float));
-  if (s != SPH2D_OK) return s;
-  float* part = static_cast<float*>(c->sur_split.ptr);
-  SPH2D_LAUNCH(c, (gemm_tc_kernel<T>), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, part, N, 1.0f, splits);
+  if (tc) {
+    sph2d_status s = ensure(c, c->host_flags_dev, 64);
+    if (s != SPH2D_OK) return s;
+    auto* tmo = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 7;
+    SPH2D_LAUNCH(c, (gemm_umma_kernel<T>), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, out, ldo, 1.0f, splits, tmo);
+  } else {
+    SPH2D_LAUNCH(c, (gemm_tc_kernel<T>), grid, 128, M, N, K, A, lda, ta, B, ldb, tb, out, ldo, 1.0f, splits);
+  }
+  if (splits == 1) return SPH2D_OK;
+  float* part = out;
   SPH2D_LAUNCH(c, (splitk_reduce_kernel), nblk(int64_t(M) * N), 256, part, splits, M, N, C, ldc, 1.0f);
   return SPH2D_OK;
 }
@@ -1065,6 +1188,14 @@ sph2d_status surrogate_train(Ctx* c, const double* pairs, int64_t P, double H, i
   float* loss = grad + kSurParams;
   float* prm = static_cast<float*>(c->sur_prm.ptr);
   float *m = prm + kSurParams, *v = m + kSurParams;
+  unsigned long long* tmo = nullptr;               // tensor-core GEMM waits that ran out
+  if (c->sur_train_engine == 1) {
+    s = ensure(c, c->host_flags_dev, 64);
+    if (s != SPH2D_OK) return s;
+    tmo = static_cast<unsigned long long*>(c->host_flags_dev.ptr) + 7;
+    e = cudaMemsetAsync(tmo, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_err(c, e, "training");
+  }
   std::mt19937_64 rng(seed);
   const int64_t steps_per = R / batch;
   const int64_t total = steps_per * epochs;
@@ -1091,9 +1222,12 @@ sph2d_status surrogate_train(Ctx* c, const double* pairs, int64_t P, double H, i
     }
   }
   float lh = 0.0f;
+  unsigned long long nt = 0;
   e = cudaMemcpyAsync(&lh, loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && tmo) e = cudaMemcpyAsync(&nt, tmo, sizeof(nt), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_err(c, e, "training");
+  if (nt) return set_err(c, SPH2D_ERR_CUDA, "tensor-core GEMM: an MMA completion wait ran out of its poll budget");
   if (final_loss) *final_loss = lh;
   return SPH2D_OK;
 }

@@ -82,15 +82,21 @@ def test_forward_matches_reference(ctx):
     # roundings themselves: ~3e-4 of the output scale, far below any layout or indexing error)
 
 
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("B", [300, 5000])
-def test_grad_matches_reference(ctx, B):
-    """B = 300: one GEMM tile row, ragged; B = 5000: the weight-gradient GEMMs split K."""
+def test_grad_matches_reference(ctx, B, engine):
+    """B = 300: one GEMM tile row, ragged; B = 5000: the weight-gradient GEMMs split K.  Both
+    training GEMM engines (mma.sync; tcgen05 with TMEM accumulators)."""
     prm = glorot(31)
     ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
     X = canonical_inputs(B, 32)
     T = np.random.default_rng(33).normal(size=(B, 3)).astype(np.float32)
-    g, loss = ctx.surrogate_grad(_t(X), _t(T))
-    g = g.cpu().numpy().astype(np.float64)
+    ctx.set_surrogate_train_engine(engine)
+    try:
+        g, loss = ctx.surrogate_grad(_t(X), _t(T))
+        g = g.cpu().numpy().astype(np.float64)
+    finally:
+        ctx.set_surrogate_train_engine("mma_sync")
     w = S.loss_weights(C2)
     L, gref = S.loss_and_grad(prm, X.astype(np.float64), T.astype(np.float64), w, emulate_tc=True)
     assert abs(float(loss.item()) - L) <= 1e-2 * L
@@ -212,6 +218,44 @@ def test_training_is_deterministic_and_learns(ctx):
     assert runs[0][1] < 0.05 * float(l_init.item()), (runs[0][1], float(l_init.item()))
 
 
+def test_tcgen05_training_engine(ctx):
+    """The tcgen05 training GEMMs: the gradient of one batch agrees with the mma.sync engine's
+    (same rounded operands, FP32 accumulation in another order: a forward activation that lands
+    on the other side of an FP16 rounding moves a few gradient entries by one FP16 step), and a
+    short training run is bit-for-bit reproducible and learns as much as the mma.sync run."""
+    prm = glorot(37)
+    ctx.surrogate_init(KERNEL, 0).set_surrogate_params(prm)
+    X = canonical_inputs(20000, 38)
+    T = np.random.default_rng(39).normal(size=(20000, 3)).astype(np.float32)
+    g = {}
+    for eng in ("mma_sync", "tcgen05"):
+        ctx.set_surrogate_train_engine(eng)
+        g[eng] = ctx.surrogate_grad(_t(X), _t(T))[0].cpu().numpy().astype(np.float64)
+    ctx.set_surrogate_train_engine("mma_sync")
+    o = 0
+    for name, shape in S.SHAPES:
+        n = int(np.prod(shape))
+        a, b = g["tcgen05"][o:o + n], g["mma_sync"][o:o + n]
+        err = np.abs(a - b) / np.abs(b).max()
+        assert err.max() < 1e-2 and np.median(err) < 1e-4, (name, err.max(), np.median(err))
+        o += n
+    rng = np.random.default_rng(61)
+    pairs = W.surrogate_training_pairs(40000, rng)
+    res = {}
+    try:
+        for eng, reps in (("tcgen05", 2), ("mma_sync", 1)):
+            ctx.set_surrogate_train_engine(eng)
+            for _ in range(reps):
+                ctx.surrogate_init(KERNEL, 7)
+                loss, _ = ctx.surrogate_train(_t(pairs), 1.0, epochs=4, batch=1024, lr=3e-3, seed=9)
+                res.setdefault(eng, []).append((ctx.surrogate_params().numpy().copy(), loss))
+    finally:
+        ctx.set_surrogate_train_engine("mma_sync")
+    assert np.array_equal(res["tcgen05"][0][0], res["tcgen05"][1][0])
+    assert res["tcgen05"][0][1] == res["tcgen05"][1][1]
+    assert res["tcgen05"][0][1] < 2.0 * res["mma_sync"][0][1], (res["tcgen05"][0][1], res["mma_sync"][0][1])
+
+
 def test_checkpoint_roundtrip_and_resume(ctx, tmp_path):
     from paper_2507_21686_gb300._lib import Sph2dError
     rng = np.random.default_rng(71)
@@ -256,6 +300,7 @@ def test_error_statuses(ctx):
     with pytest.raises(Sph2dError, match="INVALID_ARG"):
         c.set_surrogate_params(np.zeros(10, dtype=np.float32))
     assert c.lib.sph2d_surrogate_set_engine(c.h, 2) == 1         # INVALID_ARG
+    assert c.lib.sph2d_surrogate_set_train_engine(c.h, -1) == 1  # INVALID_ARG
     # surrogate mode: kernel must match, moments are not provided
     parts = np.zeros((4, 4), dtype=np.float32)
     tris = np.array([[0.0, 0.0, 0.1, 0.0, 0.0, 0.1]], dtype=np.float32)
