@@ -220,6 +220,20 @@ SPH2D_HD double fma_f(double a, double b, double c) {
   return std::fma(a, b, c);
 #endif
 }
+// a / b for the FP32 path's geometry and the correction digits of float-pair roots and
+// quotients: the hardware's fast division on the GPU (within 2 ulp for |b| in [2^-126, 2^126]),
+// exact division elsewhere and in double
+SPH2D_HD float div_fast(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+SPH2D_HD double div_fast(double a, double b) { return a / b; }
+template <typename T>
+SPH2D_HD T div_fast(T a, T b) { return a / b; }
+
 // num/den as a double-double, for small integer den: hi = num/den rounded, lo = the exact
 // residual (num - hi*den)/den, with hi*den formed exactly from a Dekker split of hi
 SPH2D_HD constexpr FFT<double> dd_rational(double num, double den) {
@@ -291,7 +305,7 @@ SPH2D_HD FFT<F> ff_sqrt(FFT<F> x) {               // one Newton step on sqrt(hi)
   const F r = sqrt(x.hi);
   const FFT<F> r2 = ff_two_prod(r, r);
   const F res = ((x.hi - r2.hi) - r2.lo) + x.lo;
-  return ff_fast_two_sum(r, res / (F(2) * r));
+  return ff_fast_two_sum(r, div_fast(res, F(2) * r));
 }
 template <typename F>
 SPH2D_HD F to_f(FFT<F> a) { return a.hi + a.lo; }
@@ -319,9 +333,9 @@ SPH2D_HD V2<float> v2_mul(V2<float> a, V2<float> b) {
 #endif
 template <typename F>
 SPH2D_HD FFT<F> operator/(FFT<F> a, FFT<F> b) {   // long division, two quotient digits
-  const F q1 = a.hi / b.hi;
+  const F q1 = div_fast(a.hi, b.hi);
   const FFT<F> r = a - b * q1;
-  const F q2 = r.hi / b.hi;
+  const F q2 = div_fast(r.hi, b.hi);
   return ff_fast_two_sum(q1, q2);
 }
 template <typename F>
@@ -869,7 +883,7 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   const R l2 = ex * ex + ey * ey;
   const R c = diff_of_products(ax, by, ay, bx);          // A x B = |A||B| sin(fan angle)
   if (l2 == R(0) || c == R(0)) return;                   // degenerate fan: zero area
-  const R il = R(1) / sqrt(l2);
+  const R il = div_fast(R(1), sqrt(l2));
   const R d = fabs(c) * il;                              // distance of the edge line
   if (d < Tiny<R>::v()) return;                          // contribution O(d log d)
   const R sg = c > R(0) ? R(1) : R(-1);
@@ -887,7 +901,7 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   const R due = atan2(d * (t2 - t1), d2 + t1 * t2);      // edge-piece angle u_2 - u_1
   const R dus = dth - due;                               // sector pieces, total angle
   // (cos u, sin u) at u_A, u_1, u_2, u_B
-  const R iA = R(1) / rA, iB = R(1) / rB, i1 = R(1) / r1, i2 = R(1) / r2;
+  const R iA = div_fast(R(1), rA), iB = div_fast(R(1), rB), i1 = div_fast(R(1), r1), i2 = div_fast(R(1), r2);
   const R cA = d * iA, sA = tA * iA, cB = d * iB, sB = tB * iB;
   const R c1 = d * i1, s1 = t1 * i1, c2 = d * i2, s2 = t2 * i2;
 
