@@ -233,6 +233,28 @@ SPH2D_HD float div_fast(float a, float b) {
 SPH2D_HD double div_fast(double a, double b) { return a / b; }
 template <typename T>
 SPH2D_HD T div_fast(T a, T b) { return a / b; }
+// 1 / sqrt(x) and sqrt(x) for x > 0 the same way: the hardware's reciprocal square root on the
+// GPU (within 2 ulp) for the FP32 geometry and the first digit of the float-pair root
+SPH2D_HD float rsqrt_fast(float x) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(x);
+#else
+  return 1.0f / std::sqrt(x);
+#endif
+}
+SPH2D_HD double rsqrt_fast(double x) { return 1.0 / sqrt(x); }
+template <typename T>
+SPH2D_HD T rsqrt_fast(T x) { return T(1) / sqrt(x); }
+SPH2D_HD float sqrt_fast(float x) {
+#if defined(__CUDA_ARCH__)
+  return x * rsqrtf(x);
+#else
+  return std::sqrt(x);
+#endif
+}
+SPH2D_HD double sqrt_fast(double x) { return sqrt(x); }
+template <typename T>
+SPH2D_HD T sqrt_fast(T x) { return sqrt(x); }
 
 // num/den as a double-double, for small integer den: hi = num/den rounded, lo = the exact
 // residual (num - hi*den)/den, with hi*den formed exactly from a Dekker split of hi
@@ -302,7 +324,7 @@ SPH2D_HD FFT<F> operator*(FFT<F> a, F b) {
 template <typename F>
 SPH2D_HD FFT<F> ff_sqrt(FFT<F> x) {               // one Newton step on sqrt(hi)
   if (x.hi <= F(0)) return FFT<F>{F(0), F(0)};
-  const F r = sqrt(x.hi);
+  const F r = sqrt_fast(x.hi);
   const FFT<F> r2 = ff_two_prod(r, r);
   const F res = ((x.hi - r2.hi) - r2.lo) + x.lo;
   return ff_fast_two_sum(r, div_fast(res, F(2) * r));
@@ -883,7 +905,7 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   const R l2 = ex * ex + ey * ey;
   const R c = diff_of_products(ax, by, ay, bx);          // A x B = |A||B| sin(fan angle)
   if (l2 == R(0) || c == R(0)) return;                   // degenerate fan: zero area
-  const R il = div_fast(R(1), sqrt(l2));
+  const R il = rsqrt_fast(l2);
   const R d = fabs(c) * il;                              // distance of the edge line
   if (d < Tiny<R>::v()) return;                          // contribution O(d log d)
   const R sg = c > R(0) ? R(1) : R(-1);
@@ -892,16 +914,16 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
   const R tA = ay * nx - ax * ny;
   const R tB = by * nx - bx * ny;
   const R dth = atan2(c, ax * bx + ay * by);             // signed fan angle u_B - u_A
-  const R ts = d < R(1) ? sqrt((R(1) - d) * (R(1) + d)) : R(0);
+  const R ts = d < R(1) ? sqrt_fast((R(1) - d) * (R(1) + d)) : R(0);
   const R t1 = fmin(fmax(tA, -ts), ts);
   const R t2 = fmin(fmax(tB, -ts), ts);
   const R d2 = d * d;
   const R r1 = sqrt(d2 + t1 * t1), r2 = sqrt(d2 + t2 * t2);
-  const R rA = sqrt(d2 + tA * tA), rB = sqrt(d2 + tB * tB);
   const R due = atan2(d * (t2 - t1), d2 + t1 * t2);      // edge-piece angle u_2 - u_1
   const R dus = dth - due;                               // sector pieces, total angle
   // (cos u, sin u) at u_A, u_1, u_2, u_B
-  const R iA = div_fast(R(1), rA), iB = div_fast(R(1), rB), i1 = div_fast(R(1), r1), i2 = div_fast(R(1), r2);
+  const R iA = rsqrt_fast(d2 + tA * tA), iB = rsqrt_fast(d2 + tB * tB);
+  const R i1 = rsqrt_fast(d2 + t1 * t1), i2 = rsqrt_fast(d2 + t2 * t2);
   const R cA = d * iA, sA = tA * iA, cB = d * iB, sB = tB * iB;
   const R c1 = d * i1, s1 = t1 * i1, c2 = d * i2, s2 = t2 * i2;
 
