@@ -54,14 +54,14 @@ __device__ __forceinline__ void quad_pair(const RT& rt, const QuadRule& qs, cons
   for (int j = 0; j < RT::N; ++j) {
     const float dx = e1x + rt.u[j] * e2x, dy = e1y + rt.u[j] * e2y;
     const float aa = dx * dx + dy * dy, bb = v0x * dx + v0y * dy;
-    const float sp = -c0 / (bb + sqrtf(fmaxf(bb * bb - aa * c0, 0.0f)));
+    const float sp = div_fast(-c0, bb + sqrtf(fmaxf(bb * bb - aa * c0, 0.0f)));
     const float ss = fminf(1.0f, sp);
     const float wj = rt.w[j] * ss * ss;
 #pragma unroll
     for (int i = 0; i < kQuadN; ++i) {
       const float s = ss * qs.u[i];
       const float px = v0x + s * dx, py = v0y + s * dy;
-      const float r = sqrtf(px * px + py * py);
+      const float r = sqrt_fast(px * px + py * py);      // > 0: the particle is off the triangle
       float k, kd;
       kernel_and_slope<KID>(r, inner, k, kd);
       const float w = wj * qs.wu[i];

@@ -111,7 +111,7 @@ __device__ __forceinline__ void kernel_and_slope(float r, bool inner, float& k, 
     kd = -12.0f + 18.0f * r;
   } else {
     k = 2.0f * m3;
-    kd = -6.0f * m2 / r;
+    kd = div_fast(-6.0f * m2, r);
   }
 }
 
