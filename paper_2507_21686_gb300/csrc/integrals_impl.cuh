@@ -301,12 +301,14 @@ __device__ __forceinline__ void write_particle(const IntArgs& a, int64_t pid, co
   }
 }
 
-// Minimum resident 128-thread blocks per SM for the FP32 pair kernels: 4 caps them at 128
-// registers (16 warps per SM), measured 25% faster for Wendland C2 with moments than the
-// compiler's own 148-register allocation (12 warps) and faster than a 96-register cap, which
-// spills.  The FP64 instantiations keep the compiler's choice.
+// Minimum resident 128-thread blocks per SM for the FP32 pair kernels: 5 caps them at 96
+// registers (20 warps per SM).  Measured on the 1024^2 box: 4 blocks (128 registers) ran 25%
+// faster for Wendland C2 with moments than the compiler's own 148-register allocation, and
+// once the fan code had shrunk (grid-extraction sums, fast division and square roots) 5 blocks
+// ran 3-7% faster than 4 although the ten-moment instances spill 80-150 bytes per thread.  The
+// FP64 instantiations keep the compiler's choice.
 #ifndef SPH2D_INT_MINB
-#define SPH2D_INT_MINB 4
+#define SPH2D_INT_MINB 5
 #endif
 #ifndef SPH2D_INT_MINB64
 #define SPH2D_INT_MINB64 1
@@ -851,11 +853,10 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
   }
 }
 
-// The cubic spline's partition kernel runs at the Wendland kernels' cap (4 blocks of 128 threads
-// per SM, <= 128 registers).  With its pieces' fans inlined it ran best at 3 blocks (168
-// registers).  With the fans looped, 4 blocks measured 6.5% faster than 3 with ten moments
-// (3.41 -> 3.19 ms on the 1024^2 box), although the ten-moment instance spills 92 bytes per
-// thread there.
+// The cubic spline's partition kernel runs at the Wendland kernels' cap.  With its pieces'
+// fans inlined it ran best at 3 blocks (168 registers); with the fans looped, 4 blocks measured
+// 6.5% faster than 3 with ten moments (3.41 -> 3.19 ms on the 1024^2 box), and later 5 blocks
+// as fast as 4 with ten moments and 7% faster without, spilling 148 bytes per thread.
 template <typename OT, int MD> constexpr int cubic_split_minb() { return int_minb<OT>(); }
 
 // chunks of 32 positions of the near/far partition

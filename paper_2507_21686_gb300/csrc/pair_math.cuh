@@ -478,12 +478,12 @@ SPH2D_HD typename LogEntType<DBL>::type log_entry(int i) {
 // two-products of both words of m with inv_i (|r| <= 2^-7.5), and ln(1 + r) = sum_k (-1)^(k+1) r^k / k.  The
 // terms through r^NP run in pair arithmetic, the rest (through r^NT) in the base precision:
 // relative to r their base-precision rounding is below the pair's unit roundoff (float pairs:
-// NP = 4, NT = 8; double pairs: NP = 7, NT = 15).  Every x near 1, on either side, has e = 0 and
+// NP = 3, NT = 8; double pairs: NP = 7, NT = 15).  Every x near 1, on either side, has e = 0 and
 // c = 1 (inv = 1, L = 0): r = x - 1 exactly, so a small logarithm keeps its relative accuracy.
 template <typename F, typename B = F>
 SPH2D_HD FFT<F> ff_log(FFT<F> x) {
   constexpr bool DBL = sizeof(B) == sizeof(double);
-  constexpr int NP = DBL ? 7 : 4, NT = DBL ? 15 : 8;
+  constexpr int NP = DBL ? 7 : 3, NT = DBL ? 15 : 8;
   int e = 0;
   const F m0 = frexp_f(x.hi, &e);                        // [1/2, 1)
   // (all of this in the working precision: a double literal here would put FP64 instructions
