@@ -306,19 +306,23 @@ __device__ __forceinline__ void write_particle(const IntArgs& a, int64_t pid, co
 // faster for Wendland C2 with moments than the compiler's own 148-register allocation, and
 // once the fan code had shrunk (grid-extraction sums, fast division and square roots) 5 blocks
 // ran 3-7% faster than 4 although the ten-moment instances spill 80-150 bytes per thread.  The
-// FP64 instantiations keep the compiler's choice.
+// FP64 instantiations keep the compiler's choice.  Without the ten moments (MD <= 1) 6 blocks
+// (80 registers) measured another 1-3% faster; with them, 3% slower than 5.
 #ifndef SPH2D_INT_MINB
 #define SPH2D_INT_MINB 5
+#endif
+#ifndef SPH2D_INT_MINB_LOW
+#define SPH2D_INT_MINB_LOW 6
 #endif
 #ifndef SPH2D_INT_MINB64
 #define SPH2D_INT_MINB64 1
 #endif
-template <typename OT> constexpr int int_minb() {
-  return sizeof(OT) == sizeof(float) ? SPH2D_INT_MINB : SPH2D_INT_MINB64;
+template <typename OT, int MD = 3> constexpr int int_minb() {
+  return sizeof(OT) == sizeof(float) ? (MD <= 1 ? SPH2D_INT_MINB_LOW : SPH2D_INT_MINB) : SPH2D_INT_MINB64;
 }
 
 template <typename OT, int KID, int MD>
-__global__ void __launch_bounds__(128, int_minb<OT>()) integrals_kernel(IntArgs a) {
+__global__ void __launch_bounds__(128, int_minb<OT, MD>()) integrals_kernel(IntArgs a) {
   constexpr int NV = nv_of(MD);
   const int lane = threadIdx.x & 31;
   const int64_t nchunks = (a.P + 31) >> 5;
@@ -857,7 +861,7 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
 // fans inlined it ran best at 3 blocks (168 registers); with the fans looped, 4 blocks measured
 // 6.5% faster than 3 with ten moments (3.41 -> 3.19 ms on the 1024^2 box), and later 5 blocks
 // as fast as 4 with ten moments and 7% faster without, spilling 148 bytes per thread.
-template <typename OT, int MD> constexpr int cubic_split_minb() { return int_minb<OT>(); }
+template <typename OT, int MD> constexpr int cubic_split_minb() { return int_minb<OT, MD>(); }
 
 // chunks of 32 positions of the near/far partition
 template <typename OT, int MD>

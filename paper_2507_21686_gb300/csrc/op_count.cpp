@@ -84,6 +84,20 @@ inline Counted<float> ldexp_f(Counted<float> x, int e) { return mk<float>(std::l
 template <typename F> struct Pow2;
 // the exact power-of-two scale of the FF edge sums (exponent-field work: not counted)
 inline Pow2<Counted<float>> pow2_scale(Counted<float> x);
+// the FP32 path's polynomial atan2, counted operation by operation as the kernels run it
+inline Counted<float> atan2_fast(Counted<float> y, Counted<float> x) {
+  const Counted<float> ax = fabs(x), ay = fabs(y);
+  const Counted<float> t = fmin(ax, ay) / fmax(ax, ay), w = t * t;
+  static const float c[10] = {-1.753866789e-03f, 1.072655618e-02f, -3.080365062e-02f, 5.755088106e-02f,
+                              -8.377224952e-02f, 1.094199046e-01f, -1.426192224e-01f, 1.999826431e-01f,
+                              -3.333328366e-01f, 1.0f};
+  Counted<float> p = Counted<float>(c[0]);
+  for (int k = 1; k < 10; ++k) p = fma_f(p, w, Counted<float>(c[k]));
+  Counted<float> a = t * p;
+  if (ay > ax) a = Counted<float>(1.57079637f) - a;
+  if (x < Counted<float>(0.0f)) a = Counted<float>(3.14159274f) - a;
+  return y < Counted<float>(0.0f) ? -a : a;
+}
 }  // namespace sph2d
 
 #include "pair_math.cuh"
