@@ -39,6 +39,9 @@ struct IntArgs {
   const int64_t* pair_off;
   int64_t P, N;
   double H, invH, C;
+  // 1/H and the kernel constant rounded to FP32 once on the host (0: not set, then the FP32
+  // path rounds a.invH and a.C per pair)
+  float invHf = 0.0f, Cf = 0.0f;
   void* gamma;
   void* grad;
   void* mom;
@@ -66,8 +69,8 @@ __device__ __forceinline__ int64_t chunk_next(unsigned long long* work, int64_t 
 }
 
 // raw integrals of one local-frame triangle -> v = (gamma, grad x, grad y, M00..M03)
-template <typename R, int KID, int MD>
-__device__ __forceinline__ void eval_local(const R* l, double C, double invH, R* v) {
+template <typename R, int KID, int MD, typename S>
+__device__ __forceinline__ void eval_local(const R* l, S C, S invH, R* v) {
   const int s = tri_orientation<R>(l[0], l[1], l[2], l[3], l[4], l[5]);
   if (s == 0) {
 #pragma unroll
@@ -153,7 +156,7 @@ __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT*
     return eval_mode<OT, KID, MD>(ld, a.C, a.invH, v);
   } else {
     // FP32 local frame straight from the FP32 inputs
-    const float ih = float(a.invH);
+    const float ih = a.invHf != 0.0f ? a.invHf : float(a.invH), cf = a.Cf != 0.0f ? a.Cf : float(a.C);
     float lf[6];
     bool ok = true;
 #pragma unroll
@@ -164,7 +167,7 @@ __device__ __forceinline__ int eval_pair(const IntArgs& a, int pid, int tid, OT*
     }
     if (ok) {
       float w[13];
-      eval_local<float, KID, MD>(lf, a.C, a.invH, w);
+      eval_local<float, KID, MD>(lf, cf, ih, w);
 #pragma unroll
       for (int i = 0; i < nv_of(MD); ++i) ok = ok && isfinite(w[i]);
       if (ok) {
@@ -411,8 +414,8 @@ __device__ __forceinline__ bool near_half(const R* l) {
 }
 
 // one piece of the cubic spline for a local triangle of orientation s != 0 -> v (scaled)
-template <typename R, int MD>
-__device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, double C, double invH, R* v) {
+template <typename R, int MD, typename S>
+__device__ __forceinline__ void cubic_piece(const R* l, int piece, int s, S C, S invH, R* v) {
   const R sc = piece ? R(2) : R(1);
   PairOut<R> h;
   clear(h);
@@ -806,7 +809,7 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
   const float4 p = a.parts[pid];
   const float* t = a.tris + 6 * int64_t(tid);
   if constexpr (sizeof(OT) == sizeof(float)) {
-    const float ih = float(a.invH);
+    const float ih = a.invHf != 0.0f ? a.invHf : float(a.invH), cf = a.Cf != 0.0f ? a.Cf : float(a.C);
     float lf[6];
     bool ok = true;
 #pragma unroll
@@ -824,7 +827,7 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
 #pragma unroll 1
       for (int piece = 0; piece < npieces; ++piece) {
         float w[13];
-        cubic_piece<float, MD>(lf, piece, s, a.C, a.invH, w);
+        cubic_piece<float, MD>(lf, piece, s, cf, ih, w);
 #pragma unroll
         for (int i = 0; i < NV; ++i) v[i] = piece ? v[i] + w[i] : w[i];
       }
@@ -992,6 +995,8 @@ static sph2d_status run_md(Ctx* c, int md, IntArgs a) {
 
 template <typename OT>
 static sph2d_status dispatch_integrals(Ctx* c, int kernel, int md, IntArgs a) {
+  a.invHf = float(a.invH);
+  a.Cf = float(a.C);
   switch (kernel) {
     case KID_WC2: return run_md<OT, KID_WC2>(c, md, a);
     case KID_WC4: return run_md<OT, KID_WC4>(c, md, a);

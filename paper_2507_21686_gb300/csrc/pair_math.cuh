@@ -498,6 +498,33 @@ SPH2D_HD typename LogEntType<DBL>::type log_entry(int i) {
   }
 }
 
+// The log's argument split: x = 2^e xm with xm.hi in [1/sqrt2, sqrt2), both words scaled exactly.
+template <typename F>
+SPH2D_HD FFT<F> log_split(FFT<F> x, int& e) {
+  const F m0 = frexp_f(x.hi, &e);                        // [1/2, 1)
+  // (all of this in the working precision: a double literal here would put FP64 instructions
+  // into the FP32 kernels)
+  using MF = decltype(raw_f(m0));
+  if (raw_f(m0) < MF(0.70710678118654752)) e -= 1;       // m = x.hi 2^-e in [1/sqrt2, sqrt2)
+  return FFT<F>{ldexp_f(x.hi, -e), ldexp_f(x.lo, -e)};
+}
+// float pairs on the GPU: straight from the exponent field and the leading mantissa bits, with
+// one exact product by 2^-e per word.  x.hi is a positive normal float here: the log's arguments
+// are ratios of sums |t| + rho >= d >= 1e-18 with |t| below 64 (local coordinates past 16 take
+// the FP64 path), between 1e-20 and 1e37.
+SPH2D_HD FFT<float> log_split(FFT<float> x, int& e) {
+#if defined(__CUDA_ARCH__)
+  const unsigned b = __float_as_uint(x.hi);
+  e = int((b >> 23) & 0xffu) - 126 - ((b & 0x7fffffu) < 0x3504f3u ? 1 : 0);
+  const float sc = __uint_as_float(unsigned(127 - e) << 23);
+  return FFT<float>{x.hi * sc, x.lo * sc};
+#else
+  const float m0 = std::frexp(x.hi, &e);
+  if (m0 < 0.70710678118654752f) e -= 1;
+  return FFT<float>{std::ldexp(x.hi, -e), std::ldexp(x.lo, -e)};
+#endif
+}
+
 // natural log of x > 0 in compensated arithmetic (float pairs, or double pairs for B = double).
 // Table reduction (Tang's method): x = 2^e m with m in [1/sqrt2, sqrt2), and c_i = (64 + i)/128
 // the table point nearest m, so that
@@ -513,12 +540,8 @@ SPH2D_HD FFT<F> ff_log(FFT<F> x) {
   constexpr bool DBL = sizeof(B) == sizeof(double);
   constexpr int NP = DBL ? 7 : 3, NT = DBL ? 15 : 8;
   int e = 0;
-  const F m0 = frexp_f(x.hi, &e);                        // [1/2, 1)
-  // (all of this in the working precision: a double literal here would put FP64 instructions
-  // into the FP32 kernels)
-  using MF = decltype(raw_f(m0));
-  if (raw_f(m0) < MF(0.70710678118654752)) e -= 1;       // m = x.hi 2^-e in [1/sqrt2, sqrt2)
-  const FFT<F> xm{ldexp_f(x.hi, -e), ldexp_f(x.lo, -e)}; // exact scaling
+  const FFT<F> xm = log_split(x, e);                     // x = 2^e xm, xm.hi in [1/sqrt2, sqrt2)
+  using MF = decltype(raw_f(xm.hi));
   const int i = int(raw_f(xm.hi) * MF(128) + MF(0.5)) - 64;   // nearest table point (either one at a tie)
   const auto ent = log_entry<DBL>(i);
   const F inv = F(ent.inv);
