@@ -147,14 +147,67 @@ __global__ void tri_fill_kernel(Grid g, const float* __restrict__ tris, int64_t 
     }
 }
 
-// sort each cell list ascending: bitonic in shared memory (<= 4096 ids), else insertion sort
+// sort each list of up to 512 ids ascending: one warp per list, a bitonic network over E ids per
+// lane (index lane + 32 r, r < E, E the smallest power of two with 32 E >= n), padded with
+// INT32_MAX.  Compare-exchanges across lanes (distance < 32) go through shuffles, the others
+// between a lane's own registers.  Longer lists are left to sort_cells_kernel.
+constexpr int kWarpSortMax = 512;
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int32_t* __restrict__ d, int64_t n, int lane) {
+  int32_t a[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) a[r] = lane + 32 * r < n ? d[lane + 32 * r] : 0x7fffffff;
+#pragma unroll
+  for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int rj = j >> 5;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if ((r & rj) != 0) continue;
+          const bool up = ((lane + 32 * r) & k) == 0;
+          const int32_t lo = min(a[r], a[r | rj]), hi = max(a[r], a[r | rj]);
+          a[r] = up ? lo : hi;
+          a[r | rj] = up ? hi : lo;
+        }
+      } else {
+        const bool lower = (lane & j) == 0;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int32_t p = __shfl_xor_sync(0xffffffffu, a[r], j);
+          const bool up = ((lane + 32 * r) & k) == 0;
+          a[r] = (lower == up) ? min(a[r], p) : max(a[r], p);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < E; ++r)
+    if (lane + 32 * r < n) d[lane + 32 * r] = a[r];
+}
+__global__ void sort_small_kernel(const int64_t* __restrict__ start, int32_t* __restrict__ data, int64_t nseg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; c < nseg; c += nw) {
+    const int64_t s = start[c], n = start[c + 1] - s;   // warp-uniform
+    if (n <= 1 || n > kWarpSortMax) continue;
+    if (n <= 64) warp_bitonic<2>(data + s, n, lane);
+    else if (n <= 128) warp_bitonic<4>(data + s, n, lane);
+    else if (n <= 256) warp_bitonic<8>(data + s, n, lane);
+    else warp_bitonic<16>(data + s, n, lane);
+  }
+}
+
+// sort each cell list of more than kWarpSortMax ids ascending: bitonic in shared memory (<= 4096
+// ids), else insertion sort
 constexpr int kSortCap = 4096;
 __global__ void sort_cells_kernel(const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_tris,
                                   int64_t n_cells) {
   __shared__ int32_t buf[kSortCap];
   for (int64_t c = blockIdx.x; c < n_cells; c += gridDim.x) {
     const int64_t s = cell_start[c], n = cell_start[c + 1] - s;
-    if (n <= 1) continue;
+    if (n <= kWarpSortMax) continue;
     if (n <= kSortCap) {
       int p2 = 1;
       while (p2 < n) p2 <<= 1;
@@ -340,19 +393,35 @@ __global__ void cull_kernel(CullArgs a, const float4* __restrict__ parts, int64_
   counts[i] = n;
 }
 
-// the compacted lists into the particle-major pair list
+// the compacted lists into the particle-major pair list: one warp per 32 consecutive particles,
+// its lanes striding over the warp's whole output range [pair_off[i0], pair_off[i0 + 32]) so
+// that every store is coalesced; a lane finds the particle of its output position by a binary
+// search over the 33 offsets, which the lanes hold in registers
 __global__ void pair_copy_kernel(int64_t N, const int64_t* __restrict__ cand_off, const int32_t* __restrict__ kept,
                                  const int64_t* __restrict__ pair_off, int32_t* __restrict__ pair_tri,
                                  int32_t* __restrict__ pair_pid) {
-  // one warp per particle, lanes over its pairs
-  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t i0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) << 5;
   const int lane = threadIdx.x & 31;
-  if (i >= N) return;
-  const int64_t s0 = pair_off[i], n = pair_off[i + 1] - s0;
-  const int32_t* src = kept + cand_off[i];
-  for (int64_t k = lane; k < n; k += 32) {
-    pair_tri[s0 + k] = src[k];
-    pair_pid[s0 + k] = int32_t(i);
+  if (i0 >= N) return;                                    // warp-uniform
+  const int64_t il = i0 + lane < N ? i0 + lane : N;
+  const int64_t off = pair_off[il];                       // lane j: start of particle i0 + j
+  const int64_t coff = i0 + lane < N ? cand_off[i0 + lane] : 0;
+  const int64_t beg = __shfl_sync(0xffffffffu, off, 0);
+  const int64_t end = pair_off[i0 + 32 < N ? i0 + 32 : N];
+  for (int64_t base = beg; base < end; base += 32) {     // uniform trip count: every lane shuffles
+    const int64_t pos = base + lane;
+    // largest j with off_j <= pos (particles with no pairs share their offset with the next)
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int64_t o = __shfl_sync(0xffffffffu, off, j + step);
+      if (o <= pos && i0 + j + step < N) j += step;
+    }
+    const int64_t oj = __shfl_sync(0xffffffffu, off, j), cj = __shfl_sync(0xffffffffu, coff, j);
+    if (pos < end) {
+      pair_tri[pos] = kept[cj + (pos - oj)];
+      pair_pid[pos] = int32_t(i0 + j);
+    }
   }
 }
 
@@ -360,7 +429,9 @@ __global__ void pair_copy_kernel(int64_t N, const int64_t* __restrict__ cand_off
 // by the adjoint, for per-triangle particle lists)
 void launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg) {
   if (nseg <= 0) return;
-  const int blocks = nseg < 65535 ? int(nseg) : 65535;
+  const int64_t wblocks = (nseg + 7) / 8;                 // 8 warps of 256 threads per block
+  SPH2D_LAUNCH(c, (sort_small_kernel), unsigned(wblocks < 65535 ? wblocks : 65535), 256, start, data, nseg);
+  const int blocks = nseg < 1216 ? int(nseg) : 1216;     // the few long lists
   SPH2D_LAUNCH(c, (sort_cells_kernel), blocks, 256, start, data, nseg);
 }
 
@@ -491,10 +562,7 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   auto* ctris = static_cast<int32_t*>(c->cell_tris.ptr);
   SPH2D_LAUNCH(c, (tri_fill_kernel), tblocks, kBlock, g, tris, M, cstart, ccount, ctris);
-  {
-    int blocks = C < 65535 ? int(C) : 65535;
-    SPH2D_LAUNCH(c, (sort_cells_kernel), blocks, 256, cstart, ctris, C);
-  }
+  launch_sort_segments(c, cstart, ctris, C);
 
   // ---- 3. cull: each particle's candidates once into a scratch segment, then scan and copy
   CullArgs a;
@@ -528,7 +596,7 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   if (s == SPH2D_OK) s = ensure(c, c->pair_pid, size_t(P > 0 ? P : 1) * sizeof(int32_t));
   if (s != SPH2D_OK) return s;
   {
-    const int64_t threads = N * 32;
+    const int64_t threads = ((N + 31) / 32) * 32;             // one warp per 32 particles
     SPH2D_LAUNCH(c, (pair_copy_kernel), unsigned((threads + kBlock - 1) / kBlock), kBlock, N, coff, kept, poff,
                  static_cast<int32_t*>(c->pair_tri.ptr), static_cast<int32_t*>(c->pair_pid.ptr));
   }
