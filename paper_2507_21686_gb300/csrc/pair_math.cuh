@@ -642,13 +642,106 @@ SPH2D_HD constexpr NumDen edge_coef_y(int q, int s) {
   if (slot_uses_drho(s) || q < 1) return c;
   return NumDen{c.num * dfact(q), c.den * dfact(q + 1)};
 }
+// Exact FP32 rows.  Every b_k has a denominator dividing 3, so each entry of edge_coef_y is a
+// ratio n/d of small integers.  Scaled by D_P, the odd part of the least common multiple of all
+// of a polynomial's denominators, every entry becomes an integer over a power of two; where the
+// odd parts of those integers all stay below 2^24 (Wendland C2 and C4, the cubic spline; not C6)
+// the scaled rows are exact in FP32.  The FP32 path then runs the whole fan computation scaled by
+// D_P (sector constants included) with one FP32 coefficient per sum term instead of a float
+// pair, and tri_poly multiplies the pair's outputs by 1/D_P once.
+struct RatI {
+  long long n, d;
+};
+SPH2D_HD constexpr long long gcd_ll(long long a, long long b) {
+  a = a < 0 ? -a : a;
+  b = b < 0 ? -b : b;
+  while (b != 0) {
+    const long long t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+SPH2D_HD constexpr long long round_ll(double x) {
+  return x >= 0.0 ? (long long)(x + 0.5) : -(long long)(-x + 0.5);
+}
+SPH2D_HD constexpr long long odd_part(long long v) {
+  while (v != 0 && v % 2 == 0) v /= 2;
+  return v;
+}
+template <class P>
+SPH2D_HD constexpr RatI edge_rat_y(int q, int s) {
+  const NumDen c = edge_coef_y<P>(q, s);
+  long long n = round_ll(c.num * 3.0), d = round_ll(c.den) * 3;
+  if (n == 0) return RatI{0, 1};
+  const long long g = gcd_ll(n, d);
+  n /= g;
+  d /= g;
+  return d < 0 ? RatI{-n, -d} : RatI{n, d};
+}
+template <class P>
+SPH2D_HD constexpr long long poly_lcm() {
+  long long L = 1;
+  for (int s = 0; s < NSL; ++s)
+    for (int q = -1; q <= P::K + 4; ++q) {
+      const long long d = odd_part(edge_rat_y<P>(q, s).d);
+      L = L / gcd_ll(L, d) * d;
+    }
+  return L;
+}
+// D_P where the scaled rows are exact in FP32, else 0 (the rows keep float-pair coefficients)
+template <class P>
+SPH2D_HD constexpr long long poly_den_eval() {
+  const long long L = poly_lcm<P>();
+  for (int s = 0; s < NSL; ++s)
+    for (int q = -1; q <= P::K + 4; ++q) {
+      const RatI r = edge_rat_y<P>(q, s);
+      if (r.n == 0) continue;
+      const long long m = odd_part(r.n) * (L / odd_part(r.d));
+      if ((m < 0 ? -m : m) >= (1LL << 24)) return 0;
+    }
+  return L;
+}
+// evaluated once, at compile time (the device code only reads the constants)
+template <class P>
+struct PolyDen {
+  static constexpr long long v = poly_den_eval<P>();
+  static constexpr double scale = v > 0 ? double(v) : 1.0;
+};
+template <class P>
+SPH2D_HD constexpr long long poly_den() { return PolyDen<P>::v; }
+// the FP32 path's scale of polynomial P (1 where the rows are not exact)
+template <class P>
+SPH2D_HD constexpr double poly_scale() { return PolyDen<P>::scale; }
+// edge_coef_y(q, s) times D_P, exact in FP32 (0 for P without exact rows): the double product
+// is within 2^-52 of the exact value, which is an FP32 number, so the rounding to FP32 recovers it
+// (checked against the integer form by rows_exact_in_fp32)
+template <class P>
+SPH2D_HD constexpr double edge_coef_s(int q, int s) {
+  if (PolyDen<P>::v == 0) return 0.0;
+  const NumDen c = edge_coef_y<P>(q, s);
+  return c.num == 0.0 ? 0.0 : double(float(c.num / c.den * PolyDen<P>::scale));
+}
+template <class P>
+SPH2D_HD constexpr bool rows_exact_in_fp32() {
+  if (poly_den<P>() == 0) return true;
+  for (int q = -1; q <= P::K + 4; ++q)
+    for (int s = 0; s < NSL; ++s) {
+      const RatI r = edge_rat_y<P>(q, s);
+      const long long od = odd_part(r.d);
+      const double exact = r.n == 0 ? 0.0 : double(r.n * (poly_den<P>() / od)) / double(r.d / od);
+      if (edge_coef_s<P>(q, s) != exact || double(float(exact)) != exact) return false;
+    }
+  return true;
+}
 template <class P>
 struct EdgeRows {
   static constexpr int QMIN = -1, QMAX = P::K + 4, ROWS = QMAX - QMIN + 1;
   double d[ROWS][NSL];                    // double
   double dlo[ROWS][NSL];                  // double-double low parts
   float fhi[ROWS][NSL], flo[ROWS][NSL];   // float-float
-  constexpr EdgeRows() : d(), dlo(), fhi(), flo() {
+  float fs[ROWS][NSL];                    // the FP32 path's exact rows, times D_P (edge_coef_s)
+  constexpr EdgeRows() : d(), dlo(), fhi(), flo(), fs() {
     for (int q = QMIN; q <= QMAX; ++q)
       for (int s = 0; s < NSL; ++s) {
         const NumDen c = edge_coef<P>(q, s);
@@ -659,6 +752,7 @@ struct EdgeRows {
         const FF ff = ff_const(cy.num / cy.den);
         fhi[q - QMIN][s] = ff.hi;
         flo[q - QMIN][s] = ff.lo;
+        fs[q - QMIN][s] = float(edge_coef_s<P>(q, s));
       }
   }
 };
@@ -685,6 +779,13 @@ SPH2D_ROWS(PolyWC4, g_rows_wc4)
 SPH2D_ROWS(PolyWC6, g_rows_wc6)
 SPH2D_ROWS(PolyCube, g_rows_cube)
 #undef SPH2D_ROWS
+static_assert(rows_exact_in_fp32<PolyWC2>() && rows_exact_in_fp32<PolyWC4>() && rows_exact_in_fp32<PolyWC6>() &&
+                  rows_exact_in_fp32<PolyCubeIn>() && rows_exact_in_fp32<PolyCubeOut>() &&
+                  rows_exact_in_fp32<PolyCube>(),
+              "a scaled edge-sum row is not exact in FP32");
+static_assert(poly_den<PolyWC2>() == 315 && poly_den<PolyWC4>() == 57915 && poly_den<PolyCube>() == 105 &&
+                  poly_den<PolyWC6>() == 0,
+              "exact FP32 rows: unexpected scales");
 
 // compensated running sum for the FF / double-double paths: s + c, where every product
 // x*k is formed to ~2^-2p and every addition's rounding error goes into c (compensated
@@ -742,7 +843,7 @@ SPH2D_HD constexpr float slot_grid(int s) {
     ++n;
   }
   if (n == 0) return 1.0f;
-  const double need = 2.0 * n * m * (1.0 + 1.0 / 128);
+  const double need = 2.0 * n * m * poly_scale<P>() * (1.0 + 1.0 / 128);   // terms scaled by D_P
   double g = 1.0;
   while (g < need) g *= 2.0;
   while (g * 0.5 >= need) g *= 0.5;
@@ -843,14 +944,25 @@ struct AccFF {
   template <class P>
   SPH2D_HD static CSum<F> madd(CSum<F> acc, FFT<F> x, int row, int slot) {
 #if SPH2D_Q_UNROLL
-    const NumDen c = edge_coef_y<P>(row - 1, slot);
-    if (c.num == 0.0) return acc;
-    const FF k = ff_const(c.num / c.den);
-    return xsum_madd(acc, x, F(k.hi), F(k.lo));
+    if constexpr (poly_den<P>() > 0) {
+      const double k = edge_coef_s<P>(row - 1, slot);   // exact in FP32: no low word
+      if (k == 0.0) return acc;
+      return xsum_madd(acc, x, F(float(k)), F(0));
+    } else {
+      const NumDen c = edge_coef_y<P>(row - 1, slot);
+      if (c.num == 0.0) return acc;
+      const FF k = ff_const(c.num / c.den);
+      return xsum_madd(acc, x, F(k.hi), F(k.lo));
+    }
 #else
     const EdgeRows<P>& r = edge_rows<P>();
-    if (r.fhi[row][slot] == 0.0f) return acc;        // uniform across the warp
-    return xsum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]));
+    if constexpr (poly_den<P>() > 0) {
+      if (r.fs[row][slot] == 0.0f) return acc;       // uniform across the warp
+      return xsum_madd(acc, x, F(r.fs[row][slot]), F(0));
+    } else {
+      if (r.fhi[row][slot] == 0.0f) return acc;
+      return xsum_madd(acc, x, F(r.fhi[row][slot]), F(r.flo[row][slot]));
+    }
 #endif
   }
   SPH2D_HD static CSum<F> maddc(CSum<F> acc, FFT<F> x, double num, double den) {
@@ -983,20 +1095,22 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
 #define SPH2D_BR(F1, FA, F2, FB) (((F1) - (FA)) + ((FB) - (F2)))
   const R I_c = SPH2D_BR(s1, sA, s2, sB);                // int cos u
   const R I_s = SPH2D_BR(cA, c1, cB, c2);                // int sin u = [-cos u]
-  constexpr double k2 = kappa<P>(2);
-  constexpr double kg = kappa_grad<P>();
+  // the FP32 path with exact rows runs the fan times D_P (undone in tri_poly)
+  constexpr double DS = AccSel<R, P, PLAIN>::type::SCALED ? poly_scale<P>() : 1.0;
+  constexpr double k2 = kappa<P>(2) * DS;
+  constexpr double kg = kappa_grad<P>() * DS;
   R eg = R(k2) * dus;                                    // gamma (edge frame = any frame)
   R en = R(kg) * I_c;                                    // gradient along n
   R et = R(kg) * I_s;                                    // gradient along e2
   R E[10];                                               // edge-frame moments s^j t^l
   if (MD >= 1) {
-    constexpr double k3 = kappa<P>(3);
+    constexpr double k3 = kappa<P>(3) * DS;
     E[0] = eg;
     E[1] = R(k3) * I_c;                                  // s
     E[2] = R(k3) * I_s;                                  // t
   }
   if (MD >= 3) {
-    constexpr double k4 = kappa<P>(4), k5 = kappa<P>(5);
+    constexpr double k4 = kappa<P>(4) * DS, k5 = kappa<P>(5) * DS;
     const R scA = sA * cA, sc1 = s1 * c1, sc2 = s2 * c2, scB = sB * cB;
     const R I_sc = SPH2D_BR(sc1, scA, sc2, scB);         // [s c]
     const R I_ss = SPH2D_BR(s1 * s1, sA * sA, s2 * s2, sB * sB);
@@ -1163,11 +1277,16 @@ SPH2D_HD void add_fan(R ax, R ay, R bx, R by, PairOut<R>& o) {
 // signed sum over the three fans of one local-frame triangle, single polynomial piece
 template <typename R, class P, int MD, bool UNROLL_FANS, bool PLAIN = false>
 SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
+  using AC = typename AccSel<R, P, PLAIN>::type;
+  constexpr bool SC = AC::SCALED && poly_den<P>() > 1;   // fans computed times D_P
+  PairOut<R> t;
+  PairOut<R>& dst = SC ? t : o;
+  if constexpr (SC) clear(t);
   R x0 = ax, y0 = ay, x1 = bx, y1 = by, x2 = cx, y2 = cy;
   if constexpr (UNROLL_FANS) {
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      add_fan<R, P, MD, PLAIN>(x0, y0, x1, y1, o);
+      add_fan<R, P, MD, PLAIN>(x0, y0, x1, y1, dst);
       const R tx = x0, ty = y0;
       x0 = x1;
       y0 = y1;
@@ -1179,7 +1298,7 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
   } else {
 #pragma unroll 1
     for (int e = 0; e < 3; ++e) {
-      add_fan<R, P, MD, PLAIN>(x0, y0, x1, y1, o);
+      add_fan<R, P, MD, PLAIN>(x0, y0, x1, y1, dst);
       const R tx = x0, ty = y0;
       x0 = x1;
       y0 = y1;
@@ -1188,6 +1307,16 @@ SPH2D_HD void tri_poly(R ax, R ay, R bx, R by, R cx, R cy, PairOut<R>& o) {
       x2 = tx;
       y2 = ty;
     }
+  }
+  if constexpr (SC) {
+    constexpr double inv = 1.0 / poly_scale<P>();
+    const R f = R(inv);
+    o.g += f * t.g;
+    o.gx += f * t.gx;
+    o.gy += f * t.gy;
+    constexpr int NM = MD >= 3 ? 10 : (MD >= 1 ? 3 : 0);
+#pragma unroll
+    for (int i = 0; i < NM; ++i) o.m[i] += f * t.m[i];
   }
 }
 

@@ -25,7 +25,7 @@ using namespace sph2d;
 template <class P>
 static void grids(const char* name) {
   for (int s = 0; s < NSL; ++s) {
-    std::printf("G %s %d %a %d", name, s, double(slot_grid<P>(s)), int(slot_uses_drho(s)));
+    std::printf("G %s %d %a %d %a", name, s, double(slot_grid<P>(s)), int(slot_uses_drho(s)), poly_scale<P>());
     for (int q = -1; q <= P::K + 4; ++q) {
       const NumDen c = edge_coef<P>(q, s);
       if (c.num != 0.0) std::printf(" %d:%a:%a", q, c.num, c.den);
@@ -33,6 +33,13 @@ static void grids(const char* name) {
     std::printf("\n");
   }
   std::printf("M %s %d\n", name, int(uses_row_m1<P>()));
+  std::printf("D %s %lld\n", name, poly_den<P>());
+  for (int q = -1; q <= P::K + 4; ++q)
+    for (int s = 0; s < NSL; ++s) {
+      const NumDen c = edge_coef_y<P>(q, s);
+      if (c.num != 0.0)
+        std::printf("E %s %d %d %a %a\n", name, q, s, double(float(edge_coef_s<P>(q, s))), c.num / c.den);
+    }
 }
 
 int main() {
@@ -95,12 +102,12 @@ def is_pow2(v):
 def test_slot_grids_bound_their_terms(lines):
     """every slot's grid g is a power of two with g >= 2 n m and g < 4 n m (1 + 2^-7), where n
     counts the non-zero rows and m is the largest |coefficient| times its input bound (1 for
-    Delta J_q, q for Delta rho^q)"""
+    Delta J_q, q for Delta rho^q) times the polynomial's FP32 scale D_P"""
     rows = [l.split() for l in lines if l.startswith("G ")]
     assert len(rows) == 4 * 12
     for r in rows:
-        g, drho = float.fromhex(r[3]), r[4] == "1"
-        terms = [t.split(":") for t in r[5:]]
+        g, drho, scale = float.fromhex(r[3]), r[4] == "1", float.fromhex(r[5])
+        terms = [t.split(":") for t in r[6:]]
         if not terms:
             continue
         n = len(terms)
@@ -109,7 +116,7 @@ def test_slot_grids_bound_their_terms(lines):
             q = int(q)
             w = abs(float.fromhex(num)) / float.fromhex(den) * (q if drho and q > 1 else 1)
             m = max(m, w)
-        need = 2 * n * m
+        need = 2 * n * m * scale                        # the FP32 rows run times D_P
         assert is_pow2(g), r
         assert g >= need, r
         assert g < 2 * need * (1 + 2 ** -7), r
@@ -163,3 +170,66 @@ def test_pow2_scale(lines):
             assert 0.5 <= abs(x) * s < 1.0, (x, s)
         else:
             assert abs(x) * s < 1.0, (x, s)
+
+
+# kernel polynomials k(q) = sum_k b_k q^k from their factored definitions (Wendland C2, C4, C6
+# and the cubic spline's (1 - q)^3 piece), in exact rationals
+def _poly_mul(a, b):
+    out = [Fraction(0)] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        for j, y in enumerate(b):
+            out[i + j] += x * y
+    return out
+
+
+def _poly_pow(a, n):
+    out = [Fraction(1)]
+    for _ in range(n):
+        out = _poly_mul(out, a)
+    return out
+
+
+_ONE_MINUS_Q = [Fraction(1), Fraction(-1)]
+POLYS = {
+    "wc2": _poly_mul(_poly_pow(_ONE_MINUS_Q, 4), [Fraction(1), Fraction(4)]),
+    "wc4": _poly_mul(_poly_pow(_ONE_MINUS_Q, 6), [Fraction(1), Fraction(6), Fraction(35, 3)]),
+    "wc6": _poly_mul(_poly_pow(_ONE_MINUS_Q, 8), [Fraction(1), Fraction(8), Fraction(25), Fraction(32)]),
+    "cube": _poly_pow(_ONE_MINUS_Q, 3),
+}
+
+
+def _odd(v):
+    v = abs(v)
+    while v and v % 2 == 0:
+        v //= 2
+    return v
+
+
+def test_exact_fp32_rows(lines):
+    """the FP32 path's scaled rows: D_P is the odd part of the least common multiple of the row
+    denominators, every scaled entry is exactly D_P times the row's rational value (so exact in
+    FP32, no low word), and D_P is 0 (float-pair rows kept) exactly where some scaled numerator
+    would need more than 24 bits (Wendland C6)"""
+    den = {l.split()[1]: int(l.split()[2]) for l in lines if l.startswith("D ")}
+    assert set(den) == set(POLYS)
+    for name, b in POLYS.items():
+        rows = [l.split() for l in lines if l.startswith("E " + name + " ")]
+        assert rows
+        vals = []
+        for r in rows:
+            v = Fraction(float.fromhex(r[5])).limit_denominator(10 ** 9)
+            assert abs(float(v) - float.fromhex(r[5])) <= 1e-15 * abs(float(v))
+            vals.append((int(r[2]), int(r[3]), v, float.fromhex(r[4])))
+        lcm = 1
+        for _, _, v, _ in vals:
+            lcm = lcm * _odd(v.denominator) // math.gcd(lcm, _odd(v.denominator))
+        fits = all(_odd((v * lcm).numerator) < 2 ** 24 for _, _, v, _ in vals)
+        assert den[name] == (lcm if fits else 0), name
+        # the leading row of gamma (q = 0, slot 0): b_0 / 2 of the factored polynomial
+        g0 = [v for q, s, v, _ in vals if q == 0 and s == 0]
+        assert g0 == [b[0] / 2], name
+        for q, s, v, scaled in vals:
+            if den[name] == 0:
+                assert scaled == 0.0
+            else:
+                assert Fraction(scaled) == v * den[name], (name, q, s)
