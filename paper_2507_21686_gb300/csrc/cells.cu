@@ -285,14 +285,14 @@ __device__ __noinline__ bool keep_exact(double px, double py, const float* __res
   return best < H2;
 }
 
-// FP32 screen: returns 1 keep, 0 reject, -1 undecided (caller runs keep_exact)
-__device__ __forceinline__ int keep_screen(float px, float py, const float* __restrict__ t, float Hf,
+// FP32 screen: returns 1 keep, 0 reject, -1 undecided (caller runs keep_exact); v the vertices
+__device__ __forceinline__ int keep_screen(float px, float py, const float* v, float Hf,
                                            float H2lo, float H2hi) {
   float x[3], y[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    x[j] = __ldg(t + 2 * j);
-    y[j] = __ldg(t + 2 * j + 1);
+    x[j] = v[2 * j];
+    y[j] = v[2 * j + 1];
   }
   float best = FLT_MAX, wmax = 0.0f;
   bool pos_sure = false, neg_sure = false, all_pos = true, all_neg = true;
@@ -383,12 +383,24 @@ __global__ void cull_kernel(CullArgs a, const float4* __restrict__ parts, int64_
   const int64_t s = cell_start[c], e = cell_start[c + 1];
   int32_t* out = kept + cand_off[i];
   int64_t n = 0;
+  // software pipeline: the next candidate's id and vertices load while this one is screened
+  int32_t t = s < e ? __ldg(cell_tris + s) : 0;
+  int32_t t1 = s + 1 < e ? __ldg(cell_tris + s + 1) : 0;
+  float v[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) v[j] = s < e ? __ldg(tris + 6 * int64_t(t) + j) : 0.0f;
   for (int64_t k = s; k < e; ++k) {
-    const int32_t t = __ldg(cell_tris + k);
-    const float* tp = tris + 6 * int64_t(t);
-    int r = keep_screen(p.x, p.y, tp, a.Hf, a.H2lo, a.H2hi);
-    if (r < 0) r = keep_exact(double(p.x), double(p.y), tp, a.H2) ? 1 : 0;
+    const int32_t t2 = k + 2 < e ? __ldg(cell_tris + k + 2) : 0;
+    float vn[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) vn[j] = k + 1 < e ? __ldg(tris + 6 * int64_t(t1) + j) : 0.0f;
+    int r = keep_screen(p.x, p.y, v, a.Hf, a.H2lo, a.H2hi);
+    if (r < 0) r = keep_exact(double(p.x), double(p.y), tris + 6 * int64_t(t), a.H2) ? 1 : 0;
     if (r) out[n++] = t;
+    t = t1;
+    t1 = t2;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = vn[j];
   }
   counts[i] = n;
 }
