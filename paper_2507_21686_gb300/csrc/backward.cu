@@ -279,7 +279,8 @@ sph2d_status launch_backward(Ctx* c, int kernel, int mode, const void* d_gamma, 
     e = cudaMemsetAsync(cnt, 0, size_t(M) * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     SPH2D_LAUNCH(c, (tri_pair_fill_kernel), pb, 256, ptri, P, toff, cnt, tq);
-    launch_sort_segments(c, toff, tq, M);
+    s = launch_sort_segments(c, toff, tq, M);
+    if (s != SPH2D_OK) return s;
     // vertex gradients: segmented per-triangle sums over the transposed list
     s = ensure(c, c->host_flags_dev, 64);
     if (s != SPH2D_OK) return s;

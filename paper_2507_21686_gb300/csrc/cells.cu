@@ -186,11 +186,14 @@ __device__ __forceinline__ void warp_bitonic(int32_t* __restrict__ d, int64_t n,
   for (int r = 0; r < E; ++r)
     if (lane + 32 * r < n) d[lane + 32 * r] = a[r];
 }
-__global__ void sort_small_kernel(const int64_t* __restrict__ start, int32_t* __restrict__ data, int64_t nseg) {
+// (long: set to 1 when some list is longer than kWarpSortMax, for sort_cells_kernel)
+__global__ void sort_small_kernel(const int64_t* __restrict__ start, int32_t* __restrict__ data, int64_t nseg,
+                                  unsigned int* __restrict__ long_flag) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; c < nseg; c += nw) {
     const int64_t s = start[c], n = start[c + 1] - s;   // warp-uniform
+    if (n > kWarpSortMax && lane == 0) *long_flag = 1u;
     if (n <= 1 || n > kWarpSortMax) continue;
     if (n <= 64) warp_bitonic<2>(data + s, n, lane);
     else if (n <= 128) warp_bitonic<4>(data + s, n, lane);
@@ -203,8 +206,9 @@ __global__ void sort_small_kernel(const int64_t* __restrict__ start, int32_t* __
 // ids), else insertion sort
 constexpr int kSortCap = 4096;
 __global__ void sort_cells_kernel(const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_tris,
-                                  int64_t n_cells) {
+                                  int64_t n_cells, const unsigned int* __restrict__ long_flag) {
   __shared__ int32_t buf[kSortCap];
+  if (*long_flag == 0u) return;                 // no list longer than kWarpSortMax (block-uniform)
   for (int64_t c = blockIdx.x; c < n_cells; c += gridDim.x) {
     const int64_t s = cell_start[c], n = cell_start[c + 1] - s;
     if (n <= kWarpSortMax) continue;
@@ -439,12 +443,18 @@ __global__ void pair_copy_kernel(int64_t N, const int64_t* __restrict__ cand_off
 
 // sort the int32 segments data[start[i] .. start[i+1]) ascending (used for cell lists and,
 // by the adjoint, for per-triangle particle lists)
-void launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg) {
-  if (nseg <= 0) return;
+sph2d_status launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg) {
+  if (nseg <= 0) return SPH2D_OK;
+  sph2d_status s = ensure(c, c->sort_flag, 256);
+  if (s != SPH2D_OK) return s;
+  auto* flag = static_cast<unsigned int*>(c->sort_flag.ptr);
+  const cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "memset");
   const int64_t wblocks = (nseg + 7) / 8;                 // 8 warps of 256 threads per block
-  SPH2D_LAUNCH(c, (sort_small_kernel), unsigned(wblocks < 65535 ? wblocks : 65535), 256, start, data, nseg);
+  SPH2D_LAUNCH(c, (sort_small_kernel), unsigned(wblocks < 65535 ? wblocks : 65535), 256, start, data, nseg, flag);
   const int blocks = nseg < 1216 ? int(nseg) : 1216;     // the few long lists
-  SPH2D_LAUNCH(c, (sort_cells_kernel), blocks, 256, start, data, nseg);
+  SPH2D_LAUNCH(c, (sort_cells_kernel), blocks, 256, start, data, nseg, flag);
+  return SPH2D_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -574,7 +584,8 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
   if (e != cudaSuccess) return cuda_err(c, e, "memset");
   auto* ctris = static_cast<int32_t*>(c->cell_tris.ptr);
   SPH2D_LAUNCH(c, (tri_fill_kernel), tblocks, kBlock, g, tris, M, cstart, ccount, ctris);
-  launch_sort_segments(c, cstart, ctris, C);
+  s = launch_sort_segments(c, cstart, ctris, C);
+  if (s != SPH2D_OK) return s;
 
   // ---- 3. cull: each particle's candidates once into a scratch segment, then scan and copy
   CullArgs a;

@@ -95,7 +95,8 @@ static sph2d_status ensure_particle_grid(Ctx* c) {
     if (e != cudaSuccess) return cuda_err(c, e, "memset");
     SPH2D_LAUNCH(c, part_fill_kernel, unsigned((N + 255) / 256), 256, g, parts, N, cnt,
                  static_cast<int32_t*>(c->part_ids.ptr));
-    launch_sort_segments(c, static_cast<const int64_t*>(c->part_start.ptr), static_cast<int32_t*>(c->part_ids.ptr), C);
+    s = launch_sort_segments(c, static_cast<const int64_t*>(c->part_start.ptr), static_cast<int32_t*>(c->part_ids.ptr), C);
+    if (s != SPH2D_OK) return s;
   } else if (C >= 0) {
     cudaError_t e = cudaMemsetAsync(c->part_start.ptr, 0, size_t(C + 1) * sizeof(int64_t), c->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "memset");

@@ -198,7 +198,7 @@ sph2d_status sph2d_destroy(sph2d_ctx* h) {
                     &c.host_flags_dev, &c.misc, &c.tri_off, &c.tri_pid, &c.tri_cursor,
                     &c.bwd_g, &c.bwd_grad, &c.pair_vals, &c.pair_list2, &c.sur_prm, &c.sur_split, &c.sur_act,
                     &c.sur_data, &c.sur_idx, &c.sur_vals, &c.sur_fb, &c.part_start, &c.part_cursor,
-                    &c.part_ids, &c.pres_vertex, &c.pres_tmp, &c.cand_off, &c.cand_kept};
+                    &c.part_ids, &c.pres_vertex, &c.pres_tmp, &c.cand_off, &c.cand_kept, &c.sort_flag};
   for (DevBuf* b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c.pinned) cudaFreeHost(c.pinned);

@@ -48,6 +48,7 @@ struct Ctx {
   DevBuf part_start, part_cursor, part_ids, pres_vertex, pres_tmp;
   // single-pass cull: per-particle candidate offsets and the compacted kept triangles
   DevBuf cand_off, cand_kept;
+  DevBuf sort_flag;            // set when a sorted segment is too long for the warp sort
   int64_t* pinned = nullptr;   // small pinned host staging area (64 int64)
   bool fixup_pending = false;  // pinned[8] holds the fix-up count of the last integral call
   bool fallback_pending = false;  // pinned[10..14]: fallback count, audit and MMA timeouts of the last surrogate call
@@ -75,7 +76,7 @@ sph2d_status build_cells(Ctx* c, const float* particles, int64_t N, const float*
                          int64_t M, double H);
 
 // ascending sort of int32 segments (cells.cu)
-void launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg);
+sph2d_status launch_sort_segments(Ctx* c, const int64_t* start, int32_t* data, int64_t nseg);
 
 // forward integrals over the context's pair list (integrals.cu)
 sph2d_status launch_integrals(Ctx* c, int kernel, int moment_degree, int mode, void* gamma,
