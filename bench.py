@@ -164,8 +164,7 @@ KERNEL_LAUNCHES = {
     "wendland_c2": "integrals_kernel<float,wendland_c2,moments> + finalize_kernel",
     "wendland_c4": "integrals_kernel<float,wendland_c4,moments> + finalize_kernel",
     "wendland_c6": "integrals_kernel<float,wendland_c6,moments> + finalize_kernel",
-    "cubic_spline": ("cubic_near_mask_kernel + scan + cubic_partition_kernel + cubic_split_kernel + "
-                     "cubic_split_finalize_kernel (float, moments)"),
+    "cubic_spline": "cubic_batch_kernel + finalize_kernel (float, moments)",
 }
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic.json")
 

@@ -383,13 +383,9 @@ __global__ void __launch_bounds__(128, int_minb<OT, MD>()) integrals_kernel(IntA
 // support H/2 and is exactly zero for a triangle at distance >= H/2, which holds for most pairs;
 // evaluated in place it would still run on every lane of a warp that holds one near pair.
 //
-// Per-particle path (run_cubic): a stable partition of the pair list puts the pairs within H/2
-// of their triangle first and the others after them, each part in pair order.  One chunk kernel
-// runs over the partition: both pieces for a near pair (piece1 + piece2, in that order), the
-// first piece for a far pair, with the segmented sums and crossing slots of integrals_kernel
-// keyed by (particle, part).  The finalize adds each particle's near-part sum and far-part sum
-// in that order.  Every order is fixed, so results are deterministic run to run.  The hybrid
-// mode's closed-form pairs (few, mostly near) take the same pair function with a per-lane flag.
+// Per-particle path (run_cubic): cubic_batch_kernel below gathers the near pairs of several
+// chunks into full warp-wide rounds of second pieces.  The hybrid mode's closed-form pairs
+// (few, mostly near) take cubic_split_pair, both pieces in one lane, with a per-lane flag.
 // ---------------------------------------------------------------------------------------
 // origin within 1/2 (+ a small margin) of the local triangle: inside, or an edge segment
 // closer than that (no division)
@@ -772,35 +768,7 @@ static sph2d_status split_order(Ctx* c, const IntArgs& a, PairSplit& sp, const i
 // cubic spline over the near/far partition: region 0 the pairs within H/2 of their triangle
 // (both pieces), region 1 the others (the first piece only)
 // ---------------------------------------------------------------------------------------
-template <typename OT>
-__global__ void __launch_bounds__(128) cubic_near_mask_kernel(IntArgs a, PairSplit sp, uint32_t* __restrict__ mask,
-                                                              int64_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < sp.nchunks; ch += nw) {
-    const int64_t q = ch * 32 + lane;
-    int region = -1;
-    if (q < a.P) {
-      const float4 p = a.parts[__ldg(a.pair_pid + q)];
-      const float* t = a.tris + 6 * int64_t(__ldg(a.pair_tri + q));
-      OT l[6];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if constexpr (sizeof(OT) == sizeof(float)) {
-          l[2 * j] = (__ldg(t + 2 * j) - p.x) * float(a.invH);
-          l[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * float(a.invH);
-        } else {
-          l[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
-          l[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
-        }
-      }
-      region = near_half<OT>(l) ? 0 : 1;
-    }
-    store_region_masks(mask, cnt, sp.nchunks, 2, ch, region);
-  }
-}
-
-// one pair of the partition: the first piece, plus the second for a near pair; FP32 pairs whose
+// one pair: the first piece, plus the second for a near pair; FP32 pairs whose
 // coordinates leave the FP32 range or whose result is not finite take the whole kernel in FP64
 // (eval_fixup64, out of line).  Returns 1 for a fix-up.
 template <typename OT, int MD>
@@ -860,41 +828,246 @@ __device__ __forceinline__ int cubic_split_pair(const IntArgs& a, int pid, int t
   }
 }
 
-// The cubic spline's partition kernel runs at the Wendland kernels' cap.  With its pieces'
-// fans inlined it ran best at 3 blocks (168 registers); with the fans looped, 4 blocks measured
-// 6.5% faster than 3 with ten moments (3.41 -> 3.19 ms on the 1024^2 box), and later 5 blocks
-// as fast as 4 with ten moments and 7% faster without, spilling 148 bytes per thread.
+// The cubic spline's pair kernels run at the Wendland kernels' cap.  The earlier partition
+// kernel, with its pieces' fans inlined, ran best at 3 blocks (168 registers); with the fans
+// looped, 4 blocks measured 6.5% faster than 3 with ten moments, and later 5 blocks as fast as 4
+// with ten moments and 7% faster without.
 template <typename OT, int MD> constexpr int cubic_split_minb() { return int_minb<OT, MD>(); }
 
-// chunks of 32 positions of the near/far partition
+
+// ---------------------------------------------------------------------------------------
+// Single-pass cubic spline (run_cubic).  Each warp fills a batch with the chunks it takes
+// (32 consecutive pairs each, in the pair list's own order, at most kCubicBatch chunks) for as
+// long as their near pairs (within H/2 of their triangle: both pieces) number at most
+// kCubicNearCap.  Rounds over the batch's near pairs, one per lane, evaluate the second piece
+// into shared memory; then each chunk of the batch runs the first piece on every lane, adds a
+// near pair's second piece (piece1 + piece2, in that order) and sums per particle with the
+// segmented sums and crossing slots of integrals_kernel.  The near pairs of several chunks so share their
+// warp-wide rounds, the pair list is read in place and the per-particle sums are those of the
+// single-polynomial kernels (finalize_kernel).  Every order is fixed, so results are
+// deterministic run to run.
+// ---------------------------------------------------------------------------------------
+constexpr int kCubicBatch = 8, kCubicNearCap = 64;
+
+// bit position of the n-th (from 0) set bit of m; m has more than n set bits
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const unsigned low = m & ((1u << w) - 1u);
+    const int c = __popc(low);
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = low;
+    }
+  }
+  return pos;
+}
+
+// local frame of pair (pid, tid) in the output precision; false if an FP32 coordinate leaves
+// the FP32 range (the pair then takes the FP64 fix-up)
+template <typename OT>
+__device__ __forceinline__ bool cubic_local(const IntArgs& a, int pid, int tid, OT* l) {
+  const float4 p = a.parts[pid];
+  const float* t = a.tris + 6 * int64_t(tid);
+  bool ok = true;
+  if constexpr (sizeof(OT) == sizeof(float)) {
+    const float ih = a.invHf != 0.0f ? a.invHf : float(a.invH);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      l[2 * j] = (__ldg(t + 2 * j) - p.x) * ih;
+      l[2 * j + 1] = (__ldg(t + 2 * j + 1) - p.y) * ih;
+      ok = ok && fabsf(l[2 * j]) <= kFixupCoordLimit && fabsf(l[2 * j + 1]) <= kFixupCoordLimit;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      l[2 * j] = (double(__ldg(t + 2 * j)) - double(p.x)) * a.invH;
+      l[2 * j + 1] = (double(__ldg(t + 2 * j + 1)) - double(p.y)) * a.invH;
+    }
+  }
+  return ok;
+}
+
+// one piece of a pair from its local frame (zeros for a degenerate triangle)
 template <typename OT, int MD>
-__global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_split_kernel(IntArgs a, PairSplit sp) {
+__device__ __forceinline__ void cubic_piece_pair(const IntArgs& a, const OT* l, int piece, OT* v) {
+  constexpr int NV = nv_of(MD);
+  const int s = tri_orientation<OT>(l[0], l[1], l[2], l[3], l[4], l[5]);
+  if (s == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = OT(0);
+    return;
+  }
+  if constexpr (sizeof(OT) == sizeof(float)) {
+    const float ih = a.invHf != 0.0f ? a.invHf : float(a.invH), cf = a.Cf != 0.0f ? a.Cf : float(a.C);
+    float w[13];
+    cubic_piece<float, MD>(l, piece, s, cf, ih, w);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = w[i];
+  } else {
+    double w[13];
+    cubic_piece<double, MD>(l, piece, s, a.C, a.invH, w);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = w[i];
+  }
+}
+
+// near flags of chunk ch (bit l: pair 32 ch + l is within H/2 of its triangle)
+template <typename OT>
+__device__ __forceinline__ unsigned cubic_near_flags(const IntArgs& a, int64_t ch) {
+  const int64_t q = ch * 32 + (threadIdx.x & 31);
+  bool near = false;
+  if (q < a.P) {
+    OT l[6];
+    cubic_local<OT>(a, __ldg(a.pair_pid + q), __ldg(a.pair_tri + q), l);
+    near = near_half<OT>(l);
+  }
+  return __ballot_sync(0xffffffffu, near);
+}
+
+// the segmented per-particle sums of one chunk (pid -1 for a lane past the list), as in
+// integrals_kernel: a particle held in the chunk is written by the head lane of its segment,
+// the chunk's first and last segments go to its two crossing slots
+template <typename OT, int MD>
+__device__ __forceinline__ void chunk_particle_sums(const IntArgs& a, int64_t ch, int pid, OT* v) {
   constexpr int NV = nv_of(MD);
   const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int pn = __shfl_down_sync(0xffffffffu, pid, o);
+    const bool same = (lane + o < 32) && (pn == pid);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const OT t = __shfl_down_sync(0xffffffffu, v[i], o);
+      if (same) v[i] += t;
+    }
+  }
+  const int pprev = __shfl_up_sync(0xffffffffu, pid, 1);
+  const bool head = pid >= 0 && (lane == 0 || pprev != pid);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const int last_head = 31 - __clz(heads);
+  if (head) {
+    const int64_t cs = ch * 32;
+    const int64_t s0 = __ldg(a.pair_off + pid), s1 = __ldg(a.pair_off + pid + 1);
+    if (s0 >= cs && s1 <= cs + 32) write_particle<OT, MD>(a, pid, v);
+    OT* slots = static_cast<OT*>(a.slots);
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) slots[(ch * 2) * NV + i] = v[i];
+    }
+    if (lane == last_head) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) slots[(ch * 2 + 1) * NV + i] = v[i];
+    }
+  }
+}
+
+template <typename OT, int MD>
+__global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_batch_kernel(IntArgs a) {
+  constexpr int NV = nv_of(MD);
+  __shared__ OT s_w2[4][kCubicNearCap][NV];          // second pieces of the batch's near pairs
+  __shared__ int64_t s_ch[4][kCubicBatch];
+  __shared__ unsigned s_mask[4][kCubicBatch];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t nchunks = (a.P + 31) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int64_t pn = sp.off[sp.nchunks];             // first far position
   unsigned long long fixes = 0;
-  for (int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; ch < nchunks;) {
-    const unsigned long long nx = chunk_prefetch(a.work);
-    const int64_t i = ch * 32 + lane;
-    bool valid = false;
-    unsigned key = 0;                                // 2 pid + part: below 2^32 for any int32 pid
-    OT v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = OT(0);
-    int fix = 0;
-    if (i < a.P) {
-      const int64_t q = sp.order[i];
-      const int pid = __ldg(a.pair_pid + q);
-      const bool near = i < pn;
-      valid = true;
-      key = 2u * unsigned(pid) + (near ? 0u : 1u);
-      fix = cubic_split_pair<OT, MD>(a, pid, __ldg(a.pair_tri + q), near, v);
+  int64_t carry = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;   // taken, not yet batched
+  unsigned long long nx = 0;
+  unsigned cmask = 0;
+  if (carry < nchunks) {
+    nx = chunk_prefetch(a.work);
+    cmask = cubic_near_flags<OT>(a, carry);
+  }
+  while (carry < nchunks) {
+    // fill the batch (warp-uniform): a single chunk never holds more than 32 near pairs
+    int k = 0, tot = 0;
+    while (carry < nchunks && k < kCubicBatch && tot + __popc(cmask) <= kCubicNearCap) {
+      if (lane == 0) {
+        s_ch[wib][k] = carry;
+        s_mask[wib][k] = cmask;
+      }
+      tot += __popc(cmask);
+      ++k;
+      carry = chunk_next(a.work, carry, nw, nx);
+      if (carry < nchunks) {
+        nx = chunk_prefetch(a.work);
+        cmask = cubic_near_flags<OT>(a, carry);
+      }
     }
-    fixes += __popc(__ballot_sync(0xffffffffu, fix));
-    keyed_chunk_sums<OT, NV, 2, unsigned>(a, sp, ch, valid, key, v);
-    ch = chunk_next(a.work, ch, nw, nx);
+    __syncwarp();
+    // rounds r < n2: lane l takes the second piece of the batch's near pair j = 32 r + l; round
+    // n2 + i: the first piece of every pair of the batch's chunk i, plus its second piece, and
+    // the sums.  One call site for both pieces keeps one copy of the piece code.
+    const int n2 = (tot + 31) >> 5;
+    int base = 0;
+#pragma unroll 1
+    for (int r = 0; r < n2 + k; ++r) {
+      int64_t q = -1;
+      unsigned m = 0;
+      const int j2 = 32 * r + lane;
+      if (r < n2) {
+        if (j2 < tot) {
+          int i = 0, b = 0;
+          while (b + __popc(s_mask[wib][i]) <= j2) {
+            b += __popc(s_mask[wib][i]);
+            ++i;
+          }
+          q = s_ch[wib][i] * 32 + nth_set_bit(s_mask[wib][i], j2 - b);
+        }
+      } else {
+        m = s_mask[wib][r - n2];
+        q = s_ch[wib][r - n2] * 32 + lane;
+        if (q >= a.P) q = -1;
+      }
+      int pid = -1, tid = 0;
+      bool ok = true;
+      OT v[NV];
+#pragma unroll
+      for (int x = 0; x < NV; ++x) v[x] = OT(0);
+      if (q >= 0) {
+        pid = __ldg(a.pair_pid + q);
+        tid = __ldg(a.pair_tri + q);
+        OT l[6];
+        ok = cubic_local<OT>(a, pid, tid, l);
+        if (ok) cubic_piece_pair<OT, MD>(a, l, r < n2 ? 1 : 0, v);
+      }
+      if (r < n2) {
+        if (q >= 0) {
+#pragma unroll
+          for (int x = 0; x < NV; ++x) s_w2[wib][j2][x] = ok ? v[x] : OT(NAN);   // NaN: the owner's fix-up
+        }
+        __syncwarp();
+        continue;
+      }
+      int fix = 0;
+      if (q >= 0) {
+        if (ok && ((m >> lane) & 1u)) {
+          const int j = base + __popc(m & ((1u << lane) - 1u));
+#pragma unroll
+          for (int x = 0; x < NV; ++x) v[x] += s_w2[wib][j][x];
+        }
+        if constexpr (sizeof(OT) == sizeof(float)) {
+#pragma unroll
+          for (int x = 0; x < NV; ++x) ok = ok && isfinite(v[x]);
+          if (!ok) {
+            float w[13];
+            eval_fixup64<KID_CUBIC, MD>(a.parts[pid], a.tris + 6 * int64_t(tid), a.invH, a.C, w);
+#pragma unroll
+            for (int x = 0; x < NV; ++x) v[x] = OT(w[x]);
+            fix = 1;
+          }
+        }
+      }
+      base += __popc(m);
+      fixes += __popc(__ballot_sync(0xffffffffu, fix));
+      chunk_particle_sums<OT, MD>(a, s_ch[wib][r - n2], pid, v);
+    }
+    __syncwarp();
   }
   if (lane == 0 && fixes) atomicAdd(a.nfix, fixes);
 }
@@ -939,25 +1112,14 @@ __global__ void __launch_bounds__(256) pair_entry_kernel(const double* __restric
 template <typename OT, int MD>
 static sph2d_status run_cubic(Ctx* c, IntArgs a) {
   constexpr int NV = nv_of(MD);
-  PairSplit sp;
-  int64_t* cnt;
-  unsigned long long* hdr;
-  unsigned char* extra;
-  sph2d_status s = split_scratch<OT>(c, a, 2, NV, 0, sp, cnt, hdr, extra);
+  const int64_t nchunks = (a.P + 31) >> 5;
+  sph2d_status s = ensure(c, c->slots, size_t(nchunks * 2 * NV + 1) * sizeof(OT));
   if (s != SPH2D_OK) return s;
   a.slots = c->slots.ptr;
-  if (a.P > 0) {
-    cudaError_t e = cudaMemsetAsync(hdr, 0, 64, c->stream);
-    if (e != cudaSuccess) return cuda_err(c, e, "memset");
-    a.work = hdr + 4;
-    SPH2D_LAUNCH(c, (cubic_near_mask_kernel<OT>), resident_blocks(c, cubic_near_mask_kernel<OT>, (sp.nchunks + 3) / 4),
-                 128, a, sp, const_cast<uint32_t*>(sp.mask), cnt);
-    s = split_order(c, a, sp, cnt);
-    if (s != SPH2D_OK) return s;
-    SPH2D_LAUNCH(c, (cubic_split_kernel<OT, MD>),
-                 resident_blocks(c, cubic_split_kernel<OT, MD>, (sp.nchunks + 3) / 4), 128, a, sp);
-  }
-  if (a.N > 0) SPH2D_LAUNCH(c, (split_finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a, sp);
+  if (a.P > 0)
+    SPH2D_LAUNCH(c, (cubic_batch_kernel<OT, MD>),
+                 resident_blocks(c, cubic_batch_kernel<OT, MD>, (nchunks + 3) / 4), 128, a);
+  if (a.N > 0) SPH2D_LAUNCH(c, (finalize_kernel<OT, MD>), unsigned((a.N + 255) / 256), 256, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(c, e, "integrals launch");
   return SPH2D_OK;

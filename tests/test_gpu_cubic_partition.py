@@ -1,9 +1,12 @@
-"""The cubic spline's per-particle path partitions the pair list into the pairs within H/2 of
-their triangle (both pieces of k = 2 (1-q)^3_+ - (1-2q)^3_+) and the others (first piece only),
-then adds each particle's two part sums.  These cases put the partition's boundaries where they
-can go wrong: every pair near, every pair far, a pair count that is an exact multiple of the
-32-pair chunk, near and far parts that alternate particle by particle, and a particle whose near
-and far parts each span several chunks.  Expected values come from the oracle."""
+"""The cubic spline's per-particle path treats the pairs within H/2 of their triangle (both
+pieces of k = 2 (1-q)^3_+ - (1-2q)^3_+) apart from the others (first piece only): its batch
+kernel gathers the near pairs of several 32-pair chunks into warp-wide rounds of second pieces
+and adds each near pair's second piece to its first.  These cases put the boundaries where they
+can go wrong: every pair near (one chunk per batch), every pair far (no second-piece round), a
+pair count that is an exact multiple of the 32-pair chunk, near and far pairs that alternate
+particle by particle, a particle whose near and far pairs each span several chunks, and chunks
+whose near pairs exactly fill a round, overflow it by one or leave one lane.  Expected values
+come from the oracle."""
 from __future__ import annotations
 
 import numpy as np
@@ -139,3 +142,20 @@ def test_parts_spanning_chunks(ctx, mode):
     near, far = check_parts(parts[:1], tris, 1.0, None, None)
     assert near > 64 and far > 64
     compare_particles(ctx, parts, tris, 1.0, "cubic_spline", 3, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("per_chunk", [16, 17, 31])
+def test_near_pairs_filling_the_second_piece_rounds(ctx, mode, per_chunk):
+    """chunks of 32 pairs with a fixed number of near pairs each, so that the near pairs of two
+    chunks exactly fill one warp-wide round of second pieces (16), overflow it by one pair and
+    start the next batch (17), or leave one lane (31); 12 chunks, one pair per particle"""
+    rng = np.random.default_rng(95 + per_chunk)
+    xy = []
+    for _ in range(12):
+        near, far = ring(rng, per_chunk, 0.0, 0.4), ring(rng, 32 - per_chunk, 0.95, 1.0)
+        chunk = np.concatenate([near, far])
+        xy.append(chunk[rng.permutation(32)])
+    parts = parts_of(np.concatenate(xy))
+    check_parts(parts, TRI, 1.0, 12 * per_chunk, 12 * (32 - per_chunk))
+    compare_particles(ctx, parts, TRI.astype(np.float32), 1.0, "cubic_spline", 3, mode)
