@@ -849,21 +849,36 @@ def run_surrogate(ctx, dev, stream, flush, n=2048, train_pairs=8_000_000, reps=3
 
 
 def run_e2e(args, ctx, parts_h, tris_h, w, dev, stream, P, ws):
-    """Same metric through the public API: pinned host inputs copied in, results copied out."""
+    """Same metric through the public API: pinned host inputs copied in, results copied out.
+
+    Steps are pipelined as a serving loop would run them: a step's inputs go to the device on
+    their own stream while the previous step still computes, and each kernel's results go to
+    the host on a side stream while the next kernel (or the next step) runs.  Every step still
+    copies all of its inputs in and all of its results out inside the timed region; the host
+    results are double-buffered so that a step never overwrites the buffers that the previous
+    step's copies are still filling."""
     import torch
     N = parts_h.shape[0]
     nm = 10
-    outs_h = [(torch.empty(N, dtype=torch.float32).pin_memory(),
-               torch.empty((N, 2), dtype=torch.float32).pin_memory(),
-               torch.empty((N, nm), dtype=torch.float32).pin_memory()) for _ in KERNELS]
+    outs_h = [[(torch.empty(N, dtype=torch.float32).pin_memory(),
+                torch.empty((N, 2), dtype=torch.float32).pin_memory(),
+                torch.empty((N, nm), dtype=torch.float32).pin_memory()) for _ in KERNELS]
+              for _ in range(2)]
 
     copy_stream = torch.cuda.Stream(dev)
+    h2d_stream = torch.cuda.Stream(dev)
+    pending = []                      # device results whose copies may still be in flight
 
-    def e2e_step():
-        # each kernel's results go to the host on a side stream while the next kernel runs
+    def e2e_step(s):
         cur = torch.cuda.current_stream(dev)
-        p = parts_h.to(dev, non_blocking=True)
-        t = tris_h.to(dev, non_blocking=True)
+        with torch.cuda.stream(h2d_stream):
+            p = parts_h.to(dev, non_blocking=True)
+            t = tris_h.to(dev, non_blocking=True)
+        arrived = torch.cuda.Event()
+        arrived.record(h2d_stream)
+        cur.wait_event(arrived)
+        p.record_stream(cur)
+        t.record_stream(cur)
         res = []
         for i, k in enumerate(KERNELS):
             if i == 0:
@@ -875,25 +890,33 @@ def run_e2e(args, ctx, parts_h, tris_h, w, dev, stream, P, ws):
             done.record(cur)
             copy_stream.wait_event(done)
             with torch.cuda.stream(copy_stream):
-                for x, hx in zip(r, outs_h[i]):
+                for x, hx in zip(r, outs_h[s % 2][i]):
                     hx.copy_(x, non_blocking=True)
-        copy_stream.synchronize()
-        cur.synchronize()
+                    x.record_stream(copy_stream)
+        pending.append(res)
+        del pending[:-2]
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+    for s in range(max(1, args.warmup)):
+        e2e_step(s)
+    copy_stream.synchronize()
+    torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    for s in range(args.steps):
+        e2e_step(s)
+    copy_stream.synchronize()
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
+    pending.clear()
     agg = aggregate(P * len(KERNELS) * args.steps, secs * 1e3, ws, dev)
     h2d = parts_h.numel() * 4 + tris_h.numel() * 4
-    d2h = sum(x.numel() * 4 for o in outs_h for x in o)
+    d2h = sum(x.numel() * 4 for o in outs_h[0] for x in o)
     return {"value": agg["value"], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": secs * 1e3 / args.steps}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": secs * 1e3 / args.steps,
+            "pipelining": "inputs of step k+1 copied in on their own stream while step k computes; "
+                          "results copied out on a side stream, double-buffered on the host; every "
+                          "copy of every step inside the timed region"}
 
 
 def main():

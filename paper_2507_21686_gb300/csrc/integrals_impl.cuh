@@ -984,9 +984,12 @@ __global__ void __launch_bounds__(128, cubic_split_minb<OT, MD>()) cubic_batch_k
     cmask = cubic_near_flags<OT>(a, carry);
   }
   while (carry < nchunks) {
-    // fill the batch (warp-uniform): a single chunk never holds more than 32 near pairs
+    // fill the batch (warp-uniform): a single chunk never holds more than 32 near pairs.  Once
+    // fewer than two chunks per warp remain, a batch takes one chunk, so that the last batches
+    // end together
     int k = 0, tot = 0;
-    while (carry < nchunks && k < kCubicBatch && tot + __popc(cmask) <= kCubicNearCap) {
+    while (carry < nchunks && k < kCubicBatch && tot + __popc(cmask) <= kCubicNearCap &&
+           (k == 0 || nchunks - carry > 2 * nw)) {
       if (lane == 0) {
         s_ch[wib][k] = carry;
         s_mask[wib][k] = cmask;
