@@ -137,11 +137,14 @@ def test_wall_strip_all_outputs(ctx, kernel, mode):
     compare_particles(ctx, w.particles, w.triangles, w.H, kernel, 3, mode)
 
 
+@pytest.mark.parametrize("kernel", ["wendland_c4", "cubic_spline"])
 @pytest.mark.parametrize("deg", [-1, 0, 1, 2])
-def test_moment_degrees(ctx, deg):
+def test_moment_degrees(ctx, deg, kernel):
+    """every moment-degree instance (none, first moments, all ten) of a single-polynomial kernel
+    and of the cubic spline's batch kernel"""
     w = W.wall_strip()
     for mode in ("fp64", "fp32_fixup"):
-        compare_particles(ctx, w.particles, w.triangles, w.H, "wendland_c4", deg, mode)
+        compare_particles(ctx, w.particles, w.triangles, w.H, kernel, deg, mode)
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32_fixup"])
