@@ -743,8 +743,20 @@ def run_adjoint(ctx, dev, stream, flush, steps=3, modes=("fp32_fixup", "fp64")):
             e[1].record(stream)
             torch.cuda.synchronize()
             bw2.append(e[0].elapsed_time(e[1]))
+        # the training loop's form: forward, then the backward over the forward's pair list
+        bwp = []
+        for _ in range(steps):
+            flush.zero_()
+            g, _, _ = ctx.boundary_integrals(parts, tris, "wendland_c4", w.H, -1, mode)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            ctx.backward_from_pairs("wendland_c4", 2.0 * (g - gs), mode)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            bwp.append(e[0].elapsed_time(e[1]))
         out[mode] = {"pairs": P, "forward_ms": float(np.mean(fw)), "backward_ms": float(np.mean(bw)),
                      "backward_pairs_per_s": P / (np.mean(bw) / 1e3),
+                     "backward_from_pairs_ms": float(np.mean(bwp)),
                      "backward_second_order_ms": float(np.mean(bw2)),
                      "backward_second_order_pairs_per_s": P / (np.mean(bw2) / 1e3)}
     return out

@@ -239,6 +239,20 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* ctx, const float* part
                                                void* d_particles, void* d_tris);
 
 /*
+ * sph2d_boundary_integrals_backward over the pair list of the context's last build
+ * (sph2d_build_cells, sph2d_boundary_integrals or a backward call), without rebuilding it: a
+ * training loop's backward after its forward call skips the cull.  The particle and triangle
+ * arrays of that build must still hold the same data (as for sph2d_integrals_from_pairs).
+ * d_gamma [N], d_grad_gamma [N][2] or NULL, d_particles [N][2], d_tris [M][6] as in
+ * sph2d_boundary_integrals_backward, with N and M of the last build; results are identical to
+ * that call's on the same inputs.  Does not synchronise.
+ * Errors: NOT_BUILT, INVALID_ARG, UNSUPPORTED (surrogate and hybrid modes; more than
+ * 2^31 - 1 pairs), OUT_OF_MEMORY, CUDA.
+ */
+sph2d_status sph2d_backward_from_pairs(sph2d_ctx* ctx, int kernel, int mode, const void* d_gamma,
+                                       const void* d_grad_gamma, void* d_particles, void* d_tris);
+
+/*
  * Allocation-free integrals over a caller-supplied pair list (gamma and grad gamma).
  * The paper has no counterpart: this serves callers that cannot allocate device memory while
  * they run -- memory pools that forbid cudaMalloc inside a solver step, frameworks that own

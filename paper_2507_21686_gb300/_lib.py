@@ -57,6 +57,7 @@ SIGNATURES = {
     "sph2d_integrals_from_pairs": (_ST, [_P, _I, _I, _I, _P, _P, _P]),
     "sph2d_pair_integrals": (_ST, [_P, _P, _I64, _I, _D, _I, _I, _P]),
     "sph2d_boundary_integrals_backward": (_ST, [_P, _P, _I64, _P, _I64, _I, _D, _I, _P, _P, _P, _P]),
+    "sph2d_backward_from_pairs": (_ST, [_P, _I, _I, _P, _P, _P, _P]),
     "sph2d_pair_list_integrals_noalloc": (_ST, [_P, _I64, _P, _I64, _P, _P, _I64, _I, _D, _I, _P, _P, _P]),
     "sph2d_field_integrals": (_ST, [_P, _I, _I, _P, _I, _P, _P]),
     "sph2d_field_integrals_p": (_ST, [_P, _I, _I, _I, _P, _I, _P, _P]),

@@ -72,6 +72,7 @@ class Context:
         if st != 0:
             raise _lib.Sph2dError(st, "sph2d_init failed")
         self.h = h
+        self._builds = 0          # pair-list builds so far (a backward can reuse the latest)
 
     def close(self):
         if getattr(self, "h", None):
@@ -99,6 +100,7 @@ class Context:
         check(self.lib, self.h, self.lib.sph2d_build_cells(self.h, _ptr(p), p.shape[0], _ptr(t),
                                                             t.shape[0], float(H)))
         self._keep = (p, t)
+        self._builds += 1
         return self
 
     def pair_count(self) -> int:
@@ -144,6 +146,7 @@ class Context:
             self.h, _ptr(p), p.shape[0], _ptr(t), t.shape[0], _kernel_id(kernel), float(H),
             int(moment_degree), _mode_id(mode), _ptr(g), _ptr(gr), _ptr(mo)))
         self._keep = (p, t)
+        self._builds += 1
         if src.type != "cuda":
             g = g.to(src)
             gr = gr.to(src) if gr is not None else None
@@ -238,6 +241,25 @@ class Context:
         check(self.lib, self.h, self.lib.sph2d_boundary_integrals_backward(
             self.h, _ptr(p), p.shape[0], _ptr(t), t.shape[0], _kernel_id(kernel), float(H),
             _mode_id(mode), _ptr(dg), _ptr(dgr) if dgr is not None else None, _ptr(dp), _ptr(dtr)))
+        self._keep = (p, t)       # the rebuilt pair list points at these
+        self._builds += 1
+        return dp, dtr
+
+    def backward_from_pairs(self, kernel, d_gamma, mode="fp64", d_grad=None):
+        """As backward, over the pair list of the last build (no cull): dL/dx [N, 2] and
+        dL/dvertices [M, 6] of that build's particles and triangles."""
+        if getattr(self, "_keep", None) is None:
+            raise _lib.Sph2dError(4, "no pair list built")
+        n, m = self._keep[0].shape[0], self._keep[1].shape[0]
+        dt = torch.float64 if _mode_id(mode) == 0 else torch.float32
+        dg = d_gamma.to(device=self._dev(), dtype=dt).contiguous()
+        dgr = d_grad.to(device=self._dev(), dtype=dt).contiguous() if d_grad is not None else None
+        dp = torch.empty((n, 2), dtype=dt, device=self._dev())
+        dtr = torch.empty((m, 6), dtype=dt, device=self._dev())
+        self._bind_stream()
+        check(self.lib, self.h, self.lib.sph2d_backward_from_pairs(
+            self.h, _kernel_id(kernel), _mode_id(mode), _ptr(dg), _ptr(dgr) if dgr is not None else None,
+            _ptr(dp), _ptr(dtr)))
         return dp, dtr
 
     # -- learned surrogate -------------------------------------------------------------
@@ -363,9 +385,11 @@ class BoundaryGamma(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, particles, tris, kernel, H, mode):
-        g, gr, _ = context().boundary_integrals(particles, tris, kernel, H, -1, mode, True)
+        c = context()
+        g, gr, _ = c.boundary_integrals(particles, tris, kernel, H, -1, mode, True)
         ctx.save_for_backward(particles, tris)
         ctx.kernel, ctx.H, ctx.mode = kernel, H, mode
+        ctx.build = c._builds
         return g, gr
 
     @staticmethod
@@ -373,7 +397,13 @@ class BoundaryGamma(torch.autograd.Function):
         particles, tris = ctx.saved_tensors
         if d_gamma is None:
             d_gamma = torch.zeros(particles.shape[0], dtype=particles.dtype, device=particles.device)
-        dp, dt = context().backward(particles, tris, ctx.kernel, ctx.H, d_gamma, ctx.mode, d_grad)
+        c = context()
+        if c._builds == ctx.build:
+            # the context still holds this forward's pair list (saved tensors are checked for
+            # in-place changes by autograd): no second cull
+            dp, dt = c.backward_from_pairs(ctx.kernel, d_gamma, ctx.mode, d_grad)
+        else:
+            dp, dt = c.backward(particles, tris, ctx.kernel, ctx.H, d_gamma, ctx.mode, d_grad)
         gp = torch.zeros_like(particles)
         gp[:, :2] = dp.to(particles.dtype)
         return gp, dt.to(tris.dtype).reshape(tris.shape), None, None, None

@@ -393,6 +393,23 @@ sph2d_status sph2d_boundary_integrals_backward(sph2d_ctx* h, const float* partic
   return launch_backward(c, kernel, mode, d_gamma, d_grad_gamma, d_particles, d_tris);
 }
 
+sph2d_status sph2d_backward_from_pairs(sph2d_ctx* h, int kernel, int mode, const void* d_gamma,
+                                       const void* d_grad_gamma, void* d_particles, void* d_tris) {
+  if (!h) return SPH2D_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  c->err.clear();
+  if (!c->cells.built) return set_err(c, SPH2D_ERR_NOT_BUILT, "no pair list built");
+  if (!valid_kernel(kernel)) return set_err(c, SPH2D_ERR_INVALID_ARG, "unknown kernel id");
+  if (mode != SPH2D_FP64 && mode != SPH2D_FP32_FIXUP)
+    return set_err(c, (mode == SPH2D_SURROGATE || mode == SPH2D_FP32_HYBRID) ? SPH2D_ERR_UNSUPPORTED
+                                                                            : SPH2D_ERR_INVALID_ARG,
+                   "backward supports SPH2D_FP64 and SPH2D_FP32_FIXUP");
+  if ((c->cells.N > 0 && (!d_gamma || !d_particles)) || (c->cells.M > 0 && !d_tris))
+    return set_err(c, SPH2D_ERR_INVALID_ARG, "null gradient pointer");
+  cudaSetDevice(c->device);
+  return launch_backward(c, kernel, mode, d_gamma, d_grad_gamma, d_particles, d_tris);
+}
+
 sph2d_status sph2d_field_integrals(sph2d_ctx* h, int kernel, int mode, const float* vertex_values, int nf,
                                    void* value, void* grad) {
   if (!h) return SPH2D_ERR_INVALID_ARG;

@@ -199,3 +199,43 @@ def test_second_order_finite_differences(ctx):
             xm_[a] -= eps
             fd = (loss_particle(i, xp_) - loss_particle(i, xm_)) / (2 * eps)
             assert abs(dp[i, a] - fd) <= 1e-6 * max(1.0, abs(fd)) / H
+
+
+# ---------------------------------------------------------------------------------------
+# backward over the last build's pair list (no second cull)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["fp64", "fp32_fixup"])
+@pytest.mark.parametrize("kernel", ["wendland_c2", "wendland_c4", "cubic_spline"])
+def test_backward_from_pairs_is_the_full_backward(ctx, kernel, mode):
+    """sph2d_backward_from_pairs after a forward call returns exactly what the rebuilding
+    backward returns, with and without the grad gamma term"""
+    import torch
+    w = W.box_obstacle(n=64)
+    rng = np.random.default_rng(41)
+    dt = torch.float64 if mode == "fp64" else torch.float32
+    dg = _t(rng.normal(size=len(w.particles))).to(dt)
+    dgr = _t(rng.normal(size=(len(w.particles), 2))).to(dt)
+    p, t = _t(w.particles), _t(w.triangles)
+    for d_grad in (None, dgr):
+        full_p, full_t = ctx.backward(p, t, kernel, w.H, dg, mode, d_grad)
+        ctx.boundary_integrals(p, t, kernel, w.H, -1, mode)
+        fp_p, fp_t = ctx.backward_from_pairs(kernel, dg, mode, d_grad)
+        assert torch.equal(fp_p, full_p) and torch.equal(fp_t, full_t)
+
+
+def test_backward_from_pairs_statuses(ctx):
+    import torch
+    from paper_2507_21686_gb300._lib import Sph2dError
+    from paper_2507_21686_gb300.api import Context, _ptr
+    fresh = Context(0)
+    dg = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = torch.zeros((4, 6), dtype=torch.float64, device="cuda")
+    assert fresh.lib.sph2d_backward_from_pairs(fresh.h, 0, 0, _ptr(dg), None, _ptr(out), _ptr(out)) == 4   # NOT_BUILT
+    w = W.wall_strip()
+    fresh.build_cells(_t(w.particles), _t(w.triangles), w.H)
+    dg = torch.zeros(len(w.particles), dtype=torch.float64, device="cuda")
+    with pytest.raises(Sph2dError, match="UNSUPPORTED"):
+        fresh.backward_from_pairs("wendland_c2", dg, "surrogate")
+    with pytest.raises(Sph2dError, match="INVALID_ARG"):
+        fresh.backward_from_pairs(9, dg, "fp64")
+    fresh.close()
