@@ -499,30 +499,74 @@ __global__ void __launch_bounds__(128) reduce_pairs_kernel(IntArgs a, const OT* 
   }
 }
 
-// particles without pairs get zeros; particles whose pairs span chunks add their partials
+// one warp's rows of a per-particle output of `width` values (out: the row of the warp's first
+// particle), transposed through shared memory so that the stores are coalesced; a particle is
+// written when its bit is set in `mine`
+template <typename OT, int W>
+__device__ __forceinline__ void warp_rows(OT* __restrict__ out, int width, unsigned mine, const OT* vals,
+                                          OT* __restrict__ buf) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (k < width) buf[lane * width + k] = vals[k];
+  __syncwarp();
+  for (int j = 0; j < width; ++j) {
+    const int w = 32 * j + lane;
+    if ((mine >> (w / width)) & 1u) out[w] = buf[w];
+  }
+  __syncwarp();
+}
+
+// the outputs of a warp's 32 consecutive particles (i: this lane's particle, mine: whether it
+// writes), rows transposed through shared memory; blocks of 256 threads
 template <typename OT, int MD>
-__global__ void finalize_kernel(IntArgs a) {
+__device__ __forceinline__ void write_particles_warp(const IntArgs& a, int64_t i, bool mine, const OT* v) {
+  constexpr int NM = nmom_of(MD), WB = NM > 2 ? NM : 2;
+  __shared__ OT s_buf[8][32 * WB];
+  const unsigned m = __ballot_sync(0xffffffffu, mine);
+  if (m == 0u) return;                                   // warp-uniform
+  const int64_t i0 = i - (threadIdx.x & 31);
+  OT* buf = s_buf[threadIdx.x >> 5];
+  if (mine) static_cast<OT*>(a.gamma)[i] = v[0];
+  if (a.grad) warp_rows<OT, 2>(static_cast<OT*>(a.grad) + 2 * i0, 2, m, v + 1, buf);
+  if (a.nm == 1) {
+    if (mine) static_cast<OT*>(a.mom)[i] = v[0];
+  } else if (MD >= 1 && a.nm > 0) {
+    warp_rows<OT, NM>(static_cast<OT*>(a.mom) + int64_t(a.nm) * i0, a.nm, m, v + 3, buf);
+  }
+}
+
+// particles without pairs get zeros; particles whose pairs span chunks add their partials.  A
+// warp writes its 32 consecutive particles' rows together (blocks of 256 threads).
+template <typename OT, int MD>
+__global__ void __launch_bounds__(256) finalize_kernel(IntArgs a) {
   constexpr int NV = nv_of(MD);
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
-  const int64_t s0 = a.pair_off[i], s1 = a.pair_off[i + 1];
   OT v[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = OT(0);
-  if (s1 > s0) {
-    const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
-    if (c0 == c1) return;   // written by the chunk kernel
-    const OT* slots = static_cast<const OT*>(a.slots);
+  bool mine = false;
+  if (i < a.N) {
+    const int64_t s0 = a.pair_off[i], s1 = a.pair_off[i + 1];
+    mine = true;
+    if (s1 > s0) {
+      const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
+      if (c0 == c1) {
+        mine = false;        // written by the chunk kernel
+      } else {
+        const OT* slots = static_cast<const OT*>(a.slots);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = slots[(c0 * 2 + 1) * NV + k];
-    for (int64_t c = c0 + 1; c < c1; ++c) {
+        for (int k = 0; k < NV; ++k) v[k] = slots[(c0 * 2 + 1) * NV + k];
+        for (int64_t c = c0 + 1; c < c1; ++c) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) v[k] += slots[(c * 2) * NV + k];
+          for (int k = 0; k < NV; ++k) v[k] += slots[(c * 2) * NV + k];
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += slots[(c1 * 2) * NV + k];
+      }
     }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += slots[(c1 * 2) * NV + k];
   }
-  write_particle<OT, MD>(a, i, v);
+  write_particles_warp<OT, MD>(a, i, mine, v);
 }
 
 // grid of at most the blocks of 128 threads that stay resident at once (grid-stride kernels)
@@ -680,51 +724,54 @@ __device__ __forceinline__ void read_particle(const IntArgs& a, int64_t pid, OT*
 // the outputs) or its crossing slots.  A particle whose pairs are all in the last region and
 // within one chunk already has its sum in the outputs.
 template <typename OT, int MD>
-__global__ void split_finalize_kernel(IntArgs a, PairSplit sp) {
+__global__ void __launch_bounds__(256) split_finalize_kernel(IntArgs a, PairSplit sp) {
   constexpr int NV = nv_of(MD);
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
   OT v[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = OT(0);
-  if (a.pair_off[i + 1] > a.pair_off[i]) {
+  bool mine = i < a.N;
+  if (mine && a.pair_off[i + 1] > a.pair_off[i]) {
     const int last = sp.nreg - 1;
     int64_t l0, l1;
     part_range(a, sp, i, last, l0, l1);
-    if (l1 - l0 == a.pair_off[i + 1] - a.pair_off[i] && (l0 >> 5) == ((l1 - 1) >> 5)) return;
-    const OT* slots = static_cast<const OT*>(a.slots);
-    bool first = true;
+    if (l1 - l0 == a.pair_off[i + 1] - a.pair_off[i] && (l0 >> 5) == ((l1 - 1) >> 5)) {
+      mine = false;          // written by the chunk kernel
+    } else {
+      const OT* slots = static_cast<const OT*>(a.slots);
+      bool first = true;
 #pragma unroll 1
-    for (int r = 0; r < sp.nreg; ++r) {
-      int64_t s0, s1;
-      part_range(a, sp, i, r, s0, s1);
-      if (s1 <= s0) continue;
-      OT w[NV];
-      const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
-      if (c0 == c1) {
-        if (r == last) {
-          read_particle<OT, MD>(a, i, w);
+      for (int r = 0; r < sp.nreg; ++r) {
+        int64_t s0, s1;
+        part_range(a, sp, i, r, s0, s1);
+        if (s1 <= s0) continue;
+        OT w[NV];
+        const int64_t c0 = s0 >> 5, c1 = (s1 - 1) >> 5;
+        if (c0 == c1) {
+          if (r == last) {
+            read_particle<OT, MD>(a, i, w);
+          } else {
+            const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) w[k] = src[k];
+          }
         } else {
-          const OT* src = static_cast<const OT*>(sp.part) + (int64_t(r) * a.N + i) * NV;
 #pragma unroll
-          for (int k = 0; k < NV; ++k) w[k] = src[k];
-        }
-      } else {
+          for (int k = 0; k < NV; ++k) w[k] = slots[(c0 * 2 + 1) * NV + k];
+          for (int64_t c = c0 + 1; c < c1; ++c) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] = slots[(c0 * 2 + 1) * NV + k];
-        for (int64_t c = c0 + 1; c < c1; ++c) {
+            for (int k = 0; k < NV; ++k) w[k] += slots[(c * 2) * NV + k];
+          }
 #pragma unroll
-          for (int k = 0; k < NV; ++k) w[k] += slots[(c * 2) * NV + k];
+          for (int k = 0; k < NV; ++k) w[k] += slots[(c1 * 2) * NV + k];
         }
 #pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] += slots[(c1 * 2) * NV + k];
+        for (int k = 0; k < NV; ++k) v[k] = first ? w[k] : v[k] + w[k];
+        first = false;
       }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) v[k] = first ? w[k] : v[k] + w[k];
-      first = false;
     }
   }
-  write_particle<OT, MD>(a, i, v);
+  write_particles_warp<OT, MD>(a, i, mine, v);
 }
 
 // scratch of a K-region partition in pair_list2: header (chunk counter at [4]) | counts
