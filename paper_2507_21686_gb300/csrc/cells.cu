@@ -424,19 +424,38 @@ __global__ void pair_copy_kernel(int64_t N, const int64_t* __restrict__ cand_off
   const int64_t coff = i0 + lane < N ? cand_off[i0 + lane] : 0;
   const int64_t beg = __shfl_sync(0xffffffffu, off, 0);
   const int64_t end = pair_off[i0 + 32 < N ? i0 + 32 : N];
-  for (int64_t base = beg; base < end; base += 32) {     // uniform trip count: every lane shuffles
-    const int64_t pos = base + lane;
+  // four output positions per lane per step, so that four searches and four gathers are in
+  // flight together; uniform trip count: every lane shuffles
+  constexpr int U = 4;
+  for (int64_t base = beg; base < end; base += 32 * U) {
+    int64_t pos[U];
+    int j[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pos[u] = base + 32 * u + lane;
+      j[u] = 0;
+    }
     // largest j with off_j <= pos (particles with no pairs share their offset with the next)
-    int j = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
-      const int64_t o = __shfl_sync(0xffffffffu, off, j + step);
-      if (o <= pos && i0 + j + step < N) j += step;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t o = __shfl_sync(0xffffffffu, off, j[u] + step);
+        if (o <= pos[u] && i0 + j[u] + step < N) j[u] += step;
+      }
     }
-    const int64_t oj = __shfl_sync(0xffffffffu, off, j), cj = __shfl_sync(0xffffffffu, coff, j);
-    if (pos < end) {
-      pair_tri[pos] = kept[cj + (pos - oj)];
-      pair_pid[pos] = int32_t(i0 + j);
+    int32_t t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t oj = __shfl_sync(0xffffffffu, off, j[u]), cj = __shfl_sync(0xffffffffu, coff, j[u]);
+      t[u] = pos[u] < end ? kept[cj + (pos[u] - oj)] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (pos[u] < end) {
+        pair_tri[pos[u]] = t[u];
+        pair_pid[pos[u]] = int32_t(i0 + j[u]);
+      }
     }
   }
 }
